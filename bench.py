@@ -1,0 +1,491 @@
+#!/usr/bin/env python3
+"""Benchmark of the dynamic graph store's hot path on the power-law workload.
+
+Workload (R-MAT scale 20: V = 1,048,576, 16,777,216 draws with a/b/c/d =
+0.57/0.19/0.19/0.05, duplicates and self-loops dropped, weights U[1,100];
+buckets from the load-factor rule with load factor 0.7).  One step is one
+pass of the whole path on one batch size B (default 2^20):
+
+    insert B new R-MAT edges -> incremental BFS, SSSP (from the max-degree
+    vertex) and WCC -> commit -> delete B live edges -> BFS, SSSP (decremental)
+    and WCC (static recompute) -> commit -> query B edges (half present)
+
+value = 3B edges (inserted + deleted + queried) / step time, in Medges/s,
+with inputs resident in device memory; `e2e` is the same through the C-ABI
+with the inputs copied from pinned host buffers and the results (flags,
+bitmap, SSSP distances) copied back inside the timed region.  L2 is flushed
+between steps by writing a 512 MiB buffer.
+
+`--impl reference` times the CPU oracle (plain single-threaded C++,
+recomputing everything from scratch) on the same workload and metric.
+Under torchrun each rank runs an independent replica (weak scaling); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched edge insert/delete/query Medges/s; incr-SSSP ms; % of HBM roofline"
+UNIT = "Medges/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--batch", type=int, default=1 << 20)
+    p.add_argument("--scale", type=int, default=20)
+    p.add_argument("--draws", type=int, default=1 << 24)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------- ranks
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, use_cuda):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def reduce_across(values, op, dist, device):
+    """all_reduce of a list of floats (op: 'max' or 'sum'); identity at N=1."""
+    if dist is None:
+        return list(values)
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.cpu().tolist()
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# -------------------------------------------------------------- workload
+
+def make_workload(args, n_batches):
+    import synth
+
+    t0 = time.time()
+    G = synth.powerlaw_graph(scale=args.scale, draws=args.draws)
+    deg = np.bincount(G.src, minlength=G.V)
+    source = int(np.argmax(deg))
+    batches = [synth.powerlaw_batch(G, k, args.batch) for k in range(n_batches)]
+    return G, source, batches, time.time() - t0
+
+
+def workload_config(args, G):
+    return {
+        "workload": "R-MAT scale %d power-law graph (V=%d, %d edges after dropping duplicates and self-loops, "
+                    "weights U[1,100]); step = insert %d + incr BFS/SSSP/WCC + delete %d + decr BFS/SSSP + "
+                    "static WCC + query %d" % (args.scale, G.V, len(G.src), args.batch, args.batch, args.batch),
+        "vertices": G.V,
+        "edges": int(len(G.src)),
+        "batch": args.batch,
+        "buckets": "load-factor rule, load factor 0.7",
+        "l2": "flushed between timed steps (512 MiB write)",
+        "parallelism": "independent replica per GPU",
+    }
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self, gpu_index=0):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        busy = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------- roofline model
+
+def algorithmic_bytes(family, ctr, n_per_launch, launches):
+    """Bytes the method must move for one kernel family over the timed
+    region, from the work counters: slabs are 128 B, an index gather counts
+    one 32 B sector, a random 8 B read-modify-write counts 8 B each way."""
+    if family == "query":
+        return launches * n_per_launch * (8 + 32 + 0.125) + 128 * ctr["query_slabs"]
+    if family == "insert":
+        return launches * n_per_launch * (12 + 32 + 32) + 128 * (ctr["insert_slabs"] + ctr["insert_new_slabs"])
+    if family == "delete":
+        return launches * n_per_launch * (8 + 32 + 32) + 128 * ctr["delete_slabs"]
+    if family == "sssp_round":
+        return (ctr["relax_lists"] * (4 + 4 + 8) + 128 * ctr["relax_slabs"] + 16 * ctr["relax_edges"]
+                + ctr["relax_improved"] * (8 + 4 + 8))
+    if family in ("wcc_hook_all", "wcc_hook_updated"):
+        return 128 * ctr["wcc_slabs"] + 16 * ctr["wcc_edges"]
+    return None
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    lib = mk.load()
+    W, K, B = args.warmup, args.steps, args.batch
+    n_e2e = 0 if args.no_e2e else K
+    G, source, batches, gen_s = make_workload(args, W + K + n_e2e)
+    V, E = G.V, len(G.src)
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def u32(a):
+        return mk.to_device_u32(a, device)
+
+    src_d = u32(G.src)
+    buckets = mk.bucket_rule(V, src_d, 0.7)
+    g = mk.Graph(V, edge_capacity_hint=E + (W + K + n_e2e + 2) * B, buckets=buckets)
+    h = g.handle
+    chunk = 1 << 22
+    dst_d, w_d = u32(G.dst), u32(G.w)
+    for i in range(0, E, chunk):
+        mk.check(lib.mk_insert_batch(h, ctypes.c_void_p(src_d[i:i + chunk].data_ptr()),
+                                     ctypes.c_void_p(dst_d[i:i + chunk].data_ptr()),
+                                     ctypes.c_void_p(w_d[i:i + chunk].data_ptr()), min(chunk, E - i), None, sp),
+                 "load")
+    del src_d, dst_d, w_d
+    g.commit()
+    out = {k: torch.empty(V, dtype=torch.int32, device=device) for k in
+           ("bd", "bp", "sd", "sp", "lab")}
+    fl_i = torch.empty(B, dtype=torch.uint8, device=device)
+    fl_d = torch.empty(B, dtype=torch.uint8, device=device)
+    bm = torch.empty((B + 31) // 32, dtype=torch.int32, device=device)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    for fn, a, b in ((lib.mk_incr_bfs, "bd", "bp"), (lib.mk_incr_sssp, "sd", "sp")):
+        mk.check(fn(h, source, P(out[a]), P(out[b]), sp), "static")
+    mk.check(lib.mk_incr_wcc(h, P(out["lab"]), sp), "static wcc")
+    g.commit()
+    torch.cuda.synchronize()
+    st = g.last_error()
+    if st != mk.MK_OK:
+        raise RuntimeError("device status %d after the load" % st)
+
+    dev_batches = []
+    for bt in batches[:W + K]:
+        dev_batches.append({k: u32(bt[k]) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst",
+                                                     "q_src", "q_dst")})
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+    names = ["insert", "bfs1", "sssp1", "wcc1", "commit1", "delete", "bfs2", "sssp2", "wcc2", "commit2", "query"]
+
+    def step(bt, ev):
+        ev[0].record(stream)
+        mk.check(lib.mk_insert_batch(h, P(bt["ins_src"]), P(bt["ins_dst"]), P(bt["ins_w"]), B, P(fl_i), sp), "ins")
+        ev[1].record(stream)
+        mk.check(lib.mk_incr_bfs(h, source, P(out["bd"]), P(out["bp"]), sp), "bfs")
+        ev[2].record(stream)
+        mk.check(lib.mk_incr_sssp(h, source, P(out["sd"]), P(out["sp"]), sp), "sssp")
+        ev[3].record(stream)
+        mk.check(lib.mk_incr_wcc(h, P(out["lab"]), sp), "wcc")
+        ev[4].record(stream)
+        mk.check(lib.mk_commit_batch(h, sp), "commit")
+        ev[5].record(stream)
+        mk.check(lib.mk_delete_batch(h, P(bt["del_src"]), P(bt["del_dst"]), B, P(fl_d), sp), "del")
+        ev[6].record(stream)
+        mk.check(lib.mk_incr_bfs(h, source, P(out["bd"]), P(out["bp"]), sp), "bfs")
+        ev[7].record(stream)
+        mk.check(lib.mk_incr_sssp(h, source, P(out["sd"]), P(out["sp"]), sp), "sssp")
+        ev[8].record(stream)
+        mk.check(lib.mk_incr_wcc(h, P(out["lab"]), sp), "wcc")
+        ev[9].record(stream)
+        mk.check(lib.mk_commit_batch(h, sp), "commit")
+        ev[10].record(stream)
+        mk.check(lib.mk_query_batch(h, P(bt["q_src"]), P(bt["q_dst"]), B, P(bm), None, sp), "query")
+        ev[11].record(stream)
+
+    def events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(12)]
+
+    for k in range(W):
+        flush.fill_(k)
+        step(dev_batches[k], events())
+    torch.cuda.synchronize()
+    if g.last_error() != mk.MK_OK:
+        raise RuntimeError("device status after warm-up")
+    g.counters(reset=True)
+    g.profile(True)
+    launches0 = g.launch_count()
+    evs = [events() for _ in range(K)]
+    clock = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+                         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
+    barrier(dist, device)
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    with clock:
+        for k in range(K):
+            flush.fill_(k + 1)
+            step(dev_batches[W + k], evs[k])
+        torch.cuda.synchronize()
+    wall = time.time() - wall0
+    barrier(dist, device)
+    launches = g.launch_count() - launches0
+    prof = g.profile_read()
+    g.profile(False)
+    ctr = g.counters()
+    status = g.last_error()
+    if status != mk.MK_OK:
+        raise RuntimeError("device status %d in the timed region" % status)
+    step_ms = [evs[k][0].elapsed_time(evs[k][11]) for k in range(K)]
+    phase = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
+             for i, n in enumerate(names)}
+    local_ms = statistics.mean(step_ms)
+    ms_max, = reduce_across([local_ms], "max", dist, device)
+    units_total, = reduce_across([3.0 * B], "sum", dist, device)
+    value = units_total / (ms_max / 1e3) / 1e6
+
+    # roofline: kernel family with the largest share of the timed region
+    fam_time = {name: t for name, (n, t) in prof.items()}
+    fam_launch = {name: n for name, (n, t) in prof.items()}
+    dom = max(fam_time, key=fam_time.get)
+    per_launch_n = B
+    bytes_total = algorithmic_bytes(dom, ctr, per_launch_n, fam_launch[dom])
+    peak, peak_kind = measured_peak()
+    roof = None
+    if bytes_total is not None and fam_time[dom] > 0:
+        per_launch_bytes = bytes_total / fam_launch[dom]
+        avg_ms = fam_time[dom] / fam_launch[dom]
+        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": int(per_launch_bytes), "avg_launch_ms": round(avg_ms, 4),
+                "launches": fam_launch[dom]}
+    # every family's share and achieved bandwidth, for the record
+    kernels = {}
+    total_prof = sum(fam_time.values()) or 1.0
+    for name in sorted(fam_time, key=fam_time.get, reverse=True):
+        bt = algorithmic_bytes(name, ctr, B, fam_launch[name])
+        kernels[name] = {"launches": fam_launch[name], "ms": round(fam_time[name], 3),
+                         "share": round(fam_time[name] / total_prof, 4)}
+        if bt is not None and fam_time[name] > 0:
+            kernels[name]["gbs"] = round(bt / (fam_time[name] / 1e3) / 1e9, 1)
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic", "config": workload_config(args, G),
+        "insert_medges_s": round(B / phase["insert"] / 1e3, 1),
+        "delete_medges_s": round(B / phase["delete"] / 1e3, 1),
+        "query_medges_s": round(B / phase["query"] / 1e3, 1),
+        "incr_sssp_ms": round(phase["sssp1"], 3), "decr_sssp_ms": round(phase["sssp2"], 3),
+        "incr_bfs_ms": round(phase["bfs1"], 3), "decr_bfs_ms": round(phase["bfs2"], 3),
+        "incr_wcc_ms": round(phase["wcc1"], 3), "static_wcc_ms": round(phase["wcc2"], 3),
+        "phases_ms": {k: round(v, 3) for k, v in phase.items()},
+        "roofline": roof, "kernels": kernels, "counters": ctr,
+        "gpu_launches": int(launches), "wall_s_timed": round(wall, 3), "gen_s": round(gen_s, 1),
+        "clocks": clock.summary(local),
+    }
+
+    # end to end through the C ABI with host buffers
+    if n_e2e:
+        host = []
+        for bt in batches[W + K:W + K + n_e2e]:
+            host.append({k: torch.from_numpy(np.ascontiguousarray(bt[k]).view(np.int32)).pin_memory()
+                         for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst", "q_src", "q_dst")})
+        stage = {k: torch.empty(B, dtype=torch.int32, device=device) for k in host[0]}
+        h_fl_i = torch.empty(B, dtype=torch.uint8).pin_memory()
+        h_fl_d = torch.empty(B, dtype=torch.uint8).pin_memory()
+        h_bm = torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory()
+        h_sd = torch.empty(V, dtype=torch.int32).pin_memory()
+        h_spar = torch.empty(V, dtype=torch.int32).pin_memory()
+        e2e_ms = []
+        for k in range(n_e2e):
+            flush.fill_(100 + k)
+            e = events()
+            torch.cuda.synchronize()
+            e[0].record(stream)
+            for key in stage:
+                stage[key].copy_(host[k][key], non_blocking=True)
+            step(stage, e[1:] + [torch.cuda.Event(enable_timing=True)])
+            h_fl_i.copy_(fl_i, non_blocking=True)
+            h_fl_d.copy_(fl_d, non_blocking=True)
+            h_bm.copy_(bm, non_blocking=True)
+            h_sd.copy_(out["sd"], non_blocking=True)
+            h_spar.copy_(out["sp"], non_blocking=True)
+            e[11].record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(e[0].elapsed_time(e[11]))
+        if g.last_error() != mk.MK_OK:
+            raise RuntimeError("device status in the e2e pass")
+        e2e_local = statistics.mean(e2e_ms)
+        e2e_max, = reduce_across([e2e_local], "max", dist, device)
+        result["e2e"] = {"value": round(units_total / (e2e_max / 1e3) / 1e6, 2), "unit": UNIT,
+                         "h2d_bytes_per_step": int(B * 4 * 7), "d2h_bytes_per_step": int(2 * B + 4 * ((B + 31) // 32)
+                                                                                         + 8 * V),
+                         "ms_per_step": round(e2e_max, 3)}
+    g.close()
+    return result, dist, G, source, batches
+
+
+# ------------------------------------------------------------- CPU oracle
+
+ORACLE_SAMPLE = ("insert, delete and query of the step's B edges each, plus one from-scratch recompute of BFS, "
+                 "Dijkstra SSSP and union-find WCC after the insert batch; the step time counts that recompute "
+                 "twice, because the full step recomputes after each of its two update batches; single thread")
+
+
+def oracle_step(o, bt, source):
+    """Seconds of one step of the workload on the oracle (bounded sample:
+    the recompute after the delete batch is taken to cost the same as the
+    one after the insert batch)."""
+    t0 = time.perf_counter()
+    o.insert(bt["ins_src"], bt["ins_dst"], bt["ins_w"])
+    t1 = time.perf_counter()
+    o.bfs(source)
+    o.sssp(source)
+    o.wcc()
+    t2 = time.perf_counter()
+    o.delete(bt["del_src"], bt["del_dst"])
+    o.query(bt["q_src"], bt["q_dst"])
+    t3 = time.perf_counter()
+    return (t1 - t0) + 2 * (t2 - t1) + (t3 - t2)
+
+
+def run_oracle_steps(G, batches, source, steps, B):
+    import oracle
+
+    o = oracle.OracleGraph(G.V)
+    o.insert(G.src, G.dst, G.w)
+    secs = [oracle_step(o, batches[k], source) for k in range(steps)]
+    return secs
+
+
+def cpu_baseline(G, batches, source, B):
+    secs = run_oracle_steps(G, batches, source, 1, B)
+    s = secs[0]
+    return {"value": round(3 * B / s / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ORACLE_SAMPLE + "; B = %d; %.1f s per step" % (B, s)}
+
+
+def run_reference(args, world, rank, local):
+    if rank != 0:
+        return None
+    W, K, B = args.warmup, args.steps, args.batch
+    G, source, batches, _ = make_workload(args, W + K)
+    import oracle
+
+    o = oracle.OracleGraph(G.V)
+    o.insert(G.src, G.dst, G.w)
+    for k in range(W):
+        oracle_step(o, batches[k], source)
+    secs = [oracle_step(o, batches[W + k], source) for k in range(K)]
+    ms = statistics.mean(secs) * 1e3
+    value = 3 * B / (ms / 1e3) / 1e6
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic", "config": workload_config(args, G),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": ORACLE_SAMPLE + "; B = %d" % B},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, world, rank, local)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return 0
+    result, dist, G, source, batches = run_ours(args, world, rank, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(G, batches, source, args.batch)
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * meerkat.h -- C ABI of the GB300 slab-hash dynamic graph store.
+ *
+ * The store keeps a directed graph with 32-bit vertex ids and 32-bit edge
+ * weights as one hash table per vertex, each bucket a chain of 128-byte
+ * slabs (paper, Sec. "Motivation": SlabGraph on SlabHash; Sec. "Memory
+ * Management in Meerkat": all head slabs in one allocation, located through an
+ * exclusive scan of per-vertex bucket counts).  A slab is 32 four-byte lanes:
+ * lanes 2p and 2p+1 (p = 0..14) hold the destination and the weight of one
+ * edge (the weighted ConcurrentMap layout), lane 30 is unused and lane 31
+ * holds the index of the next slab of the chain.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE pointers (for example the data_ptr() of a
+ *    CUDA tensor) owned by the caller.  The library never frees them and does
+ *    not keep them after the call's work has been enqueued.
+ *  - `stream` is a cudaStream_t passed as void* (0 = the legacy default
+ *    stream).  Work is enqueued on it and the call returns without waiting,
+ *    unless its comment says it synchronises.  Results are valid once the
+ *    stream has reached that point.
+ *  - The library owns the slab pool, the per-list update metadata, the change
+ *    log and the state of every incremental algorithm.  One graph must not be
+ *    used from two host threads at once.
+ *  - Vertex ids must be < V.  0xFFFFFFFF, 0xFFFFFFFE and 0xFFFFFFFD are
+ *    reserved (INF/INVALID, EMPTY key, TOMBSTONE key; paper, footnotes on
+ *    EMPTY_KEY and TOMBSTONE_KEY), so V <= 0xFFFFFFFD.
+ *  - Errors found on the host (null pointer, bad size, unknown handle) are
+ *    returned at once and nothing is enqueued.  Errors found on the device
+ *    (a vertex id >= V, a weight of 0, an exhausted slab pool, an expired
+ *    bounded wait) are recorded in the graph's sticky status word; every later
+ *    kernel of that graph then does nothing until mk_last_error() reads and
+ *    clears the word.  A batch rejected this way is not applied (an exhausted
+ *    pool is the exception: see mk_insert_batch).
+ *  - All arithmetic is unsigned integer; results are exact.
+ */
+#ifndef MEERKAT_H
+#define MEERKAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mk_graph mk_graph;
+typedef int mk_status;
+
+enum {
+    MK_OK = 0,
+    MK_ERR_INVALID_ARG = -1,    /* bad argument (host) or bad vertex id / weight (device) */
+    MK_ERR_POOL_EXHAUSTED = -2, /* the slab pool had no free slab for an insert */
+    MK_ERR_TIMEOUT = -3,        /* a bounded device loop hit its iteration limit */
+    MK_ERR_CUDA = -4,           /* a CUDA runtime call failed */
+    MK_ERR_NO_MEMORY = -5,      /* a device or host allocation failed */
+    MK_ERR_INTERNAL = -6
+};
+
+#define MK_NONE 0xFFFFFFFFu       /* INF distance, INVALID parent, null slab */
+#define MK_INVALID_LANE 0xFFu     /* update marker: the marked slab is full */
+
+/* Sizing of a new graph.  Zero fields take the defaults noted. */
+typedef struct mk_config {
+    uint32_t V;                          /* vertices [0, V) */
+    uint64_t edge_capacity_hint;         /* expected peak edge count (pool sizing) */
+    uint32_t buckets;                    /* buckets of every vertex when d_bucket_per_vertex is NULL (0 = 1) */
+    const uint32_t *d_bucket_per_vertex; /* device, V entries >= 1, or NULL */
+    uint64_t pool_slabs;                 /* overflow slabs in the pool (0 = from the hint) */
+} mk_config;
+
+/* Graph statistics (mk_graph_stats). */
+typedef struct mk_stats {
+    uint32_t V;
+    uint64_t lists;          /* slab lists = head slabs = sum of bucket counts */
+    uint64_t pool_slabs;     /* capacity of the overflow pool */
+    uint64_t pool_used;      /* pool slabs marked allocated in the bitmap */
+    uint64_t chain_slabs;    /* slabs reachable from the heads (heads included) */
+    uint64_t live_edges;     /* valid (dst, weight) pairs */
+    uint64_t tombstones;     /* deleted pairs still occupying a lane */
+    uint32_t chain_max;      /* longest chain, in slabs */
+    double chain_mean;       /* mean chain length, in slabs */
+    uint64_t device_bytes;   /* device memory held by the graph */
+    uint64_t epoch;          /* number of mk_commit_batch calls so far */
+} mk_stats;
+
+/* One line of the optional per-kernel timing (mk_profile_read). */
+typedef struct mk_kernel_time {
+    char name[48];
+    uint64_t launches;
+    double total_ms;         /* sum of CUDA-event durations on the launch stream */
+} mk_kernel_time;
+
+/* ------------------------------------------------------------------ setup */
+
+/* Per-vertex bucket counts from an initial edge list by the load-factor rule
+ * buckets(v) = max(1, ceil(outdeg(v) / (load_factor * 15))) (paper, Sec.
+ * "Motivation": a bucket count fixed a priori by the load factor and the
+ * number of adjacent vertices).  d_src: n source ids; d_buckets: V outputs.
+ * load_factor must be in (0, 1]. */
+mk_status mk_bucket_rule(uint32_t V, const uint32_t *d_src, uint64_t n, float load_factor,
+                         uint32_t *d_buckets, void *stream);
+
+/* Creates an empty graph: one allocation of sum(buckets) head slabs located
+ * by an exclusive scan of the bucket counts (paper, Sec. "Memory Management
+ * in Meerkat"), plus a slab pool with an occupancy bitmap.  The pool holds
+ * `pool_slabs` slabs, or when 0: edge_capacity_hint / 15 + lists / 8 + 1024
+ * rounded up to 32.  Synchronises `stream`.  *out receives the handle. */
+mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out);
+
+/* Same with the arguments of the paper's problem statement:
+ * graph_create(V, E, buckets) with an optional per-vertex bucket array. */
+mk_status mk_graph_create(uint32_t V, uint64_t edge_capacity_hint, uint32_t buckets,
+                          const uint32_t *d_bucket_per_vertex, void *stream, mk_graph **out);
+
+/* Frees every device buffer of the graph after synchronising the device. */
+mk_status mk_graph_destroy(mk_graph *g);
+
+/* ---------------------------------------------------------------- updates */
+
+/* Inserts n edges (d_src[i], d_dst[i]) with weight d_w[i] (d_w NULL = weight
+ * 1; a weight must be >= 1).  Set semantics (paper, Sec. "Experimental
+ * Evaluation", insertion: an edge is stored at the end of its slab list only
+ * if it is not already present): an edge already in the graph keeps its
+ * weight.  Within the batch the first occurrence of a repeated (src, dst)
+ * is the one stored.  The batch is sorted and grouped by source (a radix sort
+ * on (src, dst)); one warp handles the edges of one slab list, walks the
+ * whole chain once with 128-byte slab loads, claims free pairs with 64-bit
+ * atomicCAS and links pool slabs taken from the bitmap allocator.
+ * d_inserted (n bytes, nullable): 1 where edge i was stored by this call.
+ * If the pool runs out, the status becomes MK_ERR_POOL_EXHAUSTED and the
+ * batch is applied partially: exactly the edges flagged 1 were stored.
+ * Marks the touched slab lists as updated for the UpdateIterator. */
+mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w,
+                          uint64_t n, uint8_t *d_inserted, void *stream);
+
+/* Deletes n edges: a present edge's pair becomes TOMBSTONE (never reused;
+ * paper, Sec. "Experimental Evaluation", deletion), an absent edge is a
+ * no-op; the first occurrence of a repeated pair is the one that deletes.
+ * Sorted and grouped like mk_insert_batch.  d_deleted (n bytes, nullable):
+ * 1 where edge i was removed by this call.  Removed edges enter the graph's
+ * change log for the decremental algorithms. */
+mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                          uint8_t *d_deleted, void *stream);
+
+/* Looks up n edges (paper, Sec. "Experimental Evaluation", query: hash to one
+ * bucket, walk its chain).  d_bitmap (ceil(n/32) words, required): bit i%32 of
+ * word i/32 is 1 iff edge i is present.  d_w (n words, nullable): the stored
+ * weight, or 0 when absent.  Queries are independent and unsorted; one
+ * 8-lane group with 16-byte loads walks one query's chain. */
+mk_status mk_query_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                         uint32_t *d_bitmap, uint32_t *d_w, void *stream);
+
+/* Closes the current update epoch: runs UpdateSlabPointers (paper, Sec.
+ * "Graph Primitives", Fig. "UpdateSlabPointers()") on every updated slab
+ * list -- its marker moves to the first free lane of its last slab (or to
+ * MK_INVALID_LANE when that slab is full) and its updated flag is cleared --
+ * and empties the change log.  Incremental algorithm states that have seen
+ * every batch of the epoch stay incremental; the others recompute statically
+ * at their next call. */
+mk_status mk_commit_batch(mk_graph *g, void *stream);
+
+/* ------------------------------------------------------------- algorithms */
+
+/* Single-source shortest paths with uint32 weights (paper, Algorithm "SSSP -
+ * Incremental / Decremental").  The first call for `source` runs the static
+ * algorithm; later calls update the stored tree from the change log of the
+ * current epoch: decremental prologue (invalidate the subtrees below deleted
+ * tree edges, then relax every edge from a valid into an invalid vertex),
+ * incremental prologue (relax the edges inserted since the last commit, found
+ * with the UpdateIterator), then frontier rounds until no distance improves.
+ * Writes V entries to d_dist (distance, MK_NONE if unreachable) and d_parent
+ * (the smallest-id vertex u with dist(u) + w(u,v) = dist(v); the source is
+ * its own parent; MK_NONE if unreachable).  Either output may be NULL.  Path
+ * lengths must stay below 0xFFFFFFFF. */
+mk_status mk_incr_sssp(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream);
+
+/* Breadth-first search: mk_incr_sssp on the unweighted view (every weight
+ * read as 1); distances are hop counts.  Separate state from mk_incr_sssp. */
+mk_status mk_incr_bfs(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream);
+
+/* Weakly connected components (paper, Sec. "Incremental WCC"): union-find with
+ * Union-Async hooking of the larger root under the smaller and full path
+ * compression.  The first call, and any call whose epoch holds deletions
+ * (the paper has no decremental WCC), runs the static pass over every edge;
+ * otherwise only the edges inserted since the last commit are united, found
+ * with the UpdateIterator.  d_label (V words): the smallest vertex id of each
+ * vertex's component. */
+mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream);
+
+/* ------------------------------------------------------------- inspection */
+
+/* Writes up to `cap` live edges sorted by (src, dst) to d_src/d_dst/d_w and
+ * the total live edge count to *d_count (device, one uint64). */
+mk_status mk_graph_export(mk_graph *g, uint64_t cap, uint32_t *d_src, uint32_t *d_dst, uint32_t *d_w,
+                          uint64_t *d_count, void *stream);
+
+/* Fills *out (host memory).  Synchronises `stream`. */
+mk_status mk_graph_stats(mk_graph *g, mk_stats *out, void *stream);
+
+/* Synchronises the graph's last stream, returns the sticky device status
+ * (MK_OK or an MK_ERR_* code) and clears it. */
+mk_status mk_last_error(mk_graph *g);
+
+/* UpdateIterator marker of slab list `bucket` of vertex v (host outputs):
+ * *slab = index of the marked slab, *lane = first lane of the new entries in
+ * it (MK_INVALID_LANE if the slab was full), *updated = the list's flag.
+ * Synchronises `stream`. */
+mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *slab, uint32_t *lane,
+                         uint32_t *updated, void *stream);
+
+/* Work counters accumulated by the kernels since the last reset, in this
+ * order: query slabs loaded, insert slabs loaded, insert slabs linked,
+ * delete slabs loaded, relaxed lists, relaxation slabs loaded, live edges
+ * relaxed, improved vertices, invalidation slabs loaded, WCC slabs loaded,
+ * WCC edges united, commit slabs loaded (then 4 reserved).  Copies up to n
+ * (<= 16) values to out (host); reset != 0 zeroes them.  Synchronises
+ * `stream`. */
+mk_status mk_counters(mk_graph *g, uint64_t *out, int n, int reset, void *stream);
+
+/* Per-kernel timing: when on, every library kernel launch is bracketed by
+ * CUDA events on its stream.  mk_profile_read synchronises the device, fills
+ * up to `cap` entries of `out` (host) with the totals since the last reset,
+ * sets *n_out and resets the totals. */
+mk_status mk_profile_enable(mk_graph *g, int on);
+mk_status mk_profile_read(mk_graph *g, mk_kernel_time *out, int cap, int *n_out);
+
+/* Number of kernel launches the library has made for this graph since
+ * creation (sorting and scan calls included, counted from their launch
+ * plans). */
+uint64_t mk_launch_count(mk_graph *g);
+
+/* Library version string. */
+const char *mk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEERKAT_H */

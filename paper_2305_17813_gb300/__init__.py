@@ -1,0 +1,215 @@
+"""GB300 slab-hash dynamic graph store (Python binding).
+
+A thin layer over the C ABI of ``include/meerkat.h``: it only turns tensors
+into device pointers and CUDA streams into handles.  Every step runs in the
+CUDA kernels of ``libmeerkat.so``; if that library is missing the import of
+``Graph`` still works but any call raises.
+
+Device arrays are torch CUDA tensors; 32-bit ids and weights travel as
+``torch.int32`` tensors holding the unsigned bit patterns (numpy ``uint32``
+arrays are accepted and copied to the device).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._native import (MK_ERR_CUDA, MK_ERR_INTERNAL, MK_ERR_INVALID_ARG, MK_ERR_NO_MEMORY, MK_ERR_POOL_EXHAUSTED,
+                      MK_ERR_TIMEOUT, MK_INVALID_LANE, MK_NONE, MK_OK, MkError, check, load, mk_config, mk_kernel_time,
+                      mk_stats)
+
+__all__ = [
+    "Graph", "load", "MkError", "MK_OK", "MK_ERR_INVALID_ARG", "MK_ERR_POOL_EXHAUSTED", "MK_ERR_TIMEOUT",
+    "MK_ERR_CUDA", "MK_ERR_NO_MEMORY", "MK_ERR_INTERNAL", "MK_NONE", "MK_INVALID_LANE", "bucket_rule",
+    "to_device_u32", "to_numpy_u32",
+]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def to_device_u32(x, device="cuda"):
+    """A contiguous int32 CUDA tensor holding the uint32 values of x."""
+    torch = _torch()
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if x.dtype in (torch.int32, torch.uint32):
+            t = x.to(device=device).contiguous()
+            return t.view(torch.int32) if t.dtype == torch.uint32 else t
+        x = x.cpu().numpy()
+    a = np.ascontiguousarray(np.asarray(x))
+    if a.dtype != np.uint32:
+        if a.size and (a.min() < 0 or a.max() > 0xFFFFFFFF):
+            raise ValueError("values do not fit in uint32")
+        a = a.astype(np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+def to_numpy_u32(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def bucket_rule(V: int, src, load_factor: float = 0.7, stream=None):
+    """Per-vertex bucket counts max(1, ceil(outdeg / (load_factor * 15)))."""
+    torch = _torch()
+    lib = load()
+    s = to_device_u32(src)
+    out = torch.empty(V, dtype=torch.int32, device=s.device)
+    check(lib.mk_bucket_rule(V, _ptr(s), s.numel(), load_factor, _ptr(out), _stream(stream)), "mk_bucket_rule")
+    return out
+
+
+class Graph:
+    """One dynamic graph on the current CUDA device.
+
+    ``buckets`` is either an int (same bucket count for every vertex) or a
+    device tensor of V per-vertex counts (see ``bucket_rule``).
+    """
+
+    def __init__(self, V: int, edge_capacity_hint: int = 0, buckets=1, pool_slabs: int = 0, stream=None):
+        torch = _torch()
+        self._lib = load()
+        self.V = int(V)
+        cfg = mk_config()
+        cfg.V = self.V
+        cfg.edge_capacity_hint = int(edge_capacity_hint)
+        self._bucket_tensor = None
+        if isinstance(buckets, int):
+            cfg.buckets = buckets
+        else:
+            self._bucket_tensor = to_device_u32(buckets)
+            cfg.d_bucket_per_vertex = self._bucket_tensor.data_ptr()
+        cfg.pool_slabs = int(pool_slabs)
+        h = ctypes.c_void_p()
+        check(self._lib.mk_graph_create_ex(ctypes.byref(cfg), _stream(stream), ctypes.byref(h)), "mk_graph_create")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mk_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---------------------------------------------------------- updates
+    def insert(self, src, dst, w=None, flags: bool = True, stream=None):
+        torch = _torch()
+        s, d, ww = to_device_u32(src), to_device_u32(dst), to_device_u32(w)
+        n = s.numel()
+        f = torch.empty(n, dtype=torch.uint8, device=self.device) if flags else None
+        check(self._lib.mk_insert_batch(self._h, _ptr(s), _ptr(d), _ptr(ww), n, _ptr(f), _stream(stream)),
+              "mk_insert_batch")
+        return f
+
+    def delete(self, src, dst, flags: bool = True, stream=None):
+        torch = _torch()
+        s, d = to_device_u32(src), to_device_u32(dst)
+        n = s.numel()
+        f = torch.empty(n, dtype=torch.uint8, device=self.device) if flags else None
+        check(self._lib.mk_delete_batch(self._h, _ptr(s), _ptr(d), n, _ptr(f), _stream(stream)), "mk_delete_batch")
+        return f
+
+    def query(self, src, dst, weights: bool = True, stream=None):
+        torch = _torch()
+        s, d = to_device_u32(src), to_device_u32(dst)
+        n = s.numel()
+        bm = torch.empty((n + 31) // 32, dtype=torch.int32, device=self.device)
+        w = torch.empty(n, dtype=torch.int32, device=self.device) if weights else None
+        check(self._lib.mk_query_batch(self._h, _ptr(s), _ptr(d), n, _ptr(bm), _ptr(w), _stream(stream)),
+              "mk_query_batch")
+        return bm, w
+
+    def commit(self, stream=None):
+        check(self._lib.mk_commit_batch(self._h, _stream(stream)), "mk_commit_batch")
+
+    # ------------------------------------------------------- algorithms
+    def sssp(self, source: int, stream=None):
+        torch = _torch()
+        dist = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        par = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        check(self._lib.mk_incr_sssp(self._h, int(source), _ptr(dist), _ptr(par), _stream(stream)), "mk_incr_sssp")
+        return dist, par
+
+    def bfs(self, source: int, stream=None):
+        torch = _torch()
+        dist = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        par = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        check(self._lib.mk_incr_bfs(self._h, int(source), _ptr(dist), _ptr(par), _stream(stream)), "mk_incr_bfs")
+        return dist, par
+
+    def wcc(self, stream=None):
+        torch = _torch()
+        lab = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        check(self._lib.mk_incr_wcc(self._h, _ptr(lab), _stream(stream)), "mk_incr_wcc")
+        return lab
+
+    # ------------------------------------------------------- inspection
+    def export(self, stream=None):
+        """Live edges sorted by (src, dst) as three int32 tensors (uint32 bits)."""
+        torch = _torch()
+        st = self.stats(stream)
+        m = int(st["live_edges"])
+        s = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)
+        d = torch.empty_like(s)
+        w = torch.empty_like(s)
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        check(self._lib.mk_graph_export(self._h, m, _ptr(s), _ptr(d), _ptr(w), _ptr(cnt), _stream(stream)),
+              "mk_graph_export")
+        return s[:m], d[:m], w[:m]
+
+    def stats(self, stream=None) -> dict:
+        st = mk_stats()
+        check(self._lib.mk_graph_stats(self._h, ctypes.byref(st), _stream(stream)), "mk_graph_stats")
+        return {f: getattr(st, f) for f, _ in mk_stats._fields_}
+
+    def last_error(self) -> int:
+        return int(self._lib.mk_last_error(self._h))
+
+    def marker(self, v: int, bucket: int = 0, stream=None):
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        check(self._lib.mk_list_marker(self._h, v, bucket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                       _stream(stream)), "mk_list_marker")
+        return a.value, b.value, c.value
+
+    def counters(self, reset: bool = False, stream=None) -> dict:
+        from ._native import COUNTER_NAMES
+
+        buf = (ctypes.c_uint64 * 16)()
+        check(self._lib.mk_counters(self._h, buf, 16, 1 if reset else 0, _stream(stream)), "mk_counters")
+        return {name: int(buf[i]) for i, name in enumerate(COUNTER_NAMES)}
+
+    def profile(self, on: bool = True):
+        check(self._lib.mk_profile_enable(self._h, 1 if on else 0), "mk_profile_enable")
+
+    def profile_read(self) -> dict:
+        buf = (mk_kernel_time * 64)()
+        n = ctypes.c_int()
+        check(self._lib.mk_profile_read(self._h, buf, 64, ctypes.byref(n)), "mk_profile_read")
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
+
+    def launch_count(self) -> int:
+        return int(self._lib.mk_launch_count(self._h))

@@ -1,0 +1,129 @@
+"""ctypes declarations of the C ABI in ``include/meerkat.h``.
+
+Argument marshalling only: every call goes straight to ``libmeerkat.so``.
+The functions keep the C names (``mk_insert_batch`` and so on).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmeerkat.so")
+
+MK_OK = 0
+MK_ERR_INVALID_ARG = -1
+MK_ERR_POOL_EXHAUSTED = -2
+MK_ERR_TIMEOUT = -3
+MK_ERR_CUDA = -4
+MK_ERR_NO_MEMORY = -5
+MK_ERR_INTERNAL = -6
+MK_NONE = 0xFFFFFFFF
+MK_INVALID_LANE = 0xFF
+
+COUNTER_NAMES = ["query_slabs", "insert_slabs", "insert_new_slabs", "delete_slabs", "relax_lists", "relax_slabs",
+                 "relax_edges", "relax_improved", "invalidate_slabs", "wcc_slabs", "wcc_edges", "commit_slabs"]
+
+STATUS_NAMES = {
+    MK_OK: "MK_OK",
+    MK_ERR_INVALID_ARG: "MK_ERR_INVALID_ARG",
+    MK_ERR_POOL_EXHAUSTED: "MK_ERR_POOL_EXHAUSTED",
+    MK_ERR_TIMEOUT: "MK_ERR_TIMEOUT",
+    MK_ERR_CUDA: "MK_ERR_CUDA",
+    MK_ERR_NO_MEMORY: "MK_ERR_NO_MEMORY",
+    MK_ERR_INTERNAL: "MK_ERR_INTERNAL",
+}
+
+
+class MkError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s" % (what, STATUS_NAMES.get(status, status)))
+        self.status = status
+
+
+class mk_config(ctypes.Structure):
+    _fields_ = [
+        ("V", ctypes.c_uint32),
+        ("edge_capacity_hint", ctypes.c_uint64),
+        ("buckets", ctypes.c_uint32),
+        ("d_bucket_per_vertex", ctypes.c_void_p),
+        ("pool_slabs", ctypes.c_uint64),
+    ]
+
+
+class mk_stats(ctypes.Structure):
+    _fields_ = [
+        ("V", ctypes.c_uint32),
+        ("lists", ctypes.c_uint64),
+        ("pool_slabs", ctypes.c_uint64),
+        ("pool_used", ctypes.c_uint64),
+        ("chain_slabs", ctypes.c_uint64),
+        ("live_edges", ctypes.c_uint64),
+        ("tombstones", ctypes.c_uint64),
+        ("chain_max", ctypes.c_uint32),
+        ("chain_mean", ctypes.c_double),
+        ("device_bytes", ctypes.c_uint64),
+        ("epoch", ctypes.c_uint64),
+    ]
+
+
+class mk_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_INT = ctypes.c_int
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "mk_bucket_rule": (_INT, [_U32, _P, _U64, ctypes.c_float, _P, _P]),
+    "mk_graph_create_ex": (_INT, [ctypes.POINTER(mk_config), _P, ctypes.POINTER(_P)]),
+    "mk_graph_create": (_INT, [_U32, _U64, _U32, _P, _P, ctypes.POINTER(_P)]),
+    "mk_graph_destroy": (_INT, [_P]),
+    "mk_insert_batch": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),
+    "mk_delete_batch": (_INT, [_P, _P, _P, _U64, _P, _P]),
+    "mk_query_batch": (_INT, [_P, _P, _P, _U64, _P, _P, _P]),
+    "mk_commit_batch": (_INT, [_P, _P]),
+    "mk_incr_sssp": (_INT, [_P, _U32, _P, _P, _P]),
+    "mk_incr_bfs": (_INT, [_P, _U32, _P, _P, _P]),
+    "mk_incr_wcc": (_INT, [_P, _P, _P]),
+    "mk_graph_export": (_INT, [_P, _U64, _P, _P, _P, _P, _P]),
+    "mk_graph_stats": (_INT, [_P, ctypes.POINTER(mk_stats), _P]),
+    "mk_last_error": (_INT, [_P]),
+    "mk_list_marker": (_INT, [_P, _U32, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), _P]),
+    "mk_counters": (_INT, [_P, ctypes.POINTER(_U64), _INT, _INT, _P]),
+    "mk_profile_enable": (_INT, [_P, _INT]),
+    "mk_profile_read": (_INT, [_P, ctypes.POINTER(mk_kernel_time), _INT, ctypes.POINTER(_INT)]),
+    "mk_launch_count": (_U64, [_P]),
+    "mk_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads ``libmeerkat.so``.  Raises if it has not been built: there is no
+    fallback implementation."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    "libmeerkat.so is missing at %s; build it with paper_2305_17813_gb300.build.build()" % p)
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(status: int, what: str) -> None:
+    if status != MK_OK:
+        raise MkError(status, what)

@@ -1,0 +1,211 @@
+// Device-side layout and warp helpers of the slab-hash graph store.
+//
+// Slab (paper, Sec. "Motivation"): 128 bytes = 32 lanes of 4 bytes, read by
+// one warp in one coalesced load.  Weighted (ConcurrentMap) layout: lane 2p
+// holds the destination key and lane 2p+1 its weight for p = 0..14, lane 30
+// is unused and lane 31 holds the index of the next slab (kNil at the tail).
+// A free pair is <EMPTY_KEY, 0xFFFFFFFF> (the 64-bit value UINT64_MAX - 1), a
+// deleted pair <TOMBSTONE_KEY, TOMBSTONE_KEY> (footnotes on EMPTY_KEY and
+// TOMBSTONE_KEY).  Deleted pairs are never reused, so free pairs only exist
+// in the last slab of a chain and an insert always lands at the chain's end.
+//
+// Slab indices are 32-bit: the head slabs of all lists occupy [0, H) of one
+// allocation and the overflow pool occupies [H, H + P) of the same one.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mk {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kNil = 0xFFFFFFFFu;        // null slab / INF distance / INVALID vertex
+constexpr uint32_t kEmptyKey = 0xFFFFFFFEu;
+constexpr uint32_t kTombKey = 0xFFFFFFFDu;
+constexpr unsigned long long kEmptyPair = 0xFFFFFFFFFFFFFFFEull;
+constexpr unsigned long long kTombPair = 0xFFFFFFFDFFFFFFFDull;
+constexpr unsigned long long kInfNode = 0xFFFFFFFFFFFFFFFFull; // <INF, INVALID>
+constexpr uint32_t kPairs = 15;
+constexpr uint32_t kNextLane = 31;
+constexpr uint8_t kInvalidLane = 0xFF;
+
+// Device status codes (mirror the public MK_ERR_* values).
+constexpr int kErrInvalid = -1;
+constexpr int kErrPool = -2;
+constexpr int kErrTimeout = -3;
+
+// Work counters (slabs loaded, edges examined, ...) accumulated by the
+// kernels with one atomicAdd per warp; they give the algorithmic byte counts
+// of the roofline figures.
+enum Counter {
+    kCtrQuerySlabs = 0,
+    kCtrInsertSlabs = 1,
+    kCtrInsertNewSlabs = 2,
+    kCtrDeleteSlabs = 3,
+    kCtrRelaxLists = 4,
+    kCtrRelaxSlabs = 5,
+    kCtrRelaxEdges = 6,
+    kCtrRelaxImproved = 7,
+    kCtrInvalidSlabs = 8,
+    kCtrWccSlabs = 9,
+    kCtrWccEdges = 10,
+    kCtrCommitSlabs = 11,
+    kNumCounters = 16
+};
+
+// Mutable device-side state of one graph (one allocation).
+struct DevState {
+    int status;            // sticky error word
+    uint32_t pool_hint;    // bitmap words below this index are known full
+    uint32_t dlog_count;   // entries in the delete log
+    uint32_t pad0;
+    unsigned long long ctr[kNumCounters];
+};
+
+// Read-only view of one graph passed to kernels by value.
+struct GView {
+    uint32_t V;
+    uint32_t H;            // slab lists (= head slabs)
+    uint32_t P;            // pool slabs
+    uint32_t pool_words;   // ceil(P / 32)
+    const uint2 *vinfo;    // per vertex: {first list, bucket count}
+    uint32_t *slabs;       // (H + P) * 32 words
+    uint32_t *bitmap;      // pool occupancy, 1 bit per pool slab
+    const uint32_t *list_src; // source vertex of each list
+    unsigned long long *lmark; // per list: marker slab << 32 | marker lane
+    uint8_t *lupd;         // per list: updated since the last commit
+    DevState *st;
+};
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
+__device__ __forceinline__ bool is_key_lane(uint32_t lane) { return lane < 30 && (lane & 1) == 0; }
+constexpr uint32_t kKeyLanes = 0x15555555u; // even lanes 0..28
+
+__device__ __forceinline__ uint32_t *slab_ptr(const GView &g, uint32_t s)
+{
+    return g.slabs + (size_t)s * 32;
+}
+
+// Position of the (r+1)-th set bit of m (r < popc(m)).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r)
+{
+    for (uint32_t i = 0; i < r; ++i)
+        m &= m - 1;
+    return __ffs(m) - 1;
+}
+
+// 32-bit integer hash "lowbias32" (C. Wellons, hash-prospector, 2018).
+__device__ __forceinline__ uint32_t hash32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Bucket of destination d among nb buckets: multiply-shift range reduction
+// of the hash (any hash works; it only changes the layout, never a result).
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t nb)
+{
+    return nb <= 1 ? 0u : (uint32_t)(((unsigned long long)hash32(d) * nb) >> 32);
+}
+
+__device__ __forceinline__ unsigned long long pack_pair(uint32_t key, uint32_t w)
+{
+    return ((unsigned long long)w << 32) | key;
+}
+
+__device__ __forceinline__ void set_status(DevState *st, int code)
+{
+    atomicCAS(&st->status, 0, code);
+}
+
+// Adds a per-warp count to a work counter (lane 0 only; v must be
+// warp-uniform).
+__device__ __forceinline__ void count_add(DevState *st, int which, unsigned long long v)
+{
+    if ((threadIdx.x & 31) == 0 && v)
+        atomicAdd(&st->ctr[which], v);
+}
+
+__device__ __forceinline__ int read_status(const DevState *st)
+{
+    return *((volatile const int *)&st->status);
+}
+
+// Warp-aggregated append of one element per participating lane into a
+// compact array: one atomicAdd per warp, each lane writes at base + rank
+// (paper, Algorithm "Warp device APIs: broadcast, and frontier enqueue").
+// Must be called by the full warp.  Returns false (and writes nothing) for a
+// lane whose slot would be at or beyond `cap`.
+template <typename T>
+__device__ __forceinline__ bool warp_enqueue(T *arr, uint32_t *count, uint32_t cap, T value, bool pred)
+{
+    const uint32_t mask = __ballot_sync(kFull, pred);
+    if (mask == 0)
+        return true;
+    uint32_t base = 0;
+    const uint32_t leader = __ffs(mask) - 1;
+    if (lane_id() == leader)
+        base = atomicAdd(count, (uint32_t)__popc(mask));
+    base = __shfl_sync(kFull, base, leader);
+    if (pred) {
+        const uint32_t at = base + __popc(mask & lanemask_lt());
+        if (at < cap) {
+            arr[at] = value;
+            return true;
+        }
+        return false;
+    }
+    return true;
+}
+
+// Warp-cooperative claim of one pool slab from the occupancy bitmap.  Lanes
+// probe 32 consecutive words at once starting at a per-warp offset above the
+// hint, and the lowest lane with a free bit claims it with atomicOr.  All 32
+// lanes must call; all receive the slab index (H + bit) or kNil when a full
+// sweep of the bitmap found nothing.
+__device__ __forceinline__ uint32_t alloc_slab(const GView &g, unsigned long long warp_gid)
+{
+    const uint32_t W = g.pool_words;
+    if (W == 0)
+        return kNil;
+    const uint32_t lane = lane_id();
+    const uint32_t hint = __ldcg(&g.st->pool_hint);
+    const uint32_t span = W < 4096u ? W : 4096u;
+    const uint64_t start = (uint64_t)hint + hash32((uint32_t)warp_gid ^ (uint32_t)(warp_gid >> 32)) % span;
+    const uint32_t sweeps = W / 32 + 2;
+    for (uint32_t it = 0; it < sweeps; ++it) {
+        const uint32_t wi = (uint32_t)((start + (uint64_t)it * 32 + lane) % W);
+        uint32_t word = __ldcg(&g.bitmap[wi]);
+        uint32_t cand = __ballot_sync(kFull, word != kFull);
+        while (cand) {
+            const uint32_t l = __ffs(cand) - 1;
+            uint32_t got = kNil;
+            if (lane == l) {
+                const uint32_t b = __ffs(~word) - 1;
+                const uint32_t old = atomicOr(&g.bitmap[wi], 1u << b);
+                if (!(old & (1u << b)))
+                    got = g.H + wi * 32 + b;
+                else
+                    word = old | (1u << b);
+            }
+            got = __shfl_sync(kFull, got, l);
+            if (got != kNil)
+                return got;
+            cand = __ballot_sync(kFull, word != kFull);
+        }
+    }
+    return kNil;
+}
+
+__device__ __forceinline__ void free_slab(const GView &g, uint32_t s)
+{
+    const uint32_t i = s - g.H;
+    atomicAnd(&g.bitmap[i >> 5], ~(1u << (i & 31)));
+}
+
+} // namespace mk

@@ -1,0 +1,140 @@
+// Host-side state of one graph and launch helpers shared by the CUDA
+// translation units of the library.
+#pragma once
+
+#include "meerkat.h"
+#include "mk_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace mk {
+
+enum ConsumerKind { kSssp = 0, kBfs = 1, kWcc = 2 };
+
+// State of one incremental algorithm on one graph.
+struct Consumer {
+    int kind = 0;
+    uint32_t source = 0;
+    uint64_t epoch = ~0ull;     // graph epoch whose change log this state has applied
+    uint64_t seq = ~0ull;       // graph change counter at the last update
+    unsigned long long *D = nullptr; // BFS/SSSP: V packed <distance, parent>
+    uint32_t *front[2] = {nullptr, nullptr}; // BFS/SSSP frontiers (V each)
+    uint32_t *stamp = nullptr;  // BFS/SSSP: round in which a vertex was last enqueued
+    uint32_t *inv = nullptr;    // BFS/SSSP: bitmap of vertices invalidated by this call's deletes
+    uint32_t round = 0;         // last stamp value used
+    uint32_t *uf = nullptr;     // WCC: union-find parents (V)
+    uint32_t *counters = nullptr; // device: frontier sizes etc. (16 words)
+};
+
+struct TimedLaunch {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+// Sorting / scanning helpers (sort.cu, CUB radix sort compiled in-tree).
+cudaError_t sort_pairs_u64_u32(void *tmp, size_t &tmp_bytes, const uint64_t *kin, uint64_t *kout,
+                               const uint32_t *vin, uint32_t *vout, uint64_t n, int end_bit,
+                               cudaStream_t s);
+cudaError_t exclusive_sum_u32_u64(void *tmp, size_t &tmp_bytes, const uint32_t *in, uint64_t *out,
+                                  uint64_t n, cudaStream_t s);
+// Kernel launches made by one call of the helpers above (CUB's plan for
+// these sizes), for the launch counter.
+int sort_pairs_launches(uint64_t n, int end_bit);
+int exclusive_sum_launches(uint64_t n);
+
+} // namespace mk
+
+struct mk_graph {
+    mk::GView v{};               // device pointers + sizes
+    uint32_t vbits = 1;          // bits of a vertex id in a sort key
+    mk::DevState *d_state = nullptr;
+    uint64_t bytes = 0;          // device bytes held
+    // staging scratch, grown on demand
+    uint64_t scratch_cap = 0;
+    uint64_t *d_kin = nullptr, *d_kout = nullptr;
+    uint32_t *d_iin = nullptr, *d_iout = nullptr;
+    void *d_tmp = nullptr;
+    size_t tmp_bytes = 0;
+    // change log of the current epoch: deleted (src << 32 | dst)
+    unsigned long long *d_dlog = nullptr;
+    uint64_t dlog_cap = 0, dlog_bound = 0;
+    uint64_t epoch = 0, change_seq = 0;
+    bool epoch_has_deletes = false;
+    std::map<std::pair<int, uint32_t>, mk::Consumer *> consumers;
+    cudaStream_t last_stream = nullptr;
+    uint32_t *h_pinned = nullptr; // 16 pinned words for small device->host reads
+    // profiling
+    bool prof = false;
+    std::vector<mk::TimedLaunch> timed;
+    std::vector<cudaEvent_t> spare_events;
+    uint64_t launches = 0;
+};
+
+namespace mk {
+
+#define MK_CUDA(call)                                                                                              \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess)                                                                                     \
+            return e_ == cudaErrorMemoryAllocation ? MK_ERR_NO_MEMORY : MK_ERR_CUDA;                               \
+    } while (0)
+
+#define MK_TRY(call)                                                                                               \
+    do {                                                                                                           \
+        mk_status s_ = (call);                                                                                     \
+        if (s_ != MK_OK)                                                                                           \
+            return s_;                                                                                             \
+    } while (0)
+
+inline cudaEvent_t take_event(mk_graph *g)
+{
+    if (!g->spare_events.empty()) {
+        cudaEvent_t e = g->spare_events.back();
+        g->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Runs `launch` (which enqueues `count` kernels on s), counts the launches
+// and, when profiling is on, brackets them with events on s.
+template <typename F>
+inline mk_status timed(mk_graph *g, const char *name, cudaStream_t s, int count, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (g->prof) {
+        a = take_event(g);
+        cudaEventRecord(a, s);
+    }
+    cudaError_t e = launch();
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    g->launches += (uint64_t)count;
+    if (g->prof) {
+        b = take_event(g);
+        cudaEventRecord(b, s);
+        g->timed.push_back({name, a, b});
+    }
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? MK_ERR_NO_MEMORY : MK_ERR_CUDA;
+    return MK_OK;
+}
+
+inline uint32_t grid_for(uint64_t threads, uint32_t block)
+{
+    uint64_t b = (threads + block - 1) / block;
+    return (uint32_t)(b == 0 ? 1 : b);
+}
+
+mk_status ensure_scratch(mk_graph *g, uint64_t n, cudaStream_t s);
+mk_status device_alloc(mk_graph *g, void **p, size_t bytes);
+void device_free(mk_graph *g, void *p, size_t bytes);
+
+} // namespace mk

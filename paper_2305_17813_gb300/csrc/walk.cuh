@@ -1,0 +1,103 @@
+// Slab-list traversal and frontier helpers shared by the algorithm kernels.
+#pragma once
+
+#include "mk_device.cuh"
+
+namespace mk {
+
+// Walks one slab list with the whole warp, one 128-byte slab per step, and
+// calls f(key, weight, live) on every lane for every slab: `key` is the
+// lane's word, `weight` the word of the next lane, `live` true on key lanes
+// holding a valid vertex (neither EMPTY nor TOMBSTONE).  On the first slab
+// only lanes >= first_lane count (the UpdateIterator skips the entries that
+// were already there at the last commit).  Stops after the slab whose next
+// lane is null or after max_hops slabs; returns the number of slabs read.
+template <typename F>
+__device__ __forceinline__ uint32_t walk_list(const GView &g, uint32_t slab, uint32_t first_lane, uint32_t max_hops,
+                                              F &&f)
+{
+    const uint32_t lane = lane_id();
+    uint32_t hop = 0;
+    for (; slab != kNil && hop < max_hops; ++hop) {
+        const uint32_t v = __ldcg(slab_ptr(g, slab) + lane);
+        const uint32_t wt = __shfl_down_sync(kFull, v, 1);
+        const bool live = is_key_lane(lane) && v < kTombKey && lane >= first_lane;
+        f(v, wt, live);
+        slab = __shfl_sync(kFull, v, kNextLane);
+        first_lane = 0;
+    }
+    return hop;
+}
+
+// Start of the UpdateIterator of list L: the marker slab and lane, or the
+// slab after a full marker slab.  Returns kNil when nothing follows.
+__device__ __forceinline__ uint32_t update_begin(const GView &g, uint32_t L, uint32_t *first_lane)
+{
+    const unsigned long long m = g.lmark[L];
+    const uint32_t slab = (uint32_t)(m >> 32);
+    const uint32_t lane = (uint32_t)(m & 0xFF);
+    if (lane == kInvalidLane) {
+        *first_lane = 0;
+        return __ldcg(slab_ptr(g, slab) + kNextLane);
+    }
+    *first_lane = lane;
+    return slab;
+}
+
+// Appends the slab lists of vertex y (for every lane with pred) to the list
+// frontier `out`: lanes with few buckets write their own ids after one
+// warp-aggregated atomicAdd; a vertex with many buckets is written by the
+// whole warp.  Must be called by the full warp.  Sets *overflow on a lane
+// whose entries would not fit in `cap`.
+__device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool pred, uint32_t *out, uint32_t *count,
+                                              uint32_t cap, int *overflow)
+{
+    constexpr uint32_t kSmall = 8;
+    const uint32_t lane = lane_id();
+    uint2 vi = make_uint2(0, 0);
+    if (pred)
+        vi = g.vinfo[y];
+    const bool small = pred && vi.y <= kSmall;
+    // small vertices: exclusive scan of bucket counts across the warp
+    uint32_t c = small ? vi.y : 0, incl = c;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o)
+            incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total) {
+        uint32_t base = 0;
+        if (lane == 0)
+            base = atomicAdd(count, total);
+        base = __shfl_sync(kFull, base, 0);
+        const uint32_t at = base + incl - c;
+        for (uint32_t k = 0; k < c; ++k) {
+            if (at + k < cap)
+                out[at + k] = vi.x + k;
+            else
+                *overflow = 1;
+        }
+    }
+    // large vertices: one at a time, written by the whole warp
+    uint32_t big = __ballot_sync(kFull, pred && !small);
+    while (big) {
+        const uint32_t l = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t first = __shfl_sync(kFull, vi.x, l);
+        const uint32_t nb = __shfl_sync(kFull, vi.y, l);
+        uint32_t base = 0;
+        if (lane == 0)
+            base = atomicAdd(count, nb);
+        base = __shfl_sync(kFull, base, 0);
+        for (uint32_t k = lane; k < nb; k += 32) {
+            if (base + k < cap)
+                out[base + k] = first + k;
+            else
+                *overflow = 1;
+        }
+    }
+}
+
+} // namespace mk

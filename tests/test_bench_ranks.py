@@ -1,0 +1,68 @@
+"""The benchmark's multi-rank bookkeeping on CPU (gloo, world size 2):
+the step time is the maximum over ranks and the throughput counts the
+units of every rank (independent replicas, weak scaling)."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    w, r, _ = bench.dist_env()
+    assert (w, r) == (world, rank)
+    d = bench.dist_init(world, use_cuda=False)
+    bench.barrier(d)
+    local_ms = [10.0, 25.0][rank]
+    ms, = bench.reduce_across([local_ms], "max", d, "cpu")
+    units, = bench.reduce_across([3.0 * (1 << 20)], "sum", d, "cpu")
+    out.put((rank, ms, units))
+    d.destroy_process_group()
+
+
+def test_two_rank_aggregation_with_gloo():
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, units in res:
+        assert ms == 25.0
+        assert units == 2 * 3.0 * (1 << 20)
+
+
+def test_single_rank_is_identity():
+    import bench
+
+    assert bench.reduce_across([1.5, 2.0], "max", None, "cpu") == [1.5, 2.0]
+    assert bench.dist_init(1, use_cuda=False) is None
+
+
+def test_algorithmic_bytes_model():
+    import bench
+
+    ctr = {"query_slabs": 1000, "insert_slabs": 10, "insert_new_slabs": 2, "delete_slabs": 5, "relax_lists": 3,
+           "relax_slabs": 4, "relax_edges": 50, "relax_improved": 7, "wcc_slabs": 9, "wcc_edges": 100}
+    assert bench.algorithmic_bytes("query", ctr, 800, 1) == pytest.approx(800 * 40.125 + 128000)
+    assert bench.algorithmic_bytes("insert", ctr, 10, 2) == 2 * 10 * 76 + 128 * 12
+    assert bench.algorithmic_bytes("unknown", ctr, 1, 1) is None
