@@ -56,7 +56,7 @@ enum Counter {
 // Mutable device-side state of one graph (one allocation).
 struct DevState {
     int status;            // sticky error word
-    uint32_t pool_hint;    // bitmap words below this index are known full
+    uint32_t reserved;
     uint32_t dlog_count;   // entries in the delete log
     uint32_t pad0;
     unsigned long long ctr[kNumCounters];
@@ -163,20 +163,20 @@ __device__ __forceinline__ bool warp_enqueue(T *arr, uint32_t *count, uint32_t c
     return true;
 }
 
-// Warp-cooperative claim of one pool slab from the occupancy bitmap.  Lanes
-// probe 32 consecutive words at once starting at a per-warp offset above the
-// hint, and the lowest lane with a free bit claims it with atomicOr.  All 32
-// lanes must call; all receive the slab index (H + bit) or kNil when a full
-// sweep of the bitmap found nothing.
-__device__ __forceinline__ uint32_t alloc_slab(const GView &g, unsigned long long warp_gid)
+// Warp-cooperative claim of one pool slab from the occupancy bitmap.  The
+// warp probes 32 consecutive words at once, starting at a word chosen by
+// hashing `salt` uniformly over the whole pool (so concurrent claims land on
+// different words and a probe finds a free bit at once unless the pool is
+// nearly full), and the lowest lane that sees a free bit claims it with
+// atomicOr.  All 32 lanes must call; all receive the slab index (H + bit),
+// or kNil when a sweep over the whole bitmap found nothing.
+__device__ __forceinline__ uint32_t alloc_slab(const GView &g, uint32_t salt)
 {
     const uint32_t W = g.pool_words;
     if (W == 0)
         return kNil;
     const uint32_t lane = lane_id();
-    const uint32_t hint = __ldcg(&g.st->pool_hint);
-    const uint32_t span = W < 4096u ? W : 4096u;
-    const uint64_t start = (uint64_t)hint + hash32((uint32_t)warp_gid ^ (uint32_t)(warp_gid >> 32)) % span;
+    const uint64_t start = (uint64_t)hash32(salt) % W;
     const uint32_t sweeps = W / 32 + 2;
     for (uint32_t it = 0; it < sweeps; ++it) {
         const uint32_t wi = (uint32_t)((start + (uint64_t)it * 32 + lane) % W);

@@ -16,10 +16,16 @@
 // invalidation then spreads down the tree through the children of every
 // invalidated vertex (a top-down traversal of the affected subtrees instead
 // of the paper's per-vertex walk up to the source, so the cost follows the
-// invalidated region); then every edge from a valid vertex into an invalid
-// one is relaxed.  Incremental prologue: the edges inserted since the last
-// commit, read with the UpdateIterator, are relaxed.  Common epilogue: rounds
-// until no distance improves.
+// invalidated region); then every edge from a valid vertex into an
+// invalidated one is relaxed.  Incremental prologue: the edges inserted since
+// the last commit, read with the UpdateIterator, are relaxed.  Common
+// epilogue: rounds until no distance improves.
+//
+// The round loops run on the device: one persistent cooperative kernel
+// executes all rounds of a phase and separates them with a grid barrier whose
+// waits are bounded, so the host never reads a frontier size (the paper's
+// host loop reads it every round).  If the cooperative launch is refused, the
+// same round body runs as one launch per round driven by the host.
 #include "mk_host.h"
 #include "walk.cuh"
 
@@ -30,6 +36,18 @@ using namespace mk;
 namespace {
 
 constexpr uint32_t kInf32 = 0xFFFFFFFFu;
+constexpr uint32_t kBarrierSpins = 1u << 24;
+
+// consumer counter words
+enum {
+    kCnt0 = 0,        // kCnt0..kCnt0+2: rotating frontier sizes
+    kOverflow = 3,
+    kInvTotal = 4,
+    kRoundsDone = 5,
+    kClearWords = 8,  // words [0, 8) are cleared at the start of every call
+    kRid = 8,         // last round stamp used (kept across calls)
+    kBar = 10         // grid barrier: arrival count, generation
+};
 
 __device__ __forceinline__ uint32_t node_dist(unsigned long long d) { return (uint32_t)(d >> 32); }
 __device__ __forceinline__ uint32_t node_parent(unsigned long long d) { return (uint32_t)d; }
@@ -52,7 +70,191 @@ __device__ __forceinline__ bool first_this_round(uint32_t *stamp, uint32_t y, ui
     return atomicExch(&stamp[y], round) != round;
 }
 
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *(volatile const uint32_t *)p; }
+
 } // namespace
+
+// Arguments of the round loops (one struct so the cooperative launch passes
+// a single pointer).
+struct RoundArgs {
+    GView g;
+    unsigned long long *D;
+    uint32_t *front[2];
+    uint32_t *ctr;        // consumer counter words
+    uint32_t *stamp;
+    uint32_t *inv;
+    uint32_t cap;
+    uint32_t max_hops;
+    uint32_t max_rounds;
+    uint32_t source;
+    int unit;
+    int mode;             // 0 = relax rounds, 1 = invalidation rounds
+};
+
+namespace {
+
+// One round over frontier F[0, n): warps stride over groups of 32 lists.
+__device__ void relax_body(const RoundArgs &a, const uint32_t *F, uint32_t n, uint32_t *Fn, uint32_t *cnt,
+                           uint32_t round, uint64_t warp0, uint64_t nwarps)
+{
+    const GView &g = a.g;
+    const uint32_t lane = lane_id();
+    int *overflow = (int *)(a.ctr + kOverflow);
+    unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
+    for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+        const uint64_t i = base + lane;
+        bool todo = i < n;
+        const uint32_t mine = todo ? F[i] : 0;
+        uint32_t q;
+        while ((q = __ballot_sync(kFull, todo)) != 0) {
+            const uint32_t leader = __ffs(q) - 1;
+            if (lane == leader)
+                todo = false;
+            const uint32_t L = __shfl_sync(kFull, mine, leader);
+            const uint32_t x = g.list_src[L];
+            const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&a.D[x])), 0);
+            ++lists;
+            if (dx == kInf32)
+                continue;
+            slabs += walk_list(g, L, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
+                edges += __popc(__ballot_sync(kFull, live));
+                bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
+                up = up && first_this_round(a.stamp, y, round);
+                improved += __popc(__ballot_sync(kFull, up));
+                enqueue_lists(g, y, up, Fn, cnt, a.cap, overflow);
+            });
+        }
+    }
+    count_add(g.st, kCtrRelaxLists, lists);
+    count_add(g.st, kCtrRelaxSlabs, slabs);
+    count_add(g.st, kCtrRelaxEdges, edges);
+    count_add(g.st, kCtrRelaxImproved, improved);
+}
+
+// One round of invalidation: the tree children of the invalidated vertices
+// whose lists are in F become invalid too.
+__device__ void invalidate_body(const RoundArgs &a, const uint32_t *F, uint32_t n, uint32_t *Fn, uint32_t *cnt,
+                                uint64_t warp0, uint64_t nwarps)
+{
+    const GView &g = a.g;
+    const uint32_t lane = lane_id();
+    int *overflow = (int *)(a.ctr + kOverflow);
+    uint32_t *total = a.ctr + kInvTotal;
+    unsigned long long slabs = 0;
+    for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+        const uint64_t i = base + lane;
+        bool todo = i < n;
+        const uint32_t mine = todo ? F[i] : 0;
+        uint32_t q;
+        while ((q = __ballot_sync(kFull, todo)) != 0) {
+            const uint32_t leader = __ffs(q) - 1;
+            if (lane == leader)
+                todo = false;
+            const uint32_t L = __shfl_sync(kFull, mine, leader);
+            const uint32_t x = g.list_src[L];
+            slabs += walk_list(g, L, 0, a.max_hops, [&](uint32_t y, uint32_t, bool live) {
+                bool hit = false;
+                if (live && y != a.source) {
+                    const unsigned long long dy = __ldcg(&a.D[y]);
+                    if (dy != kInfNode && node_parent(dy) == x)
+                        hit = atomicCAS(&a.D[y], dy, kInfNode) == dy;
+                }
+                if (hit) {
+                    atomicAdd(total, 1u);
+                    atomicOr(&a.inv[y >> 5], 1u << (y & 31));
+                }
+                enqueue_lists(g, y, hit, Fn, cnt, a.cap, overflow);
+            });
+        }
+    }
+    count_add(g.st, kCtrInvalidSlabs, slabs);
+}
+
+// Round r of a phase: reads the size in ctr[kCnt0 + r % 3], appends to
+// ctr[kCnt0 + (r+1) % 3] and clears ctr[kCnt0 + (r+2) % 3] for round r+1.
+// Frontier r is front[r & 1].
+__device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t r, uint32_t n, uint64_t warp0, uint64_t nwarps,
+                                           uint32_t rid)
+{
+    const uint32_t in = r & 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        a.ctr[kCnt0 + (r + 2) % 3] = 0;
+    uint32_t *cnt = a.ctr + kCnt0 + (r + 1) % 3;
+    if (a.mode == 0)
+        relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps);
+    else
+        invalidate_body(a, a.front[in], n, a.front[in ^ 1], cnt, warp0, nwarps);
+}
+
+// Bounded sense-counting grid barrier for a co-resident (cooperative) grid.
+// Returns false when a wait gave up.
+__device__ bool grid_barrier(uint32_t *bar)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *gen = bar + 1;
+        const uint32_t g0 = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            uint32_t spins = 0;
+            while (*gen == g0) {
+                if (++spins > kBarrierSpins) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+} // namespace
+
+// All rounds of one phase in one cooperative launch.  The phase input is
+// front[0] with its size in ctr[kCnt0]; ctr[kCnt0 + 1] must be zero.
+__global__ void __launch_bounds__(256) k_rounds(RoundArgs a)
+{
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t rid = ld_volatile(a.ctr + kRid);
+    uint32_t r = 0;
+    bool ok = true;
+    for (; r < a.max_rounds; ++r) {
+        const uint32_t n = ld_volatile(a.ctr + kCnt0 + r % 3);
+        if (n == 0)
+            break;
+        round_step(a, r, n, warp0, nwarps, rid);
+        if (!grid_barrier(a.ctr + kBar)) {
+            ok = false;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctr[kRoundsDone] = r;
+        if (!ok || r >= a.max_rounds)
+            set_status(a.g.st, kErrTimeout);
+    }
+}
+
+// One round, for the host-driven fallback.
+__global__ void __launch_bounds__(256) k_round_once(RoundArgs a, uint32_t r, uint32_t n)
+{
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    round_step(a, r, n, warp0, nwarps, ld_volatile(a.ctr + kRid));
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        a.ctr[kRoundsDone] = r + 1;
+}
 
 __global__ void k_sssp_init(unsigned long long *D, uint32_t V, uint32_t source, uint32_t *front, uint32_t *count,
                             const uint2 *vinfo)
@@ -68,49 +270,8 @@ __global__ void k_sssp_init(unsigned long long *D, uint32_t V, uint32_t source, 
     }
 }
 
-// One round of the epilogue: warp per 32 frontier lists.
-__global__ void __launch_bounds__(256) k_relax_round(GView g, unsigned long long *D, const uint32_t *__restrict__ F,
-                                                     uint32_t n, uint32_t *Fn, uint32_t *cnt, uint32_t cap,
-                                                     uint32_t *stamp, uint32_t round, int unit, uint32_t max_hops,
-                                                     int *overflow)
-{
-    const uint32_t lane = lane_id();
-    const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
-    if (base >= n)
-        return;
-    const uint64_t i = base + lane;
-    bool todo = i < n;
-    const uint32_t mine = todo ? F[i] : 0;
-    unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
-    uint32_t q;
-    while ((q = __ballot_sync(kFull, todo)) != 0) {
-        const uint32_t leader = __ffs(q) - 1;
-        if (lane == leader)
-            todo = false;
-        const uint32_t L = __shfl_sync(kFull, mine, leader);
-        const uint32_t x = g.list_src[L];
-        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&D[x])), 0);
-        ++lists;
-        if (dx == kInf32)
-            continue;
-        slabs += walk_list(g, L, 0, max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            edges += __popc(__ballot_sync(kFull, live));
-            bool up = live && relax(D, x, dx, y, unit ? 1u : w);
-            up = up && first_this_round(stamp, y, round);
-            improved += __popc(__ballot_sync(kFull, up));
-            enqueue_lists(g, y, up, Fn, cnt, cap, overflow);
-        });
-    }
-    count_add(g.st, kCtrRelaxLists, lists);
-    count_add(g.st, kCtrRelaxSlabs, slabs);
-    count_add(g.st, kCtrRelaxEdges, edges);
-    count_add(g.st, kCtrRelaxImproved, improved);
-}
-
 // Decremental seeds: a deleted edge (u, v) that is v's tree edge invalidates v.
-__global__ void k_invalidate(const unsigned long long *dlog, const DevState *st, unsigned long long *D, uint32_t source,
-                             GView g, uint32_t *Fn, uint32_t *cnt, uint32_t cap, int *overflow, uint32_t *total,
-                             uint32_t *inv)
+__global__ void k_invalidate(const unsigned long long *dlog, const DevState *st, RoundArgs a)
 {
     const uint32_t n = st->dlog_count;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,74 +284,40 @@ __global__ void k_invalidate(const unsigned long long *dlog, const DevState *st,
         const unsigned long long e = dlog[i];
         const uint32_t u = (uint32_t)(e >> 32);
         v = (uint32_t)e;
-        const unsigned long long dv = __ldcg(&D[v]);
-        if (v != source && dv != kInfNode && node_parent(dv) == u)
-            hit = atomicCAS(&D[v], dv, kInfNode) == dv;
+        const unsigned long long dv = __ldcg(&a.D[v]);
+        if (v != a.source && dv != kInfNode && node_parent(dv) == u)
+            hit = atomicCAS(&a.D[v], dv, kInfNode) == dv;
     }
     if (hit) {
-        atomicAdd(total, 1u);
-        atomicOr(&inv[v >> 5], 1u << (v & 31));
+        atomicAdd(a.ctr + kInvTotal, 1u);
+        atomicOr(&a.inv[v >> 5], 1u << (v & 31));
     }
-    enqueue_lists(g, v, hit, Fn, cnt, cap, overflow);
-}
-
-// Spreads invalidation to the tree children of invalidated vertices.
-__global__ void __launch_bounds__(256) k_invalidate_round(GView g, unsigned long long *D, const uint32_t *__restrict__ F,
-                                                          uint32_t n, uint32_t *Fn, uint32_t *cnt, uint32_t cap,
-                                                          uint32_t source, uint32_t max_hops, int *overflow,
-                                                          uint32_t *total, uint32_t *inv)
-{
-    const uint32_t lane = lane_id();
-    const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
-    if (base >= n)
-        return;
-    const uint64_t i = base + lane;
-    bool todo = i < n;
-    const uint32_t mine = todo ? F[i] : 0;
-    unsigned long long slabs = 0;
-    uint32_t q;
-    while ((q = __ballot_sync(kFull, todo)) != 0) {
-        const uint32_t leader = __ffs(q) - 1;
-        if (lane == leader)
-            todo = false;
-        const uint32_t L = __shfl_sync(kFull, mine, leader);
-        const uint32_t x = g.list_src[L];
-        slabs += walk_list(g, L, 0, max_hops, [&](uint32_t y, uint32_t, bool live) {
-            bool hit = false;
-            if (live && y != source) {
-                const unsigned long long dy = __ldcg(&D[y]);
-                if (dy != kInfNode && node_parent(dy) == x)
-                    hit = atomicCAS(&D[y], dy, kInfNode) == dy;
-            }
-            if (hit) {
-                atomicAdd(total, 1u);
-                atomicOr(&inv[y >> 5], 1u << (y & 31));
-            }
-            enqueue_lists(g, y, hit, Fn, cnt, cap, overflow);
-        });
-    }
-    count_add(g.st, kCtrInvalidSlabs, slabs);
+    enqueue_lists(a.g, v, hit, a.front[0], a.ctr + kCnt0, a.cap, (int *)(a.ctr + kOverflow));
 }
 
 // After invalidation: relax every edge out of a valid vertex into a vertex
 // invalidated by this call (warp per 32 lists over all lists).  The target
 // test reads the invalidation bitmap, which stays fixed during the pass, so
 // every such edge is relaxed even after another in-neighbour has already
-// given its target a finite distance.
-__global__ void __launch_bounds__(256) k_relax_into_invalid(GView g, unsigned long long *D, uint32_t *Fn, uint32_t *cnt,
-                                                            uint32_t cap, uint32_t *stamp, uint32_t round, int unit,
-                                                            uint32_t max_hops, int *overflow, const uint32_t *inv)
+// given its target a finite distance.  Does nothing if nothing was
+// invalidated.
+__global__ void __launch_bounds__(256) k_relax_into_invalid(RoundArgs a)
 {
+    const GView &g = a.g;
+    if (ld_volatile(a.ctr + kInvTotal) == 0)
+        return;
     const uint32_t lane = lane_id();
     const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
     if (base >= g.H)
         return;
+    const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
+    int *overflow = (int *)(a.ctr + kOverflow);
     const uint64_t l = base + lane;
     bool todo = false;
     uint32_t x = 0;
     if (l < g.H) {
         x = g.list_src[l];
-        todo = node_dist(__ldcg(&D[x])) != kInf32;
+        todo = node_dist(__ldcg(&a.D[x])) != kInf32;
     }
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
     uint32_t q;
@@ -200,15 +327,15 @@ __global__ void __launch_bounds__(256) k_relax_into_invalid(GView g, unsigned lo
             todo = false;
         const uint32_t L = (uint32_t)(base + leader);
         const uint32_t src = __shfl_sync(kFull, x, leader);
-        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&D[src])), 0);
+        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&a.D[src])), 0);
         ++lists;
-        slabs += walk_list(g, L, 0, max_hops, [&](uint32_t y, uint32_t w, bool live) {
+        slabs += walk_list(g, L, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
             edges += __popc(__ballot_sync(kFull, live));
-            const bool target = live && ((inv[y >> 5] >> (y & 31)) & 1u);
-            bool up = target && relax(D, src, dx, y, unit ? 1u : w);
-            up = up && first_this_round(stamp, y, round);
+            const bool target = live && ((a.inv[y >> 5] >> (y & 31)) & 1u);
+            bool up = target && relax(a.D, src, dx, y, a.unit ? 1u : w);
+            up = up && first_this_round(a.stamp, y, round);
             improved += __popc(__ballot_sync(kFull, up));
-            enqueue_lists(g, y, up, Fn, cnt, cap, overflow);
+            enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
         });
     }
     count_add(g.st, kCtrRelaxLists, lists);
@@ -219,14 +346,15 @@ __global__ void __launch_bounds__(256) k_relax_into_invalid(GView g, unsigned lo
 
 // Incremental seeds: relax the entries inserted since the last commit
 // (UpdateIterator over the lists flagged as updated).
-__global__ void __launch_bounds__(256) k_relax_updated(GView g, unsigned long long *D, uint32_t *Fn, uint32_t *cnt,
-                                                       uint32_t cap, uint32_t *stamp, uint32_t round, int unit,
-                                                       uint32_t max_hops, int *overflow)
+__global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
 {
+    const GView &g = a.g;
     const uint32_t lane = lane_id();
     const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
     if (base >= g.H)
         return;
+    const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
+    int *overflow = (int *)(a.ctr + kOverflow);
     const uint64_t l = base + lane;
     bool todo = l < g.H && g.lupd[l];
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
@@ -237,24 +365,33 @@ __global__ void __launch_bounds__(256) k_relax_updated(GView g, unsigned long lo
             todo = false;
         const uint32_t L = (uint32_t)(base + leader);
         const uint32_t src = g.list_src[L];
-        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&D[src])), 0);
+        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&a.D[src])), 0);
         if (dx == kInf32)
             continue;
         uint32_t first_lane = 0;
         const uint32_t start = update_begin(g, L, &first_lane);
         ++lists;
-        slabs += walk_list(g, start, first_lane, max_hops, [&](uint32_t y, uint32_t w, bool live) {
+        slabs += walk_list(g, start, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
             edges += __popc(__ballot_sync(kFull, live));
-            bool up = live && relax(D, src, dx, y, unit ? 1u : w);
-            up = up && first_this_round(stamp, y, round);
+            bool up = live && relax(a.D, src, dx, y, a.unit ? 1u : w);
+            up = up && first_this_round(a.stamp, y, round);
             improved += __popc(__ballot_sync(kFull, up));
-            enqueue_lists(g, y, up, Fn, cnt, cap, overflow);
+            enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
         });
     }
     count_add(g.st, kCtrRelaxLists, lists);
     count_add(g.st, kCtrRelaxSlabs, slabs);
     count_add(g.st, kCtrRelaxEdges, edges);
     count_add(g.st, kCtrRelaxImproved, improved);
+}
+
+// Ends a call: advances the round stamp past every id used, reports an
+// overflowed frontier.
+__global__ void k_sssp_finish(uint32_t *ctr, DevState *st)
+{
+    ctr[kRid] += ctr[kRoundsDone] + 2;
+    if (ctr[kOverflow])
+        set_status(st, kErrTimeout);
 }
 
 __global__ void k_unpack(const unsigned long long *D, uint32_t V, uint32_t *dist, uint32_t *parent)
@@ -269,18 +406,9 @@ __global__ void k_unpack(const unsigned long long *D, uint32_t V, uint32_t *dist
         parent[v] = node_parent(d);
 }
 
-__global__ void k_flag_overflow(const int *overflow, DevState *st)
-{
-    if (*overflow)
-        set_status(st, kErrTimeout);
-}
-
 // ---------------------------------------------------------------- host side
 
 namespace {
-
-// counters layout (device words)
-enum { kCntA = 0, kCntB = 1, kInvTotal = 2, kOverflow = 3 };
 
 mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
 {
@@ -322,33 +450,46 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
     return MK_OK;
 }
 
-mk_status read_word(mk_graph *g, const uint32_t *d_word, uint32_t *out, cudaStream_t s)
+// Co-resident grid of k_rounds (blocks per SM x SMs), computed once.
+int rounds_grid()
 {
-    MK_CUDA(cudaMemcpyAsync(g->h_pinned, d_word, 4, cudaMemcpyDeviceToHost, s));
-    MK_CUDA(cudaStreamSynchronize(s));
-    *out = g->h_pinned[0];
-    return MK_OK;
+    static int grid = -1;
+    if (grid < 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rounds, 256, 0);
+        grid = std::max(1, sms * std::max(per_sm, 1));
+    }
+    return grid;
 }
 
-// Runs rounds of `kernel_launch(cur, n, next)` until the frontier is empty.
-// The frontier in front[*cur] holds `n` lists; returns with n == 0.
-template <typename Launch>
-mk_status run_rounds(mk_graph *g, Consumer *c, int *cur, uint32_t n, cudaStream_t s, const char *name,
-                     Launch &&launch)
+// Runs every round of one phase.  Input: front[0], size in ctr[kCnt0],
+// ctr[kCnt0 + 1] zero.
+mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
 {
-    const uint64_t limit = (uint64_t)g->v.V + 2;
-    for (uint64_t r = 0; n != 0; ++r) {
-        if (r > limit) {
-            mk_status st = MK_ERR_TIMEOUT;
-            return st;
-        }
-        const int nxt = *cur ^ 1;
-        MK_CUDA(cudaMemsetAsync(c->counters + nxt, 0, 4, s));
-        MK_TRY(timed(g, name, s, 1, [&]() { return launch(*cur, n, nxt); }));
-        MK_TRY(read_word(g, c->counters + nxt, &n, s));
-        *cur = nxt;
+    const int grid = rounds_grid();
+    void *args[] = {&a};
+    mk_status st = timed(g, name, s, 1, [&]() {
+        return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(256), args, 0, s);
+    });
+    if (st == MK_OK)
+        return MK_OK;
+    cudaGetLastError();
+    // fallback: one launch per round, the host reads each size
+    for (uint32_t r = 0;; ++r) {
+        if (r > a.max_rounds)
+            return MK_ERR_TIMEOUT;
+        MK_CUDA(cudaMemcpyAsync(g->h_pinned, a.ctr + kCnt0 + r % 3, 4, cudaMemcpyDeviceToHost, s));
+        MK_CUDA(cudaStreamSynchronize(s));
+        const uint32_t n = g->h_pinned[0];
+        if (n == 0)
+            return MK_OK;
+        MK_TRY(timed(g, name, s, 1, [&]() {
+            k_round_once<<<grid_for((uint64_t)n, 256), 256, 0, s>>>(a, r, n);
+            return cudaSuccess;
+        }));
     }
-    return MK_OK;
 }
 
 mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, cudaStream_t s)
@@ -358,75 +499,59 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     g->last_stream = s;
     Consumer *c = nullptr;
     MK_TRY(get_consumer(g, kind, source, &c));
-    const int unit = kind == kBfs ? 1 : 0;
-    const uint32_t V = g->v.V, H = g->v.H, cap = H;
-    const uint32_t max_hops = g->v.P + 2;
-    int *overflow = (int *)(c->counters + kOverflow);
-    int cur = 0;
-    uint32_t n = 0;
+    const uint32_t V = g->v.V, H = g->v.H;
+    RoundArgs a{};
+    a.g = g->v;
+    a.D = c->D;
+    a.front[0] = c->front[0];
+    a.front[1] = c->front[1];
+    a.ctr = c->counters;
+    a.stamp = c->stamp;
+    a.inv = c->inv;
+    a.cap = H;
+    a.max_hops = g->v.P + 2;
+    a.max_rounds = V + 2;
+    a.source = source;
+    a.unit = kind == kBfs ? 1 : 0;
     const bool incremental = c->epoch == g->epoch;
-    MK_CUDA(cudaMemsetAsync(c->counters, 0, 64, s));
-    auto relax_launch = [&](int a, uint32_t na, int b) {
-        k_relax_round<<<grid_for((uint64_t)na, 256), 256, 0, s>>>(g->v, c->D, c->front[a], na, c->front[b],
-                                                                  c->counters + b, cap, c->stamp, ++c->round, unit,
-                                                                  max_hops, overflow);
-        return cudaSuccess;
-    };
+    MK_CUDA(cudaMemsetAsync(c->counters, 0, kClearWords * 4, s));
+    MK_CUDA(cudaMemsetAsync(c->counters + kBar, 0, 8, s));
     if (!incremental) {
         MK_TRY(timed(g, "sssp_init", s, 1, [&]() {
-            k_sssp_init<<<grid_for(V, 256), 256, 0, s>>>(c->D, V, source, c->front[0], c->counters + 0, g->v.vinfo);
+            k_sssp_init<<<grid_for(V, 256), 256, 0, s>>>(c->D, V, source, c->front[0], c->counters + kCnt0,
+                                                         g->v.vinfo);
             return cudaSuccess;
         }));
-        MK_TRY(read_word(g, c->counters + 0, &n, s));
     } else {
-        // both prologues seed the first epilogue frontier under one round stamp
-        const uint32_t seeds_round = ++c->round;
         if (g->epoch_has_deletes) {
-            // decremental prologue: invalidate, spread down the tree
-            MK_CUDA(cudaMemsetAsync(c->counters, 0, 16, s));
+            // decremental prologue: invalidate, spread down the tree, then
+            // relax the edges from valid into invalidated vertices
             MK_CUDA(cudaMemsetAsync(c->inv, 0, (size_t)(V + 31) / 32 * 4, s));
             MK_TRY(timed(g, "sssp_invalidate", s, 1, [&]() {
-                k_invalidate<<<grid_for(std::max<uint64_t>(g->dlog_bound, 1), 256), 256, 0, s>>>(
-                    g->d_dlog, g->d_state, c->D, source, g->v, c->front[0], c->counters + 0, cap, overflow,
-                    c->counters + kInvTotal, c->inv);
+                k_invalidate<<<grid_for(std::max<uint64_t>(g->dlog_bound, 1), 256), 256, 0, s>>>(g->d_dlog,
+                                                                                                 g->d_state, a);
                 return cudaSuccess;
             }));
-            MK_TRY(read_word(g, c->counters + 0, &n, s));
-            MK_TRY(run_rounds(g, c, &cur, n, s, "sssp_invalidate_round", [&](int a, uint32_t na, int b) {
-                k_invalidate_round<<<grid_for((uint64_t)na, 256), 256, 0, s>>>(
-                    g->v, c->D, c->front[a], na, c->front[b], c->counters + b, cap, source, max_hops, overflow,
-                    c->counters + kInvTotal, c->inv);
+            a.mode = 1;
+            MK_TRY(run_phase(g, a, "sssp_invalidate_rounds", s));
+            a.mode = 0;
+            MK_CUDA(cudaMemsetAsync(c->counters + kCnt0, 0, 12, s));
+            MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
+                k_relax_into_invalid<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
-            uint32_t invalidated = 0;
-            MK_TRY(read_word(g, c->counters + kInvTotal, &invalidated, s));
-            cur = 0;
-            MK_CUDA(cudaMemsetAsync(c->counters, 0, 8, s));
-            if (invalidated) {
-                const uint32_t round = seeds_round;
-                MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
-                    k_relax_into_invalid<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(
-                        g->v, c->D, c->front[0], c->counters + 0, cap, c->stamp, round, unit, max_hops, overflow,
-                        c->inv);
-                    return cudaSuccess;
-                }));
-            }
-        } else {
-            MK_CUDA(cudaMemsetAsync(c->counters, 0, 8, s));
         }
         // incremental prologue: edges inserted since the last commit
-        const uint32_t round = seeds_round;
         MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
-            k_relax_updated<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(g->v, c->D, c->front[0], c->counters + 0, cap,
-                                                                       c->stamp, round, unit, max_hops, overflow);
+            k_relax_updated<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(a);
             return cudaSuccess;
         }));
-        MK_TRY(read_word(g, c->counters + 0, &n, s));
     }
-    // common epilogue
-    MK_TRY(run_rounds(g, c, &cur, n, s, "sssp_round", relax_launch));
+    // common epilogue: rounds until no distance improves
+    a.mode = 0;
+    MK_TRY(run_phase(g, a, "sssp_rounds", s));
     MK_TRY(timed(g, "sssp_unpack", s, 2, [&]() {
-        k_flag_overflow<<<1, 1, 0, s>>>(overflow, g->d_state);
+        k_sssp_finish<<<1, 1, 0, s>>>(c->counters, g->d_state);
         if (d_dist || d_parent)
             k_unpack<<<grid_for(V, 256), 256, 0, s>>>(c->D, V, d_dist, d_parent);
         return cudaSuccess;

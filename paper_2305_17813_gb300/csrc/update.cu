@@ -31,28 +31,6 @@ __global__ void k_build_keys(const uint32_t *__restrict__ src, const uint32_t *_
         set_status(st, kErrInvalid);
 }
 
-// Advances the pool hint to the first bitmap word that still has a free bit
-// (one block; words below the hint are all full).
-__global__ void k_pool_hint(GView g)
-{
-    __shared__ uint32_t first;
-    if (threadIdx.x == 0)
-        first = 0xFFFFFFFFu;
-    __syncthreads();
-    const uint32_t W = g.pool_words;
-    for (uint32_t base = g.st->pool_hint; base < W; base += blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        if (i < W && g.bitmap[i] != kFull)
-            atomicMin(&first, i);
-        __syncthreads();
-        if (first != 0xFFFFFFFFu)
-            break;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        g.st->pool_hint = first == 0xFFFFFFFFu ? W : first;
-}
-
 // Sorted-batch prologue shared by insert and delete: decodes this lane's
 // edge, flags the first occurrence of each (src, dst) and finds its list.
 struct LaneEdge {
@@ -195,7 +173,7 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
             }
             // the tail is full: take a pool slab, fill it privately with up
             // to 15 absent edges, then publish it with a CAS on the next lane
-            const uint32_t ns = alloc_slab(g, warp);
+            const uint32_t ns = alloc_slab(g, (uint32_t)warp * 0x9E3779B9u ^ tail ^ (uint32_t)(guard << 24));
             if (ns == kNil) {
                 if (lane == 0)
                     set_status(g.st, kErrPool);
@@ -337,8 +315,7 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
         MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
     MK_TRY(stage(g, d_src, d_dst, d_w, n, s));
     const uint32_t max_hops = g->v.P + 2;
-    return timed(g, "insert", s, 2, [&]() {
-        k_pool_hint<<<1, 1024, 0, s>>>(g->v);
+    return timed(g, "insert", s, 1, [&]() {
         k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_kout, g->d_iout, d_w, n, g->vbits, d_inserted, max_hops);
         return cudaSuccess;
     });
