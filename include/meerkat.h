@@ -133,6 +133,30 @@ mk_status mk_graph_destroy(mk_graph *g);
 mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w,
                           uint64_t n, uint8_t *d_inserted, void *stream);
 
+/* mk_insert_batch without any allocation.  The paper has no counterpart:
+ * this is a service of this library.  mk_insert_batch grows its staging
+ * buffers with cudaMalloc the first time it sees a larger batch (after a
+ * cudaStreamSynchronize and cudaFree of the old ones); a caller that must
+ * not synchronise or allocate at that point -- a serving loop between
+ * requests, or a process whose device memory is owned by another allocator
+ * or fixed at start-up -- uses this entry point instead.  Results and flags
+ * are identical to mk_insert_batch.
+ *  - n <= MK_NOALLOC_MAX_BATCH (65,536); a larger n returns
+ *    MK_ERR_INVALID_ARG and enqueues nothing.
+ *  - The staging scratch is one fixed 3.5 MiB device array inside the library
+ *    (every GPU that loads the library holds it until the process exits).
+ *    The first call on each device looks up the array's address and checks
+ *    the sort workspace size (cudaGetSymbolAddress, no allocation); make that
+ *    first call before any stream capture.
+ *  - Every call on a device shares the array and it keeps the last call's
+ *    contents; nothing in it needs to start at zero.  Two calls whose work
+ *    overlaps on the GPU (different streams, or different graphs at the same
+ *    time) race on it: order them on one stream or with events.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define MK_NOALLOC_MAX_BATCH 65536u
+mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w,
+                                  uint64_t n, uint8_t *d_inserted, void *stream);
+
 /* Deletes n edges: a present edge's pair becomes TOMBSTONE (never reused;
  * paper, Sec. "Experimental Evaluation", deletion), an absent edge is a
  * no-op; the first occurrence of a repeated pair is the one that deletes.

@@ -21,6 +21,7 @@ MK_ERR_NO_MEMORY = -5
 MK_ERR_INTERNAL = -6
 MK_NONE = 0xFFFFFFFF
 MK_INVALID_LANE = 0xFF
+MK_NOALLOC_MAX_BATCH = 65536
 
 COUNTER_NAMES = ["query_slabs", "insert_slabs", "insert_new_slabs", "delete_slabs", "relax_lists", "relax_slabs",
                  "relax_edges", "relax_improved", "invalidate_slabs", "wcc_slabs", "wcc_edges", "commit_slabs"]
@@ -84,6 +85,7 @@ SIGNATURES = {
     "mk_graph_create": (_INT, [_U32, _U64, _U32, _P, _P, ctypes.POINTER(_P)]),
     "mk_graph_destroy": (_INT, [_P]),
     "mk_insert_batch": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),
+    "mk_insert_batch_noalloc": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),
     "mk_delete_batch": (_INT, [_P, _P, _P, _U64, _P, _P]),
     "mk_query_batch": (_INT, [_P, _P, _P, _U64, _P, _P, _P]),
     "mk_commit_batch": (_INT, [_P, _P]),
