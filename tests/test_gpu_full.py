@@ -1,0 +1,151 @@
+"""Full-size workloads in the launch configuration the benchmark times.
+
+Power-law (R-MAT scale 20, 16M edges, load-factor buckets): every batch size
+of the workload (2^12, 2^16, 2^20, 2^22) is inserted, deleted and queried with
+per-edge flags and bitmaps compared to the oracle, the final edge set is
+compared in full, and BFS, SSSP and WCC from the max-degree vertex are
+compared in full after the last insert and the last delete batch.
+
+Road-like (4,096 x 4,096 grid + 0.1% long-range edges, 67M edges): 64 mixed
+batches of 2^16 with incremental SSSP from the corner after each batch; each
+result is checked against properties that fix it at any size (triangle
+inequality on every live edge, every parent edge live and tight, nothing
+reachable outside the reachable set), and the first and last against a full
+Dijkstra of the oracle.  A 256 x 256 version is compared in full after every
+batch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+NONE = 0xFFFFFFFF
+
+
+def _mk():
+    import paper_2305_17813_gb300 as mk
+
+    mk.load()
+    return mk
+
+
+def u32(t):
+    return _mk().to_numpy_u32(t)
+
+
+def check_tree_properties(es, ed, ew, dist, par, src):
+    """Properties that determine the shortest-path tree with min-id parents."""
+    reach = dist != NONE
+    du = dist[es].astype(np.int64)
+    dv = dist[ed].astype(np.int64)
+    w = ew.astype(np.int64)
+    ru = reach[es]
+    assert np.all(reach[ed][ru]), "an edge leaves the reachable set"
+    assert np.all(dv[ru] <= du[ru] + w[ru]), "triangle inequality"
+    assert dist[src] == 0 and par[src] == src
+    assert np.all(par[~reach] == NONE)
+    # min tight predecessor for every reachable vertex
+    tight = ru & (du + w == dv) & (ed != src)
+    best = np.full(len(dist), NONE, np.int64)
+    np.minimum.at(best, ed[tight], es[tight].astype(np.int64))
+    v = np.nonzero(reach)[0]
+    v = v[v != src]
+    assert np.array_equal(par[v].astype(np.int64), best[v]), "parent is not the min-id tight predecessor"
+
+
+def test_powerlaw_full_size_all_batch_sizes(cuda_lib):
+    mk = _mk()
+    G = synth.powerlaw_graph()
+    src = int(np.argmax(np.bincount(G.src, minlength=G.V)))
+    buckets = mk.bucket_rule(G.V, G.src, 0.7)
+    g = mk.Graph(G.V, edge_capacity_hint=len(G.src) + (1 << 24), buckets=buckets)
+    o = oracle.OracleGraph(G.V)
+    chunk = 1 << 22
+    for i in range(0, len(G.src), chunk):
+        g.insert(G.src[i:i + chunk], G.dst[i:i + chunk], G.w[i:i + chunk], flags=False)
+    o.insert(G.src, G.dst, G.w)
+    g.commit()
+    g.sssp(src)
+    g.bfs(src)
+    g.wcc()
+    g.commit()
+    for k, B in enumerate([1 << 12, 1 << 16, 1 << 20, 1 << 22]):
+        b = synth.powerlaw_batch(G, k, B)
+        f = g.insert(b.ins_src, b.ins_dst, b.ins_w).cpu().numpy()
+        assert np.array_equal(f, o.insert(b.ins_src, b.ins_dst, b.ins_w)), "insert flags, batch %d" % B
+        last = k == 3
+        if last:
+            for (d, p), (od, op) in ((g.sssp(src), o.sssp(src)), (g.bfs(src), o.bfs(src))):
+                assert np.array_equal(u32(d), od) and np.array_equal(u32(p), op)
+            assert np.array_equal(u32(g.wcc()), o.wcc())
+        else:
+            g.sssp(src)
+            g.bfs(src)
+            g.wcc()
+        g.commit()
+        f = g.delete(b.del_src, b.del_dst).cpu().numpy()
+        assert np.array_equal(f, o.delete(b.del_src, b.del_dst)), "delete flags, batch %d" % B
+        if last:
+            for (d, p), (od, op) in ((g.sssp(src), o.sssp(src)), (g.bfs(src), o.bfs(src))):
+                assert np.array_equal(u32(d), od) and np.array_equal(u32(p), op)
+            assert np.array_equal(u32(g.wcc()), o.wcc())
+        else:
+            g.sssp(src)
+            g.bfs(src)
+            g.wcc()
+        g.commit()
+        bm, w = g.query(b.q_src, b.q_dst)
+        obm, ow = o.query(b.q_src, b.q_dst)
+        assert np.array_equal(u32(bm), obm) and np.array_equal(u32(w), ow), "query, batch %d" % B
+        assert g.last_error() == mk.MK_OK
+    es, ed, ew = g.export()
+    os_, od_, ow_ = o.export()
+    assert np.array_equal(u32(es), os_) and np.array_equal(u32(ed), od_) and np.array_equal(u32(ew), ow_)
+    g.close()
+
+
+def road_run(rows, cols, batches, full_check_every):
+    mk = _mk()
+    R = synth.road_graph(rows, cols)
+    g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + batches * (1 << 16), buckets=1)
+    o = oracle.OracleGraph(R.V)
+    chunk = 1 << 22
+    for i in range(0, len(R.src), chunk):
+        g.insert(R.src[i:i + chunk], R.dst[i:i + chunk], R.w[i:i + chunk], flags=False)
+    o.insert(R.src, R.dst, R.w)
+    g.commit()
+    d, p = g.sssp(0)
+    od, op = o.sssp(0)
+    assert np.array_equal(u32(d), od) and np.array_equal(u32(p), op)
+    g.commit()
+    B = 1 << 16 if rows >= 1024 else 1 << 10
+    for k in range(batches):
+        b = synth.road_batch(R, k, B)
+        fd = g.delete(b.del_src, b.del_dst).cpu().numpy()
+        assert np.array_equal(fd, o.delete(b.del_src, b.del_dst))
+        fi = g.insert(b.ins_src, b.ins_dst, b.ins_w).cpu().numpy()
+        assert np.array_equal(fi, o.insert(b.ins_src, b.ins_dst, b.ins_w))
+        d, p = g.sssp(0)
+        g.commit()
+        assert g.last_error() == mk.MK_OK
+        dist, par = u32(d), u32(p)
+        if full_check_every and (k % full_check_every == 0 or k == batches - 1):
+            od, op = o.sssp(0)
+            assert np.array_equal(dist, od) and np.array_equal(par, op), "batch %d" % k
+        elif k in (0, batches - 1) or k % 16 == 0:
+            es, ed, ew = (u32(x) for x in g.export())
+            check_tree_properties(es, ed, ew, dist, par, 0)
+    if not full_check_every:
+        od, op = o.sssp(0)
+        assert np.array_equal(u32(d), od) and np.array_equal(u32(p), op)
+    g.close()
+
+
+def test_road_small_every_batch(cuda_lib):
+    road_run(256, 256, 16, full_check_every=1)
+
+
+def test_road_full_size_64_batches(cuda_lib):
+    road_run(4096, 4096, 64, full_check_every=0)
