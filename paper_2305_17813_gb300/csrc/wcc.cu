@@ -1,11 +1,14 @@
 // Static and incremental weakly connected components (paper, Sec.
 // "Incremental WCC" and Sec. "Auxiliary Data Structures", Union-Find).
 //
-// Union-Async: to unite a and b, find both roots and hook the larger root
-// under the smaller with one CAS, retrying from the new parent when the CAS
-// loses.  Parents therefore never exceed their child's id, the root of every
-// tree is its smallest vertex, and after full path compression each label is
-// the smallest vertex id of its component.  Finds use path halving.
+// Union-Async: to unite sets, find their roots and hook the larger root under
+// the smaller with one CAS, retrying with fresh roots when the CAS loses.
+// Parents therefore never exceed their child's id, the root of every tree is
+// its smallest vertex, and after full path compression each label is the
+// smallest vertex id of its component.  Finds use path halving.  A warp unites
+// a whole slab at once: the source and the slab's live destinations are
+// hooked under the smallest of their roots (one parallel round of finds and
+// CASes per slab instead of one union per edge on the same source root).
 //
 // Static pass: every live edge of every list.  Incremental pass (insert-only
 // epochs): only the entries written since the last commit, read with the
@@ -31,23 +34,35 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *p, uint32_t x)
     }
 }
 
-// Returns false if the retry bound was hit.
-__device__ __forceinline__ bool uf_union(uint32_t *p, uint32_t a, uint32_t b, uint32_t limit)
+// Warp-wide union of the sets of every active lane's element: all roots are
+// found in parallel, the warp's smallest root m is the anchor, and every
+// other root is hooked under it with one CAS on its parent (m is smaller, so
+// parents keep decreasing).  A lane whose CAS loses (its root was hooked by
+// another warp meanwhile) retries with fresh roots of its element and of the
+// anchor, hooking the larger under the smaller.  Returns false if the retry
+// bound was hit.  Must be called by the full warp.
+__device__ __forceinline__ bool warp_union(uint32_t *p, uint32_t e, bool active, uint32_t limit)
 {
+    uint32_t r = active ? uf_find(p, e) : kNil;
+    uint32_t m = r;
+#pragma unroll
+    for (uint32_t o = 16; o; o >>= 1)
+        m = min(m, __shfl_xor_sync(kFull, m, o));
+    bool pending = active && r != m;
     for (uint32_t it = 0; it < limit; ++it) {
-        a = uf_find(p, a);
-        b = uf_find(p, b);
-        if (a == b)
+        if (!__any_sync(kFull, pending))
             return true;
-        if (a < b) {
-            const uint32_t t = a;
-            a = b;
-            b = t;
+        if (pending) {
+            const uint32_t a = uf_find(p, m);
+            r = uf_find(p, r);
+            if (r == a) {
+                pending = false;
+            } else {
+                const uint32_t hi = max(r, a), lo = min(r, a);
+                if (atomicCAS(&p[hi], hi, lo) == hi)
+                    pending = false;
+            }
         }
-        const uint32_t old = atomicCAS(&p[a], a, b);
-        if (old == a)
-            return true;
-        a = old;
     }
     return false;
 }
@@ -83,9 +98,11 @@ __global__ void __launch_bounds__(256) k_uf_hook(GView g, uint32_t *p, int all_l
         uint32_t first_lane = 0, start = L;
         if (!all_lists)
             start = update_begin(g, L, &first_lane);
+        // lane 30 (no key) carries the list's source into each slab's union
         slabs += walk_list(g, start, first_lane, max_hops, [&](uint32_t y, uint32_t, bool live) {
             edges += __popc(__ballot_sync(kFull, live));
-            if (live && !uf_union(p, src, y, 1u << 20))
+            const bool act = live || lane == 30;
+            if (!warp_union(p, lane == 30 ? src : y, act, 1u << 20) && lane == 0)
                 *failed = 1;
         });
     }
