@@ -93,36 +93,35 @@ struct RoundArgs {
 
 namespace {
 
-// One round over frontier F[0, n): warps stride over groups of 32 lists.
+// One round over frontier F[0, n): warps stride over groups of 32 lists and
+// walk them four at a time (8-lane groups, walk_lists_g8).
 __device__ void relax_body(const RoundArgs &a, const uint32_t *F, uint32_t n, uint32_t *Fn, uint32_t *cnt,
                            uint32_t round, uint64_t warp0, uint64_t nwarps)
 {
     const GView &g = a.g;
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 3;
     int *overflow = (int *)(a.ctr + kOverflow);
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
     for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
         const uint64_t i = base + lane;
-        bool todo = i < n;
+        const bool todo = i < n;
         const uint32_t mine = todo ? F[i] : 0;
-        uint32_t q;
-        while ((q = __ballot_sync(kFull, todo)) != 0) {
-            const uint32_t leader = __ffs(q) - 1;
-            if (lane == leader)
-                todo = false;
-            const uint32_t L = __shfl_sync(kFull, mine, leader);
-            const uint32_t x = g.list_src[L];
-            const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&a.D[x])), 0);
-            ++lists;
-            if (dx == kInf32)
-                continue;
-            slabs += walk_list(g, L, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-                edges += __popc(__ballot_sync(kFull, live));
-                bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
-                up = up && first_this_round(a.stamp, y, round);
-                improved += __popc(__ballot_sync(kFull, up));
-                enqueue_lists(g, y, up, Fn, cnt, a.cap, overflow);
-            });
+        const uint32_t q = __ballot_sync(kFull, todo);
+        lists += __popc(q);
+        for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
+            const uint32_t owner = group_item(q, pass, gi);
+            const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
+            const bool has = owner < 32;
+            const uint32_t x = has ? g.list_src[L] : 0;
+            const uint32_t dx = has ? node_dist(__ldcg(&a.D[x])) : kInf32;
+            slabs += walk_lists_g8(g, dx != kInf32 ? L : kNil, 0, a.max_hops,
+                                   [&](uint32_t y, uint32_t w, bool live) {
+                                       edges += __popc(__ballot_sync(kFull, live));
+                                       bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
+                                       up = up && first_this_round(a.stamp, y, round);
+                                       improved += __popc(__ballot_sync(kFull, up));
+                                       enqueue_lists(g, y, up, Fn, cnt, a.cap, overflow);
+                                   });
         }
     }
     count_add(g.st, kCtrRelaxLists, lists);
@@ -132,27 +131,26 @@ __device__ void relax_body(const RoundArgs &a, const uint32_t *F, uint32_t n, ui
 }
 
 // One round of invalidation: the tree children of the invalidated vertices
-// whose lists are in F become invalid too.
+// whose lists are in F become invalid too (lists walked four at a time).
 __device__ void invalidate_body(const RoundArgs &a, const uint32_t *F, uint32_t n, uint32_t *Fn, uint32_t *cnt,
                                 uint64_t warp0, uint64_t nwarps)
 {
     const GView &g = a.g;
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 3;
     int *overflow = (int *)(a.ctr + kOverflow);
     uint32_t *total = a.ctr + kInvTotal;
     unsigned long long slabs = 0;
     for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
         const uint64_t i = base + lane;
-        bool todo = i < n;
+        const bool todo = i < n;
         const uint32_t mine = todo ? F[i] : 0;
-        uint32_t q;
-        while ((q = __ballot_sync(kFull, todo)) != 0) {
-            const uint32_t leader = __ffs(q) - 1;
-            if (lane == leader)
-                todo = false;
-            const uint32_t L = __shfl_sync(kFull, mine, leader);
-            const uint32_t x = g.list_src[L];
-            slabs += walk_list(g, L, 0, a.max_hops, [&](uint32_t y, uint32_t, bool live) {
+        const uint32_t q = __ballot_sync(kFull, todo);
+        for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
+            const uint32_t owner = group_item(q, pass, gi);
+            const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
+            const bool has = owner < 32;
+            const uint32_t x = has ? g.list_src[L] : 0;
+            slabs += walk_lists_g8(g, has ? L : kNil, 0, a.max_hops, [&](uint32_t y, uint32_t, bool live) {
                 bool hit = false;
                 if (live && y != a.source) {
                     const unsigned long long dy = __ldcg(&a.D[y]);
@@ -306,7 +304,7 @@ __global__ void __launch_bounds__(256) k_relax_into_invalid(RoundArgs a)
     const GView &g = a.g;
     if (ld_volatile(a.ctr + kInvTotal) == 0)
         return;
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 3;
     const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
     if (base >= g.H)
         return;
@@ -314,31 +312,30 @@ __global__ void __launch_bounds__(256) k_relax_into_invalid(RoundArgs a)
     int *overflow = (int *)(a.ctr + kOverflow);
     const uint64_t l = base + lane;
     bool todo = false;
-    uint32_t x = 0;
+    uint32_t x = 0, dx = kInf32;
     if (l < g.H) {
         x = g.list_src[l];
-        todo = node_dist(__ldcg(&a.D[x])) != kInf32;
+        dx = node_dist(__ldcg(&a.D[x]));
+        todo = dx != kInf32;
     }
-    unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
-    uint32_t q;
-    while ((q = __ballot_sync(kFull, todo)) != 0) {
-        const uint32_t leader = __ffs(q) - 1;
-        if (lane == leader)
-            todo = false;
-        const uint32_t L = (uint32_t)(base + leader);
-        const uint32_t src = __shfl_sync(kFull, x, leader);
-        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&a.D[src])), 0);
-        ++lists;
-        slabs += walk_list(g, L, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            edges += __popc(__ballot_sync(kFull, live));
-            const bool target = live && ((a.inv[y >> 5] >> (y & 31)) & 1u);
-            bool up = target && relax(a.D, src, dx, y, a.unit ? 1u : w);
-            up = up && first_this_round(a.stamp, y, round);
-            improved += __popc(__ballot_sync(kFull, up));
-            enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
-        });
+    const uint32_t q = __ballot_sync(kFull, todo);
+    unsigned long long slabs = 0, edges = 0, improved = 0;
+    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
+        const uint32_t owner = group_item(q, pass, gi);
+        const bool has = owner < 32;
+        const uint32_t src = __shfl_sync(kFull, x, owner & 31);
+        const uint32_t dsrc = __shfl_sync(kFull, dx, owner & 31);
+        slabs += walk_lists_g8(g, has ? (uint32_t)(base + owner) : kNil, 0, a.max_hops,
+                               [&](uint32_t y, uint32_t w, bool live) {
+                                   edges += __popc(__ballot_sync(kFull, live));
+                                   const bool target = live && ((a.inv[y >> 5] >> (y & 31)) & 1u);
+                                   bool up = target && relax(a.D, src, dsrc, y, a.unit ? 1u : w);
+                                   up = up && first_this_round(a.stamp, y, round);
+                                   improved += __popc(__ballot_sync(kFull, up));
+                                   enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+                               });
     }
-    count_add(g.st, kCtrRelaxLists, lists);
+    count_add(g.st, kCtrRelaxLists, __popc(q));
     count_add(g.st, kCtrRelaxSlabs, slabs);
     count_add(g.st, kCtrRelaxEdges, edges);
     count_add(g.st, kCtrRelaxImproved, improved);
@@ -349,37 +346,39 @@ __global__ void __launch_bounds__(256) k_relax_into_invalid(RoundArgs a)
 __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
 {
     const GView &g = a.g;
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 3;
     const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
     if (base >= g.H)
         return;
     const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
     int *overflow = (int *)(a.ctr + kOverflow);
     const uint64_t l = base + lane;
-    bool todo = l < g.H && g.lupd[l];
-    unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
-    uint32_t q;
-    while ((q = __ballot_sync(kFull, todo)) != 0) {
-        const uint32_t leader = __ffs(q) - 1;
-        if (lane == leader)
-            todo = false;
-        const uint32_t L = (uint32_t)(base + leader);
-        const uint32_t src = g.list_src[L];
-        const uint32_t dx = __shfl_sync(kFull, node_dist(__ldcg(&a.D[src])), 0);
-        if (dx == kInf32)
-            continue;
-        uint32_t first_lane = 0;
-        const uint32_t start = update_begin(g, L, &first_lane);
-        ++lists;
-        slabs += walk_list(g, start, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
+    bool todo = false;
+    uint32_t x = 0, dx = kInf32;
+    if (l < g.H && g.lupd[l]) {
+        x = g.list_src[l];
+        dx = node_dist(__ldcg(&a.D[x]));
+        todo = dx != kInf32;
+    }
+    const uint32_t q = __ballot_sync(kFull, todo);
+    unsigned long long slabs = 0, edges = 0, improved = 0;
+    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
+        const uint32_t owner = group_item(q, pass, gi);
+        const bool has = owner < 32;
+        const uint32_t src = __shfl_sync(kFull, x, owner & 31);
+        const uint32_t dsrc = __shfl_sync(kFull, dx, owner & 31);
+        uint32_t first_lane = 0, start = kNil;
+        if (has)
+            start = update_begin(g, (uint32_t)(base + owner), &first_lane);
+        slabs += walk_lists_g8(g, start, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
             edges += __popc(__ballot_sync(kFull, live));
-            bool up = live && relax(a.D, src, dx, y, a.unit ? 1u : w);
+            bool up = live && relax(a.D, src, dsrc, y, a.unit ? 1u : w);
             up = up && first_this_round(a.stamp, y, round);
             improved += __popc(__ballot_sync(kFull, up));
             enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
         });
     }
-    count_add(g.st, kCtrRelaxLists, lists);
+    count_add(g.st, kCtrRelaxLists, __popc(q));
     count_add(g.st, kCtrRelaxSlabs, slabs);
     count_add(g.st, kCtrRelaxEdges, edges);
     count_add(g.st, kCtrRelaxImproved, improved);

@@ -101,3 +101,57 @@ __device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool p
 }
 
 } // namespace mk
+
+namespace mk {
+
+// Tiled walk: each 8-lane group of the warp walks its own slab list (so a
+// warp has four 128-byte slab loads in flight instead of one); lane `sub` of
+// a group loads words 4*sub .. 4*sub+3 of the slab as one 16-byte vector,
+// i.e. pairs 2*sub and 2*sub+1 (lane 7: pair 14, the unused lane 30 and the
+// next-slab lane).  `slab` and `first_lane` are per group (kNil = the group
+// has no list).  Per slab, f(key, weight, live) is called twice by every
+// lane of the warp (convergent), once for each pair the lane holds; `live`
+// is false for free / deleted keys, for key words below first_lane on the
+// first slab, and for groups without a list.  Returns the number of slabs
+// loaded by the warp.
+template <typename F>
+__device__ __forceinline__ uint32_t walk_lists_g8(const GView &g, uint32_t slab, uint32_t first_lane,
+                                                  uint32_t max_hops, F &&f)
+{
+    const uint32_t lane = lane_id(), sub = lane & 7u, gbase = lane & ~7u;
+    bool active = slab != kNil;
+    uint32_t loads = 0;
+    for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+        if (active)
+            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
+        loads += __popc(__ballot_sync(kFull, active && sub == 0));
+        const bool last = sub == 7u;
+        const bool l0 = active && x.x < kTombKey && 4 * sub >= first_lane;
+        const bool l1 = active && !last && x.z < kTombKey && 4 * sub + 2 >= first_lane;
+        f(x.x, x.y, l0);
+        f(x.z, x.w, l1);
+        const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
+        if (active) {
+            if (nxt == kNil || hop + 1 >= max_hops)
+                active = false;
+            else
+                slab = nxt;
+        }
+        first_lane = 0;
+    }
+    return loads;
+}
+
+// The k-th set bit of q handed to 8-lane group `gi` in pass `pass` (four
+// groups per pass): returns the lane index holding that group's item, or
+// 32 when the pass has fewer items than groups.
+__device__ __forceinline__ uint32_t group_item(uint32_t q, uint32_t pass, uint32_t gi)
+{
+    const uint32_t k = pass * 4 + gi;
+    if (k >= (uint32_t)__popc(q))
+        return 32;
+    return nth_set_bit(q, k);
+}
+
+} // namespace mk

@@ -8,7 +8,8 @@
 // smallest vertex id of its component.  Finds use path halving.  A warp unites
 // a whole slab at once: the source and the slab's live destinations are
 // hooked under the smallest of their roots (one parallel round of finds and
-// CASes per slab instead of one union per edge on the same source root).
+// CASes per slab instead of one union per edge on the same source root), and
+// a warp walks four lists at a time.
 //
 // Static pass: every live edge of every list.  Incremental pass (insert-only
 // epochs): only the entries written since the last commit, read with the
@@ -34,34 +35,37 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *p, uint32_t x)
     }
 }
 
-// Warp-wide union of the sets of every active lane's element: all roots are
-// found in parallel, the warp's smallest root m is the anchor, and every
-// other root is hooked under it with one CAS on its parent (m is smaller, so
-// parents keep decreasing).  A lane whose CAS loses (its root was hooked by
-// another warp meanwhile) retries with fresh roots of its element and of the
-// anchor, hooking the larger under the smaller.  Returns false if the retry
-// bound was hit.  Must be called by the full warp.
-__device__ __forceinline__ bool warp_union(uint32_t *p, uint32_t e, bool active, uint32_t limit)
+// Union of the sets of up to 16 elements held by one 8-lane group, two per
+// lane: all roots are found in parallel, the group's smallest root m is the
+// anchor, and every other root is hooked under it with one CAS on its parent
+// (m is smaller, so parents keep decreasing).  An element whose CAS loses
+// (its root was hooked by another warp meanwhile) retries with fresh roots
+// of itself and of the anchor, hooking the larger under the smaller.
+// Returns false if the retry bound was hit.  Must be called by the full warp.
+__device__ __forceinline__ bool group_union2(uint32_t *p, uint32_t e0, bool a0, uint32_t e1, bool a1,
+                                             uint32_t limit)
 {
-    uint32_t r = active ? uf_find(p, e) : kNil;
-    uint32_t m = r;
-#pragma unroll
-    for (uint32_t o = 16; o; o >>= 1)
-        m = min(m, __shfl_xor_sync(kFull, m, o));
-    bool pending = active && r != m;
+    uint32_t r0 = a0 ? uf_find(p, e0) : kNil;
+    uint32_t r1 = a1 ? uf_find(p, e1) : kNil;
+    uint32_t m = min(r0, r1);
+    m = min(m, __shfl_xor_sync(kFull, m, 4));
+    m = min(m, __shfl_xor_sync(kFull, m, 2));
+    m = min(m, __shfl_xor_sync(kFull, m, 1));
+    bool p0 = a0 && r0 != m, p1 = a1 && r1 != m;
     for (uint32_t it = 0; it < limit; ++it) {
-        if (!__any_sync(kFull, pending))
+        if (!__any_sync(kFull, p0 || p1))
             return true;
-        if (pending) {
+        if (p0) {
             const uint32_t a = uf_find(p, m);
-            r = uf_find(p, r);
-            if (r == a) {
-                pending = false;
-            } else {
-                const uint32_t hi = max(r, a), lo = min(r, a);
-                if (atomicCAS(&p[hi], hi, lo) == hi)
-                    pending = false;
-            }
+            r0 = uf_find(p, r0);
+            if (r0 == a || atomicCAS(&p[max(r0, a)], max(r0, a), min(r0, a)) == max(r0, a))
+                p0 = false;
+        }
+        if (p1) {
+            const uint32_t a = uf_find(p, m);
+            r1 = uf_find(p, r1);
+            if (r1 == a || atomicCAS(&p[max(r1, a)], max(r1, a), min(r1, a)) == max(r1, a))
+                p1 = false;
         }
     }
     return false;
@@ -76,35 +80,52 @@ __global__ void k_uf_init(uint32_t *p, uint32_t V)
         p[v] = v;
 }
 
-// Unites src with every live destination of the selected lists; warp per 32
-// lists.  all_lists: every list from its head; otherwise only updated lists
-// from their UpdateIterator start.
+// Unites src with every live destination of the selected lists.  Each warp
+// owns 32 consecutive lists and walks the selected ones four at a time, one
+// per 8-lane group with 16-byte loads (pairs 2*sub and 2*sub+1 per lane); the
+// unused slot of lane 7 (slab lane 30) carries the list's source, so each
+// slab's source and destinations are united in one group_union2.
+// all_lists: every list from its head; otherwise only updated lists from
+// their UpdateIterator start.
 __global__ void __launch_bounds__(256) k_uf_hook(GView g, uint32_t *p, int all_lists, uint32_t max_hops, int *failed)
 {
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
     const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
     if (base >= g.H)
         return;
     const uint64_t l = base + lane;
-    bool todo = l < g.H && (all_lists || g.lupd[l]);
+    const bool todo = l < g.H && (all_lists || g.lupd[l]);
+    const uint32_t q = __ballot_sync(kFull, todo);
     unsigned long long slabs = 0, edges = 0;
-    uint32_t q;
-    while ((q = __ballot_sync(kFull, todo)) != 0) {
-        const uint32_t leader = __ffs(q) - 1;
-        if (lane == leader)
-            todo = false;
-        const uint32_t L = (uint32_t)(base + leader);
-        const uint32_t src = g.list_src[L];
-        uint32_t first_lane = 0, start = L;
-        if (!all_lists)
-            start = update_begin(g, L, &first_lane);
-        // lane 30 (no key) carries the list's source into each slab's union
-        slabs += walk_list(g, start, first_lane, max_hops, [&](uint32_t y, uint32_t, bool live) {
-            edges += __popc(__ballot_sync(kFull, live));
-            const bool act = live || lane == 30;
-            if (!warp_union(p, lane == 30 ? src : y, act, 1u << 20) && lane == 0)
+    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
+        const uint32_t owner = group_item(q, pass, gi);
+        const bool has = owner < 32;
+        const uint32_t L = (uint32_t)(base + (owner & 31));
+        const uint32_t src = has ? g.list_src[L] : 0;
+        uint32_t first_lane = 0, slab = kNil;
+        if (has)
+            slab = all_lists ? L : update_begin(g, L, &first_lane);
+        bool active = slab != kNil;
+        for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+            uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+            if (active)
+                x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
+            slabs += __popc(__ballot_sync(kFull, active && sub == 0));
+            const bool last = sub == 7u;
+            const bool a0 = active && x.x < kTombKey && 4 * sub >= first_lane;
+            const bool a1 = last ? active : (active && x.z < kTombKey && 4 * sub + 2 >= first_lane);
+            edges += __popc(__ballot_sync(kFull, a0)) + __popc(__ballot_sync(kFull, a1 && !last));
+            if (!group_union2(p, x.x, a0, last ? src : x.z, a1, 1u << 20) && lane == 0)
                 *failed = 1;
-        });
+            const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
+            if (active) {
+                if (nxt == kNil || hop + 1 >= max_hops)
+                    active = false;
+                else
+                    slab = nxt;
+            }
+            first_lane = 0;
+        }
     }
     count_add(g.st, kCtrWccSlabs, slabs);
     count_add(g.st, kCtrWccEdges, edges);
