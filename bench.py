@@ -54,6 +54,9 @@ def parse_args(argv=None):
     p.add_argument("--draws", type=int, default=1 << 24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", choices=["powerlaw", "growth"], default="powerlaw",
+                   help="powerlaw: the benchmark line; growth: the learned-sizing study on the R-MAT "
+                        "scale-22 growth stream (prints its own JSON line)")
     return p.parse_args(argv)
 
 
@@ -405,6 +408,114 @@ def run_ours(args, world, rank, local):
     return result, dist, G, source, batches
 
 
+# ------------------------------------------------------- learned sizing
+
+def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.7, keep_graphs=False):
+    """Learned slab sizing on a growth stream S (synth.growth_stream).
+
+    A graph sized by the load-factor rule at the initial load runs batches
+    1..split while a degree trace records every applied insert and delete.
+    The network is trained on (features at batch t, edges gained per batch
+    over the next `horizon` batches) for every t with a full window, then
+    predicts each vertex's growth over the remaining batches.  Two graphs are
+    rebuilt from the live edges at `split`: one with the learned bucket
+    counts, one with the load-factor rule on the current degrees (the judge).
+    Both run the remaining batches; the insert time, a query batch over live
+    edges, chain lengths and slabs walked per query are compared."""
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+    from paper_2305_17813_gb300 import sizing
+
+    V = S.V
+    n_batches = len(S.batches)
+    u = lambda a: mk.to_device_u32(a)  # noqa: E731
+    total_edges = len(S.init.src) + sum(len(b.ins_src) for b in S.batches)
+    b0 = mk.bucket_rule(V, u(S.init.src), load_factor)
+    g = mk.Graph(V, edge_capacity_hint=2 * total_edges, buckets=b0)
+    trace = sizing.DegreeTrace(V)
+    s0, d0 = u(S.init.src), u(S.init.dst)
+    f = g.insert(s0, d0, u(S.init.w))
+    trace.apply(s0, d0, f, +1)
+    g.commit()
+    trace.snapshot()
+    snaps = {0: trace.out_deg.clone()}
+    feats = {}
+    for k in range(split):
+        b = S.batches[k]
+        si, di = u(b.ins_src), u(b.ins_dst)
+        trace.apply(si, di, g.insert(si, di, u(b.ins_w)), +1)
+        sd, dd = u(b.del_src), u(b.del_dst)
+        trace.apply(sd, dd, g.delete(sd, dd), -1)
+        g.commit()
+        trace.snapshot()
+        t = k + 1
+        snaps[t] = trace.out_deg.clone()
+        if t >= 4 and t + horizon <= split:
+            feats[t] = trace.features(b0)
+    X = torch.cat([feats[t] for t in sorted(feats)])
+    T = torch.cat([sizing.growth_targets(snaps[t], snaps[t + horizon], horizon) for t in sorted(feats)])
+    model = sizing.SizingModel(seed=0)
+    t0 = time.time()
+    losses = model.train(X, T, epochs=epochs, lr=lr)
+    train_s = time.time() - t0
+    x_now = trace.features(b0)
+    learned_b, _ = model.buckets(x_now, trace.out_deg, horizon=n_batches - split, load_factor=load_factor)
+    es, ed, ew = g.export()
+    rule_b = mk.bucket_rule(V, es, load_factor)
+    source = int(torch.argmax(trace.out_deg).item())
+    g.close()
+    out = {"vertices": V, "batches": n_batches, "split": split, "horizon": horizon, "train_samples": int(X.shape[0]),
+           "train_losses": [round(x, 5) for x in losses], "train_s": round(train_s, 2), "source": source}
+    graphs = []
+    rng = np.random.default_rng(7)
+    for name, bk in (("learned", learned_b), ("rule", rule_b)):
+        gg = mk.Graph(V, edge_capacity_hint=2 * total_edges, buckets=bk)
+        gg.insert(es, ed, ew, flags=False)
+        gg.commit()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ins_ms = 0.0
+        n_ins = 0
+        for k in range(split, n_batches):
+            b = S.batches[k]
+            si, di, wi = u(b.ins_src), u(b.ins_dst), u(b.ins_w)
+            sd, dd = u(b.del_src), u(b.del_dst)
+            ev[0].record()
+            gg.insert(si, di, wi, flags=False)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ins_ms += ev[0].elapsed_time(ev[1])
+            n_ins += len(b.ins_src)
+            gg.delete(sd, dd, flags=False)
+            gg.commit()
+        ls, ld, _ = gg.export()
+        pick = torch.from_numpy(rng.integers(0, ls.numel(), min(ls.numel(), 1 << 20)))
+        qs, qd = ls[pick.cuda()].contiguous(), ld[pick.cuda()].contiguous()
+        gg.counters(reset=True)
+        gg.query(qs, qd, weights=False)
+        torch.cuda.synchronize()
+        ev[0].record()
+        gg.query(qs, qd, weights=False)
+        ev[1].record()
+        torch.cuda.synchronize()
+        q_ms = ev[0].elapsed_time(ev[1])
+        ctr = gg.counters()
+        st = gg.stats()
+        out[name] = {"lists": int(st["lists"]), "chain_mean": round(st["chain_mean"], 4), "chain_max": int(st["chain_max"]),
+                     "device_bytes": int(st["device_bytes"]),
+                     "query_slabs_per_query": round(ctr["query_slabs"] / 2 / qs.numel(), 4),
+                     "insert_medges_s": round(n_ins / ins_ms / 1e3, 1), "query_medges_s": round(qs.numel() / q_ms / 1e3, 1)}
+        if keep_graphs:
+            graphs.append(gg)
+        else:
+            gg.close()
+    model.close()
+    if keep_graphs:
+        out["graphs"] = graphs
+    return out
+
+
 # ------------------------------------------------------------- CPU oracle
 
 ORACLE_SAMPLE = ("insert, delete and query of the step's B edges each, plus one from-scratch recompute of BFS, "
@@ -469,9 +580,30 @@ def run_reference(args, world, rank, local):
     }
 
 
+def run_growth(args):
+    import torch
+
+    import synth
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    S = synth.growth_stream(scale=22, draws=1 << 26, n_batches=64)
+    gen_s = time.time() - t0
+    res = growth_experiment(S, split=32, horizon=8, epochs=20)
+    res.update({"workload": "R-MAT scale 22 growth stream (67,108,864 draws; first 50% loaded; 64 insert batches "
+                            "with preferential source skew 0.5, each followed by 10% deletes); network trained on "
+                            "batches 1-32, graphs rebuilt at batch 32 with learned vs load-factor bucket counts",
+                "gen_s": round(gen_s, 1)})
+    return res
+
+
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
+    if args.workload == "growth":
+        if rank == 0:
+            print(json.dumps(run_growth(args)), flush=True)
+        return 0
     if args.impl == "reference":
         res = run_reference(args, world, rank, local)
         if res is not None:

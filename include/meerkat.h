@@ -211,6 +211,62 @@ mk_status mk_incr_bfs(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *
  * vertex's component. */
 mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream);
 
+/* -------------------------------------------------------- learned sizing */
+/*
+ * Learned slab sizing.  The paper fixes each vertex's bucket count a priori
+ * from the load factor and its degree (Sec. "Motivation"); this library adds
+ * a small MLP, trained on the degree traces of the running graph, that
+ * predicts how many edges each vertex will gain so a rebuilt graph can give
+ * it enough buckets.  The load-factor rule stays the fallback and the judge.
+ * Bucket counts change the layout (chain lengths) but never a result.
+ *
+ * Network: 8 -> 64 (ReLU) -> 64 (ReLU) -> 1, MK_MLP_NPARAMS fp32 master
+ * parameters laid out as W1[8][64], b1[64], W2[64][64], b2[64], W3[64], b3.
+ * Every pass uses the masters rounded to bf16 (round to nearest even) and
+ * accumulates in fp32; loss = mean squared error; Adam on the masters.
+ */
+#define MK_MLP_NPARAMS 4801
+typedef struct mk_mlp mk_mlp;
+
+/* New network with He-uniform weights drawn from `seed`, zero biases. */
+mk_status mk_mlp_create(uint64_t seed, mk_mlp **out);
+mk_status mk_mlp_destroy(mk_mlp *m);
+int mk_mlp_num_params(void);
+/* Copy the fp32 master parameters to / from host memory (set also resets
+ * the Adam moments). */
+mk_status mk_mlp_get_params(mk_mlp *m, float *h_out);
+mk_status mk_mlp_set_params(mk_mlp *m, const float *h_in);
+/* d_y[i] = network(d_x[8*i .. 8*i+7]) for i < n (device arrays). */
+mk_status mk_mlp_forward(mk_mlp *m, const float *d_x, uint64_t n, float *d_y, void *stream);
+/* d_grad (device, MK_MLP_NPARAMS floats) = gradient of mean((y - t)^2)
+ * over the n samples with respect to the parameters; *d_sse (device double,
+ * nullable) = sum of squared errors. */
+mk_status mk_mlp_gradient(mk_mlp *m, const float *d_x, const float *d_t, uint64_t n, float *d_grad, double *d_sse,
+                          void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the n samples. */
+mk_status mk_mlp_adam_step(mk_mlp *m, const float *d_x, const float *d_t, uint64_t n, float lr, double *d_sse,
+                           void *stream);
+/* Degree trace: for every edge i with d_flags[i] != 0 (or every edge when
+ * d_flags is NULL), d_out_deg[src] += sign and d_in_deg[dst] += sign
+ * (sign = +1 or -1; either output may be NULL). */
+mk_status mk_degree_update(uint32_t V, const uint32_t *d_src, const uint32_t *d_dst, const uint8_t *d_flags,
+                           uint64_t n, int sign, uint32_t *d_out_deg, uint32_t *d_in_deg, void *stream);
+/* Per-vertex features (d_x: V x 8 floats) from out-degree snapshots
+ * d_out_hist[k*V + v] = out-degree of v k batches ago (k = 0..4), the
+ * in-degree and the current bucket count: log1p(d), log1p(d - d_k) for
+ * k = 1..4, log1p(in), log1p(in) - log1p(d), d / (15 * buckets). */
+mk_status mk_sizing_features(uint32_t V, const uint32_t *d_out_hist, const uint32_t *d_in_deg,
+                             const uint32_t *d_buckets, float *d_x, void *stream);
+/* Training targets: d_t[v] = log1p(max(0, later[v] - then[v]) / horizon),
+ * the out-edges gained per batch between two degree snapshots. */
+mk_status mk_sizing_targets(uint32_t V, const uint32_t *d_deg_then, const uint32_t *d_deg_later, float horizon,
+                            float *d_t, void *stream);
+/* Bucket counts from the network: y = net(x) is log1p of the predicted edges
+ * gained per batch; buckets = clamp(ceil((deg + horizon * expm1(max(y, 0)))
+ * / (load_factor * 15)), 1, max_buckets).  d_y receives y (V floats). */
+mk_status mk_sizing_buckets(mk_mlp *m, const float *d_x, const uint32_t *d_out_deg, uint32_t V, float horizon,
+                            float load_factor, uint32_t max_buckets, float *d_y, uint32_t *d_buckets, void *stream);
+
 /* ------------------------------------------------------------- inspection */
 
 /* Writes up to `cap` live edges sorted by (src, dst) to d_src/d_dst/d_w and

@@ -22,6 +22,7 @@ MK_ERR_INTERNAL = -6
 MK_NONE = 0xFFFFFFFF
 MK_INVALID_LANE = 0xFF
 MK_NOALLOC_MAX_BATCH = 65536
+MK_MLP_NPARAMS = 4801
 
 COUNTER_NAMES = ["query_slabs", "insert_slabs", "insert_new_slabs", "delete_slabs", "relax_lists", "relax_slabs",
                  "relax_edges", "relax_improved", "invalidate_slabs", "wcc_slabs", "wcc_edges", "commit_slabs"]
@@ -101,6 +102,18 @@ SIGNATURES = {
     "mk_profile_read": (_INT, [_P, ctypes.POINTER(mk_kernel_time), _INT, ctypes.POINTER(_INT)]),
     "mk_launch_count": (_U64, [_P]),
     "mk_version": (ctypes.c_char_p, []),
+    "mk_mlp_create": (_INT, [_U64, ctypes.POINTER(_P)]),
+    "mk_mlp_destroy": (_INT, [_P]),
+    "mk_mlp_num_params": (_INT, []),
+    "mk_mlp_get_params": (_INT, [_P, _P]),
+    "mk_mlp_set_params": (_INT, [_P, _P]),
+    "mk_mlp_forward": (_INT, [_P, _P, _U64, _P, _P]),
+    "mk_mlp_gradient": (_INT, [_P, _P, _P, _U64, _P, _P, _P]),
+    "mk_mlp_adam_step": (_INT, [_P, _P, _P, _U64, ctypes.c_float, _P, _P]),
+    "mk_degree_update": (_INT, [_U32, _P, _P, _P, _U64, _INT, _P, _P, _P]),
+    "mk_sizing_features": (_INT, [_U32, _P, _P, _P, _P, _P]),
+    "mk_sizing_targets": (_INT, [_U32, _P, _P, ctypes.c_float, _P, _P]),
+    "mk_sizing_buckets": (_INT, [_P, _P, _P, _U32, ctypes.c_float, ctypes.c_float, _U32, _P, _P, _P]),
 }
 
 _lock = threading.Lock()

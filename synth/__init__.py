@@ -289,3 +289,39 @@ def road_batch(g: Batch, k: int, B: int = 1 << 16, wlo: int = 1, whi: int = 1000
     nd = B - ni
     di = np.take(perm, (k * nd + np.arange(nd)) % g.n_grid)
     return Batch(ins_src=s, ins_dst=d, ins_w=w, del_src=g.src[di], del_dst=g.dst[di])
+
+
+def growth_stream(scale: int = 22, draws: int = 1 << 26, n_batches: int = 64, del_frac: float = 0.1,
+                  skew: float = 0.5, seed: int = 0, wlo: int = 1, whi: int = 100) -> Batch:
+    """Learned-sizing workload: an R-MAT growth stream.  `draws` R-MAT pairs
+    (seed `seed`), self-loops and duplicates dropped; the first half is the
+    initial load and the rest arrives in `n_batches` insert batches.  Batch k
+    (seed 2000 + k) is skewed towards vertices that already have edges: with
+    probability `skew` an edge's source is replaced by the source of an
+    edge drawn uniformly from everything loaded so far (preferential
+    attachment).  Each insert batch is followed by a delete batch of
+    del_frac x its size, drawn without replacement from the initial edges."""
+    V = 1 << scale
+    s, d = rmat_pairs(scale, draws, substream(seed, TAG_PAIRS))
+    s, d = dedup_pairs(s, d, V, drop_self=True)
+    E = len(s)
+    half = E // 2
+    w = weights(E, substream(seed, TAG_W), wlo, whi)
+    init = Batch(src=s[:half].copy(), dst=d[:half].copy(), w=w[:half].copy())
+    rest = np.arange(half, E)
+    chunks = np.array_split(rest, n_batches)
+    perm = permutation(half, substream(seed, TAG_PERM))
+    history = s[:half].copy()
+    batches = []
+    used = 0
+    for k, idx in enumerate(chunks):
+        bs = skew_sources(s[idx], skew, substream(2000 + k, TAG_PAIRS), history)
+        bd = d[idx]
+        keep = bs != bd
+        bs, bd, bw = bs[keep], bd[keep], w[idx][keep]
+        history = np.concatenate([history, bs])
+        nd = int(round(del_frac * len(bs)))
+        di = perm[used:used + nd]
+        used += nd
+        batches.append(Batch(ins_src=bs, ins_dst=bd, ins_w=bw, del_src=s[di].copy(), del_dst=d[di].copy()))
+    return Batch(V=V, scale=scale, init=init, batches=batches)
