@@ -54,9 +54,10 @@ def parse_args(argv=None):
     p.add_argument("--draws", type=int, default=1 << 24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", choices=["powerlaw", "growth"], default="powerlaw",
+    p.add_argument("--workload", choices=["powerlaw", "growth", "served"], default="powerlaw",
                    help="powerlaw: the benchmark line; growth: the learned-sizing study on the R-MAT "
-                        "scale-22 growth stream (prints its own JSON line)")
+                        "scale-22 growth stream; served: plain vs continuous-batching serving on the R-MAT "
+                        "scale-21 request stream (each prints its own JSON line)")
     return p.parse_args(argv)
 
 
@@ -253,6 +254,10 @@ def run_ours(args, world, rank, local):
     if st != mk.MK_OK:
         raise RuntimeError("device status %d after the load" % st)
 
+    # X2 autotuner: kernel shapes for this graph (untimed setup)
+    tb = batches[0]
+    tuning = g.autotune(tb["q_src"], tb["q_dst"], source)
+    g.commit()
     dev_batches = []
     for bt in batches[:W + K]:
         dev_batches.append({k: u32(bt[k]) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst",
@@ -364,6 +369,7 @@ def run_ours(args, world, rank, local):
         "phases_ms": {k: round(v, 3) for k, v in phase.items()},
         "roofline": roof, "kernels": kernels, "counters": ctr,
         "gpu_launches": int(launches), "wall_s_timed": round(wall, 3), "gen_s": round(gen_s, 1),
+        "tuning": {k: tuning[k] for k in ("query_group", "query_block", "rounds_blocks_per_sm")},
         "clocks": clock.summary(local),
     }
 
@@ -493,18 +499,19 @@ def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.
         pick = torch.from_numpy(rng.integers(0, ls.numel(), min(ls.numel(), 1 << 20)))
         qs, qd = ls[pick.cuda()].contiguous(), ld[pick.cuda()].contiguous()
         gg.counters(reset=True)
-        gg.query(qs, qd, weights=False)
-        torch.cuda.synchronize()
-        ev[0].record()
-        gg.query(qs, qd, weights=False)
-        ev[1].record()
-        torch.cuda.synchronize()
-        q_ms = ev[0].elapsed_time(ev[1])
+        q_times = []
+        for _ in range(7):
+            ev[0].record()
+            gg.query(qs, qd, weights=False)
+            ev[1].record()
+            torch.cuda.synchronize()
+            q_times.append(ev[0].elapsed_time(ev[1]))
+        q_ms = statistics.median(q_times)
         ctr = gg.counters()
         st = gg.stats()
         out[name] = {"lists": int(st["lists"]), "chain_mean": round(st["chain_mean"], 4), "chain_max": int(st["chain_max"]),
                      "device_bytes": int(st["device_bytes"]),
-                     "query_slabs_per_query": round(ctr["query_slabs"] / 2 / qs.numel(), 4),
+                     "query_slabs_per_query": round(ctr["query_slabs"] / 7 / qs.numel(), 4),
                      "insert_medges_s": round(n_ins / ins_ms / 1e3, 1), "query_medges_s": round(qs.numel() / q_ms / 1e3, 1)}
         if keep_graphs:
             graphs.append(gg)
@@ -513,6 +520,185 @@ def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.
     model.close()
     if keep_graphs:
         out["graphs"] = graphs
+    return out
+
+
+# ---------------------------------------------------------------- serving
+
+def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=8, retain_every=16,
+                     retain_sssp_every=64, n_req=None, log=None, keep_outputs=False, query_pool=1 << 21,
+                     insert_pool=1 << 22):
+    """Plain one-launch-per-request execution against the continuous-batching
+    server on the same request stream R (synth.request_stream) over graph G.
+    First both run with every request available at once (capacity), then
+    with Poisson arrivals at each fraction of the plain capacity; latency =
+    completion - arrival.  The outputs of a deterministic sample of requests
+    (every retain_every-th; every retain_sssp_every-th SSSP) are kept and
+    must be identical between the two modes."""
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+    import synth
+
+    lib = mk.load()
+    V, E = G.V, len(G.src)
+    N = n_req or len(R.kind)
+    kinds, sizes, offs, srcs = R.kind[:N], R.size[:N], R.offset[:N], R.source[:N]
+    u = lambda a: mk.to_device_u32(a)  # noqa: E731
+    QP, IP = query_pool, insert_pool
+    rng = np.random.default_rng(11)
+    pick = rng.integers(0, E, QP)
+    live = rng.random(QP) < 0.5
+    qs = u(np.where(live, G.src[pick], rng.integers(0, V, QP)).astype(np.uint32))
+    qd = u(np.where(live, G.dst[pick], rng.integers(0, V, QP)).astype(np.uint32))
+    is_, id_ = synth.rmat_pairs(int(np.log2(V)), IP, synth.substream(3100, 1))
+    is_, id_ = u(is_), u(id_)
+    iw = u(synth.weights(IP, synth.substream(3100, 2), 1, 100))
+    perm = synth.permutation(E, synth.substream(3100, 3))
+    ds, dd = u(G.src[perm]), u(G.dst[perm])
+    P_ = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    maxn = int(sizes.max()) if N else 1
+    ring = []
+    for _ in range(max_inflight):
+        ring.append({"bm": torch.empty((maxn + 31) // 32, dtype=torch.int32, device="cuda"),
+                     "fl": torch.empty(maxn, dtype=torch.uint8, device="cuda"),
+                     "dist": torch.empty(V, dtype=torch.int32, device="cuda")})
+    retained = {}
+
+    def outputs(i, store):
+        """(out0, out1) for request i; retained requests get their own."""
+        k, n = int(kinds[i]), int(sizes[i])
+        keep = (i % retain_every == 0) if k != 3 else (i % retain_sssp_every == 0)
+        if keep:
+            if k == 0:
+                t = (torch.empty((n + 31) // 32, dtype=torch.int32, device="cuda"), None)
+            elif k in (1, 2):
+                t = (torch.empty(n, dtype=torch.uint8, device="cuda"), None)
+            else:
+                t = (torch.empty(V, dtype=torch.int32, device="cuda"), torch.empty(V, dtype=torch.int32, device="cuda"))
+            store[i] = t
+            return t
+        slot = ring[i % max_inflight]
+        if k == 0:
+            return slot["bm"], None
+        if k in (1, 2):
+            return slot["fl"], None
+        return slot["dist"], None
+
+    def inputs(i):
+        k, n, o = int(kinds[i]), int(sizes[i]), int(offs[i])
+        if k == 0:
+            return qs[o:o + n], qd[o:o + n], None
+        if k == 1:
+            return is_[o:o + n], id_[o:o + n], iw[o:o + n]
+        if k == 2:
+            o %= E
+            if o + n > E:
+                o = 0
+            return ds[o:o + n], dd[o:o + n], None
+        return None, None, None
+
+    pool = int((E + IP) / 15 * 1.3) + (1 << 21)
+
+    def fresh():
+        b = mk.bucket_rule(V, u(G.src), 0.7)
+        g = mk.Graph(V, buckets=b, pool_slabs=pool)
+        g.insert(G.src, G.dst, G.w, flags=False)
+        g.commit()
+        torch.cuda.synchronize()
+        return g
+
+    def run_plain(arrivals, store):
+        g = fresh()
+        h = g.handle
+        sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        lat = np.zeros(N)
+        n_upd = 0
+        t0 = time.perf_counter()
+        for i in range(N):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            k, n = int(kinds[i]), int(sizes[i])
+            a, b, w = inputs(i)
+            o0, o1 = outputs(i, store)
+            if k == 0:
+                rc = lib.mk_query_batch(h, P_(a), P_(b), n, P_(o0), None, sp)
+            elif k == 1:
+                rc = lib.mk_insert_batch(h, P_(a), P_(b), P_(w), n, P_(o0), sp)
+            elif k == 2:
+                rc = lib.mk_delete_batch(h, P_(a), P_(b), n, P_(o0), sp)
+            else:
+                rc = lib.mk_incr_sssp(h, int(srcs[i]), P_(o0), P_(o1), sp)
+            mk.check(rc, "plain request")
+            if k in (1, 2):
+                n_upd += 1
+                if commit_every and n_upd % commit_every == 0:
+                    mk.check(lib.mk_commit_batch(h, sp), "commit")
+            torch.cuda.synchronize()
+            lat[i] = time.perf_counter() - t0 - arrivals[i]
+        total = time.perf_counter() - t0
+        assert g.last_error() == mk.MK_OK
+        g.close()
+        return total, lat
+
+    def run_served(arrivals, store):
+        g = fresh()
+        srv = mk.Server(g, max_inflight=max_inflight, commit_every=commit_every)
+        lat = np.zeros(N)
+        bad = 0
+        nxt = done = 0
+        t0 = time.perf_counter()
+        while done < N:
+            now = time.perf_counter() - t0
+            while nxt < N and arrivals[nxt] <= now:
+                k, n = int(kinds[nxt]), int(sizes[nxt])
+                a, b, w = inputs(nxt)
+                o0, o1 = outputs(nxt, store)
+                srv.submit(k, a, b, w, n, int(srcs[nxt]), o0, o1, tag=nxt)
+                nxt += 1
+            for tag, st in srv.progress():
+                lat[tag] = time.perf_counter() - t0 - arrivals[tag]
+                bad += st != 0
+                done += 1
+        total = time.perf_counter() - t0
+        srv.close()
+        assert bad == 0, "%d requests refused or failed" % bad
+        assert g.last_error() == mk.MK_OK
+        g.close()
+        return total, lat
+
+    edges = float(sizes.sum())
+
+    def summary(total, lat):
+        return {"seconds": round(total, 3), "requests_per_s": round(N / total, 1),
+                "medges_per_s": round(edges / total / 1e6, 1),
+                "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+
+    out = {"requests": N, "edges": int(edges), "max_inflight": max_inflight, "commit_every": commit_every}
+    zero = np.zeros(N)
+    store_p, store_s = {}, {}
+    tp, lp = run_plain(zero, store_p)
+    ts, ls = run_served(zero, store_s)
+    out["capacity"] = {"plain": summary(tp, lp), "served": summary(ts, ls)}
+    if log:
+        log(out)
+    mism = [i for i in store_p if not all(torch.equal(x, y) for x, y in zip(store_p[i], store_s[i]) if x is not None)]
+    out["compared_requests"] = len(store_p)
+    out["mismatches"] = len(mism)
+    if keep_outputs:
+        out["outputs"] = (store_p, store_s)
+        out["inputs"] = inputs
+    cap = N / tp
+    for frac in rate_fracs:
+        arr = np.cumsum(R.gaps[:N]) / (frac * cap)
+        sp_, ss_ = {}, {}
+        t1, l1 = run_plain(arr, sp_)
+        t2, l2 = run_served(arr, ss_)
+        m = [i for i in sp_ if not all(torch.equal(x, y) for x, y in zip(sp_[i], ss_[i]) if x is not None)]
+        out["rate_%d%%" % round(frac * 100)] = {"rate_req_s": round(frac * cap, 1), "plain": summary(t1, l1),
+                                                "served": summary(t2, l2), "mismatches": len(m)}
+        out["mismatches"] += len(m)
     return out
 
 
@@ -580,6 +766,25 @@ def run_reference(args, world, rank, local):
     }
 
 
+def run_served(args):
+    import torch
+
+    import synth
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    G = synth.powerlaw_graph(scale=21, draws=1 << 25)
+    R = synth.request_stream(100000, G.V, len(G.src))
+    gen_s = time.time() - t0
+    res = serve_experiment(G, R)
+    res.update({"workload": "R-MAT scale 21 graph (V=2,097,152, 2^25 draws, duplicates and self-loops dropped, "
+                            "weights U[1,100]) under a Poisson stream of 100,000 requests: 60% query, 15% insert, "
+                            "15% delete, 10% incremental SSSP from a pool of 16 sources; sizes log-uniform in "
+                            "[1, 2^20]; arrival rates 50% and 90% of the measured plain capacity",
+                "gen_s": round(gen_s, 1)})
+    return res
+
+
 def run_growth(args):
     import torch
 
@@ -600,9 +805,10 @@ def run_growth(args):
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
-    if args.workload == "growth":
+    if args.workload in ("growth", "served"):
         if rank == 0:
-            print(json.dumps(run_growth(args)), flush=True)
+            res = run_growth(args) if args.workload == "growth" else run_served(args)
+            print(json.dumps(res), flush=True)
         return 0
     if args.impl == "reference":
         res = run_reference(args, world, rank, local)

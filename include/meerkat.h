@@ -183,6 +183,109 @@ mk_status mk_query_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_d
  * at their next call. */
 mk_status mk_commit_batch(mk_graph *g, void *stream);
 
+/* ----------------------------------------------- batching and autotuning */
+/*
+ * Batched execution (a project addition; the paper launches one kernel per
+ * batch and reads the frontier size on the host every round).
+ */
+
+/* One query request: n edges, outputs as in mk_query_batch (device
+ * pointers; d_w nullable). */
+typedef struct mk_query_req {
+    const uint32_t *d_src;
+    const uint32_t *d_dst;
+    uint64_t n;
+    uint32_t *d_bitmap;
+    uint32_t *d_w;
+} mk_query_req;
+
+/* Answers every request of the host array h_reqs in ONE persistent launch
+ * (results identical to one mk_query_batch per request).  The descriptors
+ * are copied to the device before the call returns. */
+mk_status mk_query_multi(mk_graph *g, const mk_query_req *h_reqs, uint32_t nreq, void *stream);
+
+/* A batcher captures the multi-request query launch (descriptor copy from
+ * pinned memory + kernel) in a CUDA graph once and replays it for every
+ * group of requests: mk_batcher_add_query queues a request on the host,
+ * mk_batcher_launch enqueues all queued requests as one graph launch on the
+ * batcher's private stream, ordered after `stream`'s prior work and before
+ * its later work.  max_requests bounds one group.  The graph uses the tuning
+ * in force at creation. */
+typedef struct mk_batcher mk_batcher;
+mk_status mk_batcher_create(mk_graph *g, uint32_t max_requests, mk_batcher **out);
+mk_status mk_batcher_destroy(mk_batcher *b);
+mk_status mk_batcher_add_query(mk_batcher *b, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                               uint32_t *d_bitmap, uint32_t *d_w);
+mk_status mk_batcher_launch(mk_batcher *b, void *stream);
+
+/* Kernel shapes: lanes per slab chain in the query kernels (4, 8, 16 or 32:
+ * 32/G words per lane, one vector load each), their block size (128, 256,
+ * 512) and the blocks per SM of the persistent BFS/SSSP round kernel (0 =
+ * occupancy limit).  Timings (ms) are filled by mk_autotune. */
+typedef struct mk_tuning {
+    int query_group;
+    int query_block;
+    int rounds_blocks_per_sm;
+    float query_best_ms;
+    float rounds_best_ms;
+    float query_ms[16];   /* per (group, block) in the order tried */
+    float rounds_ms[8];   /* per blocks-per-SM 1..8 */
+} mk_tuning;
+
+/* Autotuner: times the query kernel on the sample (d_src, d_dst, n) for
+ * every group x block shape and a static BFS from bfs_source for every
+ * blocks-per-SM value, on this graph, and keeps the fastest shapes for this
+ * graph (*out receives them and the timings).  Synchronises `stream`.
+ * Leaves a valid BFS state for bfs_source. */
+mk_status mk_autotune(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n, uint32_t bfs_source,
+                      void *stream, mk_tuning *out);
+mk_status mk_get_tuning(mk_graph *g, mk_tuning *out);
+mk_status mk_set_tuning(mk_graph *g, const mk_tuning *t);
+
+/* ---------------------------------------------------------------- serving */
+/*
+ * Serving engine (a project addition; the paper has no serving layer):
+ * continuous batching of mixed requests on one graph.  Requests are queued in
+ * arrival order by mk_server_submit and admitted by mk_server_progress while
+ * fewer than max_inflight are in flight.  A run of consecutive read requests
+ * (queries, BFS/SSSP) is one group: its queries go out as one CUDA-graph
+ * replay of the multi-request query kernel, its BFS/SSSP calls on a second
+ * stream, overlapping on the device.  An insert or delete is a barrier: it
+ * waits for every earlier read and every later read waits for it, so each
+ * result equals that of running the requests one at a time in arrival
+ * order.  An insert is admitted only if the slab pool has at least n free
+ * slabs (the worst case of one new slab per edge); otherwise it completes
+ * with MK_ERR_POOL_EXHAUSTED and changes nothing.  Every commit_every
+ * updates (0 = never) the server commits the epoch (mk_commit_batch).
+ * Buffers named in a request must stay valid until it completes.
+ */
+enum { MK_REQ_QUERY = 0, MK_REQ_INSERT = 1, MK_REQ_DELETE = 2, MK_REQ_SSSP = 3, MK_REQ_BFS = 4 };
+
+typedef struct mk_request {
+    int kind;               /* MK_REQ_* */
+    const uint32_t *d_src;  /* query / insert / delete: n edges (device) */
+    const uint32_t *d_dst;
+    const uint32_t *d_w;    /* insert weights (nullable = 1) */
+    uint64_t n;
+    uint32_t source;        /* SSSP / BFS source */
+    uint32_t *d_out0;       /* query: bitmap; insert/delete: flags (uint8_t*, nullable); SSSP/BFS: dist */
+    uint32_t *d_out1;       /* query: weights (nullable); SSSP/BFS: parent (nullable) */
+    uint64_t tag;           /* returned on completion */
+} mk_request;
+
+typedef struct mk_server mk_server;
+mk_status mk_server_create(mk_graph *g, uint32_t max_inflight, uint32_t commit_every, mk_server **out);
+mk_status mk_server_destroy(mk_server *s);
+/* Queues one request (host only; nothing is launched). */
+mk_status mk_server_submit(mk_server *s, const mk_request *r);
+/* Retires finished requests, admits and launches queued ones, and reports up
+ * to `cap` completed tags (with their MK_* status, nullable) in completion
+ * order.  Never blocks on the device except to re-read the free pool slab
+ * count when an insert does not fit the running estimate. */
+mk_status mk_server_progress(mk_server *s, uint64_t *done_tags, int *done_status, uint32_t cap, uint32_t *n_done);
+/* Requests queued and requests in flight or finished but not yet reported. */
+mk_status mk_server_pending(mk_server *s, uint64_t *queued, uint64_t *inflight);
+
 /* ------------------------------------------------------------- algorithms */
 
 /* Single-source shortest paths with uint32 weights (paper, Algorithm "SSSP -
@@ -277,8 +380,8 @@ mk_status mk_graph_export(mk_graph *g, uint64_t cap, uint32_t *d_src, uint32_t *
 /* Fills *out (host memory).  Synchronises `stream`. */
 mk_status mk_graph_stats(mk_graph *g, mk_stats *out, void *stream);
 
-/* Synchronises the graph's last stream, returns the sticky device status
- * (MK_OK or an MK_ERR_* code) and clears it. */
+/* Synchronises the device, returns the sticky device status (MK_OK or an
+ * MK_ERR_* code) and clears it. */
 mk_status mk_last_error(mk_graph *g);
 
 /* UpdateIterator marker of slab list `bucket` of vertex v (host outputs):

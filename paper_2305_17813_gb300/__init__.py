@@ -22,7 +22,7 @@ from ._native import (MK_ERR_CUDA, MK_ERR_INTERNAL, MK_ERR_INVALID_ARG, MK_ERR_N
 __all__ = [
     "Graph", "load", "MkError", "MK_OK", "MK_ERR_INVALID_ARG", "MK_ERR_POOL_EXHAUSTED", "MK_ERR_TIMEOUT",
     "MK_ERR_CUDA", "MK_ERR_NO_MEMORY", "MK_ERR_INTERNAL", "MK_NONE", "MK_INVALID_LANE", "bucket_rule",
-    "to_device_u32", "to_numpy_u32",
+    "to_device_u32", "to_numpy_u32", "Batcher", "Server",
 ]
 
 
@@ -202,6 +202,57 @@ class Graph:
         check(self._lib.mk_counters(self._h, buf, 16, 1 if reset else 0, _stream(stream)), "mk_counters")
         return {name: int(buf[i]) for i, name in enumerate(COUNTER_NAMES)}
 
+    # ----------------------------------------------- batching and tuning
+    def query_multi(self, requests, weights: bool = True, stream=None):
+        """Answer a list of (src, dst) requests in one launch; returns a list
+        of (bitmap, weights) like query()."""
+        torch = _torch()
+        from ._native import mk_query_req
+
+        keep, outs = [], []
+        arr = (mk_query_req * max(1, len(requests)))()
+        for i, (src, dst) in enumerate(requests):
+            s, d = to_device_u32(src), to_device_u32(dst)
+            n = s.numel()
+            bm = torch.empty(max(1, (n + 31) // 32), dtype=torch.int32, device=self.device)
+            w = torch.empty(max(1, n), dtype=torch.int32, device=self.device) if weights else None
+            arr[i].d_src, arr[i].d_dst, arr[i].n = s.data_ptr(), d.data_ptr(), n
+            arr[i].d_bitmap = bm.data_ptr()
+            arr[i].d_w = w.data_ptr() if w is not None else None
+            keep.append((s, d))
+            outs.append((bm[:(n + 31) // 32], None if w is None else w[:n]))
+        check(self._lib.mk_query_multi(self._h, arr, len(requests), _stream(stream)), "mk_query_multi")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        del keep
+        return outs
+
+    def autotune(self, src, dst, bfs_source: int, stream=None) -> dict:
+        from ._native import mk_tuning
+
+        s, d = to_device_u32(src), to_device_u32(dst)
+        t = mk_tuning()
+        check(self._lib.mk_autotune(self._h, _ptr(s), _ptr(d), s.numel(), int(bfs_source), _stream(stream),
+                                    ctypes.byref(t)), "mk_autotune")
+        return {"query_group": t.query_group, "query_block": t.query_block,
+                "rounds_blocks_per_sm": t.rounds_blocks_per_sm, "query_best_ms": t.query_best_ms,
+                "rounds_best_ms": t.rounds_best_ms, "query_ms": list(t.query_ms)[:12],
+                "rounds_ms": [x for x in t.rounds_ms if x > 0]}
+
+    def tuning(self) -> dict:
+        from ._native import mk_tuning
+
+        t = mk_tuning()
+        check(self._lib.mk_get_tuning(self._h, ctypes.byref(t)), "mk_get_tuning")
+        return {"query_group": t.query_group, "query_block": t.query_block,
+                "rounds_blocks_per_sm": t.rounds_blocks_per_sm}
+
+    def set_tuning(self, query_group=8, query_block=256, rounds_blocks_per_sm=0):
+        from ._native import mk_tuning
+
+        t = mk_tuning()
+        t.query_group, t.query_block, t.rounds_blocks_per_sm = query_group, query_block, rounds_blocks_per_sm
+        check(self._lib.mk_set_tuning(self._h, ctypes.byref(t)), "mk_set_tuning")
+
     def profile(self, on: bool = True):
         check(self._lib.mk_profile_enable(self._h, 1 if on else 0), "mk_profile_enable")
 
@@ -213,3 +264,86 @@ class Graph:
 
     def launch_count(self) -> int:
         return int(self._lib.mk_launch_count(self._h))
+
+
+class Batcher:
+    """CUDA-graph batcher of query requests (mk_batcher_*)."""
+
+    def __init__(self, graph: "Graph", max_requests: int = 1024):
+        self._lib = graph._lib
+        self.graph = graph
+        h = ctypes.c_void_p()
+        check(self._lib.mk_batcher_create(graph.handle, max_requests, ctypes.byref(h)), "mk_batcher_create")
+        self._h = h
+
+    def add_query(self, src, dst, bitmap, w=None):
+        """src/dst/bitmap/w: device int32 tensors owned by the caller and kept
+        alive until the launch has completed."""
+        check(self._lib.mk_batcher_add_query(self._h, _ptr(src), _ptr(dst), src.numel(), _ptr(bitmap), _ptr(w)),
+              "mk_batcher_add_query")
+
+    def launch(self, stream=None):
+        check(self._lib.mk_batcher_launch(self._h, _stream(stream)), "mk_batcher_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mk_batcher_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving engine (mk_server_*).  Buffers passed to
+    submit() must stay alive until their request is reported done."""
+
+    QUERY, INSERT, DELETE, SSSP, BFS = 0, 1, 2, 3, 4
+
+    def __init__(self, graph: "Graph", max_inflight: int = 64, commit_every: int = 8):
+        self._lib = graph._lib
+        h = ctypes.c_void_p()
+        check(self._lib.mk_server_create(graph.handle, max_inflight, commit_every, ctypes.byref(h)),
+              "mk_server_create")
+        self._h = h
+        self._cap = 4096
+        self._tags = (ctypes.c_uint64 * self._cap)()
+        self._st = (ctypes.c_int * self._cap)()
+
+    def submit(self, kind, src=None, dst=None, w=None, n=0, source=0, out0=None, out1=None, tag=0):
+        from ._native import mk_request
+
+        r = mk_request()
+        r.kind, r.n, r.source, r.tag = int(kind), int(n), int(source), int(tag)
+        r.d_src = None if src is None else src.data_ptr()
+        r.d_dst = None if dst is None else dst.data_ptr()
+        r.d_w = None if w is None else w.data_ptr()
+        r.d_out0 = None if out0 is None else out0.data_ptr()
+        r.d_out1 = None if out1 is None else out1.data_ptr()
+        check(self._lib.mk_server_submit(self._h, ctypes.byref(r)), "mk_server_submit")
+
+    def progress(self):
+        """[(tag, status)] of the requests completed since the last call."""
+        n = ctypes.c_uint32()
+        check(self._lib.mk_server_progress(self._h, self._tags, self._st, self._cap, ctypes.byref(n)),
+              "mk_server_progress")
+        return [(self._tags[i], self._st[i]) for i in range(n.value)]
+
+    def pending(self):
+        q, f = ctypes.c_uint64(), ctypes.c_uint64()
+        check(self._lib.mk_server_pending(self._h, ctypes.byref(q), ctypes.byref(f)), "mk_server_pending")
+        return q.value, f.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mk_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -70,6 +70,26 @@ class mk_stats(ctypes.Structure):
     ]
 
 
+class mk_query_req(ctypes.Structure):
+    _fields_ = [("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("d_bitmap", ctypes.c_void_p), ("d_w", ctypes.c_void_p)]
+
+
+class mk_tuning(ctypes.Structure):
+    _fields_ = [("query_group", ctypes.c_int), ("query_block", ctypes.c_int), ("rounds_blocks_per_sm", ctypes.c_int),
+                ("query_best_ms", ctypes.c_float), ("rounds_best_ms", ctypes.c_float),
+                ("query_ms", ctypes.c_float * 16), ("rounds_ms", ctypes.c_float * 8)]
+
+
+class mk_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p),
+                ("d_w", ctypes.c_void_p), ("n", ctypes.c_uint64), ("source", ctypes.c_uint32),
+                ("d_out0", ctypes.c_void_p), ("d_out1", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+MK_REQ_QUERY, MK_REQ_INSERT, MK_REQ_DELETE, MK_REQ_SSSP, MK_REQ_BFS = 0, 1, 2, 3, 4
+
+
 class mk_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -102,6 +122,19 @@ SIGNATURES = {
     "mk_profile_read": (_INT, [_P, ctypes.POINTER(mk_kernel_time), _INT, ctypes.POINTER(_INT)]),
     "mk_launch_count": (_U64, [_P]),
     "mk_version": (ctypes.c_char_p, []),
+    "mk_server_create": (_INT, [_P, _U32, _U32, ctypes.POINTER(_P)]),
+    "mk_server_destroy": (_INT, [_P]),
+    "mk_server_submit": (_INT, [_P, ctypes.POINTER(mk_request)]),
+    "mk_server_progress": (_INT, [_P, _P, _P, _U32, ctypes.POINTER(_U32)]),
+    "mk_server_pending": (_INT, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    "mk_query_multi": (_INT, [_P, ctypes.POINTER(mk_query_req), _U32, _P]),
+    "mk_batcher_create": (_INT, [_P, _U32, ctypes.POINTER(_P)]),
+    "mk_batcher_destroy": (_INT, [_P]),
+    "mk_batcher_add_query": (_INT, [_P, _P, _P, _U64, _P, _P]),
+    "mk_batcher_launch": (_INT, [_P, _P]),
+    "mk_autotune": (_INT, [_P, _P, _P, _U64, _U32, _P, ctypes.POINTER(mk_tuning)]),
+    "mk_get_tuning": (_INT, [_P, ctypes.POINTER(mk_tuning)]),
+    "mk_set_tuning": (_INT, [_P, ctypes.POINTER(mk_tuning)]),
     "mk_mlp_create": (_INT, [_U64, ctypes.POINTER(_P)]),
     "mk_mlp_destroy": (_INT, [_P]),
     "mk_mlp_num_params": (_INT, []),

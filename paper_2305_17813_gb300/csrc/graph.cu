@@ -104,9 +104,10 @@ __global__ void k_set_vinfo(uint2 *vinfo, const uint32_t *b, const uint64_t *off
         vinfo[v] = make_uint2((uint32_t)off[v], b[v]);
 }
 
-// Per list: its source vertex, marker at lane 0 of its head slab, not updated.
+// Per list: its source vertex (also the owner of its head slab), marker at
+// lane 0 of its head slab, not updated.
 __global__ void k_init_lists(const uint2 *vinfo, uint32_t V, uint32_t *list_src, unsigned long long *lmark,
-                             uint8_t *lupd)
+                             uint8_t *lupd, uint32_t *owner)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V)
@@ -115,6 +116,7 @@ __global__ void k_init_lists(const uint2 *vinfo, uint32_t V, uint32_t *list_src,
     for (uint32_t b = 0; b < vi.y; ++b) {
         const uint32_t l = vi.x + b;
         list_src[l] = v;
+        owner[l] = v;
         lmark[l] = (unsigned long long)l << 32;
         lupd[l] = 0;
     }
@@ -360,7 +362,6 @@ mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out)
     const uint32_t V = cfg->V;
     mk_graph *g = new mk_graph;
     g->vbits = bits_for(V);
-    g->last_stream = s;
     auto fail = [&](mk_status st) {
         mk_graph_destroy(g);
         return st;
@@ -437,6 +438,8 @@ mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out)
     if (st == MK_OK)
         st = device_alloc(g, (void **)&v.lupd, (size_t)H);
     if (st == MK_OK)
+        st = device_alloc(g, (void **)&v.owner, (size_t)(H + P) * 4);
+    if (st == MK_OK)
         st = device_alloc(g, (void **)&g->d_state, sizeof(DevState));
     if (st == MK_OK && cudaMallocHost((void **)&g->h_pinned, 64) != cudaSuccess)
         st = MK_ERR_NO_MEMORY;
@@ -447,7 +450,8 @@ mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out)
     v.st = g->d_state;
     k_set_vinfo<<<grid_for(V, 256), 256, 0, s>>>((uint2 *)v.vinfo, d_b, d_off, V);
     k_init_slabs<<<std::min<uint64_t>(grid_for(H * 32, 256), 152 * 64), 256, 0, s>>>(v.slabs, 0, H);
-    k_init_lists<<<grid_for(V, 256), 256, 0, s>>>(v.vinfo, V, (uint32_t *)v.list_src, v.lmark, v.lupd);
+    cudaMemsetAsync(v.owner + H, 0xFF, (size_t)P * 4, s);
+    k_init_lists<<<grid_for(V, 256), 256, 0, s>>>(v.vinfo, V, (uint32_t *)v.list_src, v.lmark, v.lupd, v.owner);
     k_init_bitmap<<<grid_for(v.pool_words, 256), 256, 0, s>>>(v.bitmap, v.pool_words, v.P);
     cudaMemsetAsync(g->d_state, 0, sizeof(DevState), s);
     g->launches += 5;
@@ -485,6 +489,7 @@ mk_status mk_graph_destroy(mk_graph *g)
     cudaFree((void *)v.list_src);
     cudaFree(v.lmark);
     cudaFree(v.lupd);
+    cudaFree(v.owner);
     cudaFree(g->d_state);
     cudaFree(g->d_kin);
     cudaFree(g->d_kout);
@@ -509,7 +514,6 @@ mk_status mk_commit_batch(mk_graph *g, void *stream)
     if (!g)
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    g->last_stream = s;
     const uint32_t max_hops = g->v.P + 2;
     MK_TRY(timed(g, "update_slab_pointers", s, 2, [&]() {
         k_update_slab_pointers<<<grid_for((uint64_t)g->v.H, 256), 256, 0, s>>>(g->v, max_hops);
@@ -534,7 +538,6 @@ mk_status mk_graph_export(mk_graph *g, uint64_t cap, uint32_t *d_src, uint32_t *
     if (!g || !d_count)
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    g->last_stream = s;
     const uint64_t H = g->v.H;
     const uint32_t max_hops = g->v.P + 2;
     uint32_t *d_cnt = nullptr;
@@ -620,7 +623,9 @@ mk_status mk_last_error(mk_graph *g)
 {
     if (!g)
         return MK_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize(g->last_stream) != cudaSuccess)
+    // the whole device, not a remembered stream: a caller's stream may have
+    // been destroyed since its last use
+    if (cudaDeviceSynchronize() != cudaSuccess)
         return MK_ERR_CUDA;
     int st = 0;
     MK_CUDA(cudaMemcpy(&st, &g->d_state->status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -72,6 +72,7 @@ struct GView {
     uint32_t *slabs;       // (H + P) * 32 words
     uint32_t *bitmap;      // pool occupancy, 1 bit per pool slab
     const uint32_t *list_src; // source vertex of each list
+    uint32_t *owner;       // per slab (heads and pool): source vertex of its list, kNil if unused
     unsigned long long *lmark; // per list: marker slab << 32 | marker lane
     uint8_t *lupd;         // per list: updated since the last commit
     DevState *st;

@@ -49,8 +49,18 @@ int exclusive_sum_launches(uint64_t n);
 
 } // namespace mk
 
+namespace mk {
+// Kernel shapes picked by the autotuner (mk_autotune).
+struct Tuning {
+    int query_group = 8;          // lanes per query chain (4, 8, 16 or 32)
+    int query_block = 256;        // threads per block of the query kernels
+    int rounds_blocks_per_sm = 0; // blocks per SM of the persistent round kernel (0 = occupancy limit)
+};
+} // namespace mk
+
 struct mk_graph {
     mk::GView v{};               // device pointers + sizes
+    mk::Tuning tune{};
     uint32_t vbits = 1;          // bits of a vertex id in a sort key
     mk::DevState *d_state = nullptr;
     uint64_t bytes = 0;          // device bytes held
@@ -66,7 +76,6 @@ struct mk_graph {
     uint64_t epoch = 0, change_seq = 0;
     bool epoch_has_deletes = false;
     std::map<std::pair<int, uint32_t>, mk::Consumer *> consumers;
-    cudaStream_t last_stream = nullptr;
     uint32_t *h_pinned = nullptr; // 16 pinned words for small device->host reads
     // profiling
     bool prof = false;
@@ -127,6 +136,20 @@ inline mk_status timed(mk_graph *g, const char *name, cudaStream_t s, int count,
     return MK_OK;
 }
 
+// Streaming multiprocessors of the current device (queried once).
+inline int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0)
+            sms = 1;
+    }
+    return sms;
+}
+
 inline uint32_t grid_for(uint64_t threads, uint32_t block)
 {
     uint64_t b = (threads + block - 1) / block;
@@ -134,6 +157,8 @@ inline uint32_t grid_for(uint64_t threads, uint32_t block)
 }
 
 mk_status ensure_scratch(mk_graph *g, uint64_t n, cudaStream_t s);
+int rounds_grid(int blocks_per_sm);
+int rounds_max_blocks_per_sm();
 mk_status device_alloc(mk_graph *g, void **p, size_t bytes);
 void device_free(mk_graph *g, void *p, size_t bytes);
 

@@ -92,7 +92,6 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = nullptr;
     MK_TRY(setup_device(&base));
-    g->last_stream = s;
     g->change_seq++;
     if (n == 0)
         return MK_OK;

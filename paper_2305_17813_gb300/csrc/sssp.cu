@@ -294,48 +294,53 @@ __global__ void k_invalidate(const unsigned long long *dlog, const DevState *st,
 }
 
 // After invalidation: relax every edge out of a valid vertex into a vertex
-// invalidated by this call (warp per 32 lists over all lists).  The target
-// test reads the invalidation bitmap, which stays fixed during the pass, so
-// every such edge is relaxed even after another in-neighbour has already
-// given its target a finite distance.  Does nothing if nothing was
-// invalidated.
-__global__ void __launch_bounds__(256) k_relax_into_invalid(RoundArgs a)
+// invalidated by this call.  The target test reads the invalidation bitmap,
+// which stays fixed during the pass, so every such edge is relaxed even after
+// another in-neighbour has already given its target a finite distance; does
+// nothing if nothing was invalidated.  A streaming scan over every slab in
+// use (through the per-slab owner array): a warp reads four consecutive
+// slabs per step and the owner's tree node and the slab load independently.
+__global__ void __launch_bounds__(256) k_relax_into_invalid_slabs(RoundArgs a)
 {
     const GView &g = a.g;
     if (ld_volatile(a.ctr + kInvTotal) == 0)
         return;
-    const uint32_t lane = lane_id(), gi = lane >> 3;
-    const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
-    if (base >= g.H)
-        return;
+    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
+    const uint64_t total = (uint64_t)g.H + g.P;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
     int *overflow = (int *)(a.ctr + kOverflow);
-    const uint64_t l = base + lane;
-    bool todo = false;
-    uint32_t x = 0, dx = kInf32;
-    if (l < g.H) {
-        x = g.list_src[l];
-        dx = node_dist(__ldcg(&a.D[x]));
-        todo = dx != kInf32;
+    unsigned long long slabs = 0, edges = 0, improved = 0, lists = 0;
+    for (uint64_t base = warp0 * 4; base < total; base += nwarps * 4) {
+        const uint64_t s = base + gi;
+        const uint32_t own = s < total ? g.owner[s] : kNil;
+        bool active = own != kNil;
+        uint32_t dx = kInf32;
+        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+        if (active) {
+            if (sub == 0)
+                dx = node_dist(__ldcg(&a.D[own]));
+            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s) + sub * 4));
+        }
+        dx = __shfl_sync(kFull, dx, gbase);
+        slabs += __popc(__ballot_sync(kFull, active && sub == 0));
+        active = active && dx != kInf32;
+        lists += __popc(__ballot_sync(kFull, active && sub == 0));
+        const bool last = sub == 7u;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t y = k ? x.z : x.x, w = k ? x.w : x.y;
+            const bool live = active && !(k && last) && y < kTombKey;
+            edges += __popc(__ballot_sync(kFull, live));
+            const bool target = live && ((a.inv[y >> 5] >> (y & 31)) & 1u);
+            bool up = target && relax(a.D, own, dx, y, a.unit ? 1u : w);
+            up = up && first_this_round(a.stamp, y, round);
+            improved += __popc(__ballot_sync(kFull, up));
+            enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+        }
     }
-    const uint32_t q = __ballot_sync(kFull, todo);
-    unsigned long long slabs = 0, edges = 0, improved = 0;
-    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
-        const uint32_t owner = group_item(q, pass, gi);
-        const bool has = owner < 32;
-        const uint32_t src = __shfl_sync(kFull, x, owner & 31);
-        const uint32_t dsrc = __shfl_sync(kFull, dx, owner & 31);
-        slabs += walk_lists_g8(g, has ? (uint32_t)(base + owner) : kNil, 0, a.max_hops,
-                               [&](uint32_t y, uint32_t w, bool live) {
-                                   edges += __popc(__ballot_sync(kFull, live));
-                                   const bool target = live && ((a.inv[y >> 5] >> (y & 31)) & 1u);
-                                   bool up = target && relax(a.D, src, dsrc, y, a.unit ? 1u : w);
-                                   up = up && first_this_round(a.stamp, y, round);
-                                   improved += __popc(__ballot_sync(kFull, up));
-                                   enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
-                               });
-    }
-    count_add(g.st, kCtrRelaxLists, __popc(q));
+    count_add(g.st, kCtrRelaxLists, lists);
     count_add(g.st, kCtrRelaxSlabs, slabs);
     count_add(g.st, kCtrRelaxEdges, edges);
     count_add(g.st, kCtrRelaxImproved, improved);
@@ -449,25 +454,44 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
     return MK_OK;
 }
 
-// Co-resident grid of k_rounds (blocks per SM x SMs), computed once.
-int rounds_grid()
+} // namespace
+
+namespace mk {
+
+// Co-resident grid of k_rounds: SMs x blocks per SM, the latter the
+// occupancy limit or the tuned value if smaller.
+int rounds_grid(int blocks_per_sm)
 {
-    static int grid = -1;
-    if (grid < 0) {
-        int dev = 0, sms = 0, per_sm = 0;
+    static int sms = 0, per_sm_max = 0;
+    if (!sms) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rounds, 256, 0);
-        grid = std::max(1, sms * std::max(per_sm, 1));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, k_rounds, 256, 0);
+        per_sm_max = std::max(per_sm_max, 1);
     }
-    return grid;
+    const int per = blocks_per_sm > 0 ? std::min(blocks_per_sm, per_sm_max) : per_sm_max;
+    return std::max(1, sms * per);
 }
+
+int rounds_max_blocks_per_sm()
+{
+    rounds_grid(0);
+    int dev = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds, 256, 0);
+    return std::max(per, 1);
+}
+
+} // namespace mk
+
+namespace {
 
 // Runs every round of one phase.  Input: front[0], size in ctr[kCnt0],
 // ctr[kCnt0 + 1] zero.
 mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
 {
-    const int grid = rounds_grid();
+    const int grid = rounds_grid(g->tune.rounds_blocks_per_sm);
     void *args[] = {&a};
     mk_status st = timed(g, name, s, 1, [&]() {
         return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(256), args, 0, s);
@@ -495,7 +519,6 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
 {
     if (!g || source >= g->v.V)
         return MK_ERR_INVALID_ARG;
-    g->last_stream = s;
     Consumer *c = nullptr;
     MK_TRY(get_consumer(g, kind, source, &c));
     const uint32_t V = g->v.V, H = g->v.H;
@@ -536,7 +559,9 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
             a.mode = 0;
             MK_CUDA(cudaMemsetAsync(c->counters + kCnt0, 0, 12, s));
             MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
-                k_relax_into_invalid<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(a);
+                const uint64_t warps = ((uint64_t)H + g->v.P + 3) / 4;
+                const uint32_t grid = (uint32_t)std::min<uint64_t>(grid_for(warps * 32, 256), (uint64_t)num_sms() * 16);
+                k_relax_into_invalid_slabs<<<grid, 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
         }
@@ -561,6 +586,30 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
 }
 
 } // namespace
+
+namespace mk {
+
+// Duration of one static BFS from `source` (CUDA events on s), for the
+// autotuner; leaves a valid BFS state for that source.
+mk_status time_static_bfs(mk_graph *g, uint32_t source, cudaStream_t s, float *ms)
+{
+    Consumer *c = nullptr;
+    MK_TRY(get_consumer(g, kBfs, source, &c));
+    c->epoch = ~0ull;
+    cudaEvent_t a, b;
+    MK_CUDA(cudaEventCreate(&a));
+    MK_CUDA(cudaEventCreate(&b));
+    cudaEventRecord(a, s);
+    mk_status st = run_sssp(g, kBfs, source, nullptr, nullptr, s);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+} // namespace mk
 
 extern "C" {
 

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
         const uint32_t members = __ballot_sync(kFull, e.first && e.list == L) & todo;
         todo &= ~members;
         const bool mine = (members >> lane) & 1u;
+        const uint32_t src_of_list = __shfl_sync(kFull, e.src, leader);
         bool absent = mine;
         // walk the whole chain: a present destination is a duplicate
         uint32_t slab = L, v = 0, em = 0, nxt = kNil, hop = 0;
@@ -192,6 +193,8 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
             else
                 word = (lane & 1) ? kFull : kEmptyKey;
             __stcg(slab_ptr(g, ns) + lane, word);
+            if (lane == 0)
+                g.owner[ns] = src_of_list;
             __threadfence();
             uint32_t old = kNil;
             if (lane == 0)
@@ -209,6 +212,8 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
                 em = __ballot_sync(kFull, is_key_lane(lane) && v == kEmptyKey);
                 nxt = kNil;
             } else {
+                if (lane == 0)
+                    g.owner[ns] = kNil;
                 __threadfence();
                 if (lane == 0)
                     free_slab(g, ns);
@@ -307,7 +312,6 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     if (!g || (n > 0 && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    g->last_stream = s;
     g->change_seq++;
     if (n == 0)
         return MK_OK;
@@ -327,7 +331,6 @@ mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     if (!g || (n > 0 && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    g->last_stream = s;
     g->change_seq++;
     if (n == 0)
         return MK_OK;

@@ -54,6 +54,8 @@ __device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool p
 {
     constexpr uint32_t kSmall = 8;
     const uint32_t lane = lane_id();
+    if (!__any_sync(kFull, pred))
+        return;
     uint2 vi = make_uint2(0, 0);
     if (pred)
         vi = g.vinfo[y];

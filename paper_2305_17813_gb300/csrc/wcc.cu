@@ -18,6 +18,8 @@
 #include "mk_host.h"
 #include "walk.cuh"
 
+#include <algorithm>
+
 using namespace mk;
 
 namespace {
@@ -131,6 +133,38 @@ __global__ void __launch_bounds__(256) k_uf_hook(GView g, uint32_t *p, int all_l
     count_add(g.st, kCtrWccEdges, edges);
 }
 
+// Static pass as a streaming scan over every slab in use (heads and linked
+// pool slabs, found through the per-slab owner array) instead of chain
+// walks: each 8-lane group takes one slab, so a warp reads four consecutive
+// slabs (512 contiguous bytes) per step and no load waits on a next pointer.
+// The slab's owner and its live destinations are united in one
+// group_union2, exactly as in the list walk.
+__global__ void __launch_bounds__(256) k_uf_hook_slabs(GView g, uint32_t *p, int *failed)
+{
+    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u;
+    const uint64_t total = (uint64_t)g.H + g.P;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long slabs = 0, edges = 0;
+    for (uint64_t base = warp0 * 4; base < total; base += nwarps * 4) {
+        const uint64_t s = base + gi;
+        const uint32_t own = s < total ? g.owner[s] : kNil;
+        const bool active = own != kNil;
+        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+        if (active)
+            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s) + sub * 4));
+        slabs += __popc(__ballot_sync(kFull, active && sub == 0));
+        const bool last = sub == 7u;
+        const bool a0 = active && x.x < kTombKey;
+        const bool a1 = last ? active : (active && x.z < kTombKey);
+        edges += __popc(__ballot_sync(kFull, a0)) + __popc(__ballot_sync(kFull, a1 && !last));
+        if (!group_union2(p, x.x, a0, last ? own : x.z, a1, 1u << 20) && lane == 0)
+            *failed = 1;
+    }
+    count_add(g.st, kCtrWccSlabs, slabs);
+    count_add(g.st, kCtrWccEdges, edges);
+}
+
 __global__ void k_uf_compress(uint32_t *p, uint32_t V, uint32_t *label)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,7 +187,6 @@ extern "C" mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream)
     if (!g)
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    g->last_stream = s;
     const uint32_t V = g->v.V, H = g->v.H;
     auto key = std::make_pair((int)kWcc, 0u);
     Consumer *c = nullptr;
@@ -185,10 +218,19 @@ extern "C" mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream)
             return cudaSuccess;
         }));
     }
-    MK_TRY(timed(g, incremental ? "wcc_hook_updated" : "wcc_hook_all", s, 1, [&]() {
-        k_uf_hook<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(g->v, c->uf, incremental ? 0 : 1, max_hops, failed);
-        return cudaSuccess;
-    }));
+    if (incremental) {
+        MK_TRY(timed(g, "wcc_hook_updated", s, 1, [&]() {
+            k_uf_hook<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(g->v, c->uf, 0, max_hops, failed);
+            return cudaSuccess;
+        }));
+    } else {
+        MK_TRY(timed(g, "wcc_hook_all", s, 1, [&]() {
+            const uint64_t warps = ((uint64_t)H + g->v.P + 3) / 4;
+            const uint32_t grid = (uint32_t)std::min<uint64_t>(grid_for(warps * 32, 256), (uint64_t)num_sms() * 16);
+            k_uf_hook_slabs<<<grid, 256, 0, s>>>(g->v, c->uf, failed);
+            return cudaSuccess;
+        }));
+    }
     MK_TRY(timed(g, "wcc_compress", s, 2, [&]() {
         k_uf_compress<<<grid_for(V, 256), 256, 0, s>>>(c->uf, V, d_label);
         k_uf_failed<<<1, 1, 0, s>>>(failed, g->d_state);

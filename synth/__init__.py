@@ -325,3 +325,39 @@ def growth_stream(scale: int = 22, draws: int = 1 << 26, n_batches: int = 64, de
         used += nd
         batches.append(Batch(ins_src=bs, ins_dst=bd, ins_w=bw, del_src=s[di].copy(), del_dst=d[di].copy()))
     return Batch(V=V, scale=scale, init=init, batches=batches)
+
+
+def request_stream(n_req: int, V: int, n_edges: int, mix=(0.6, 0.15, 0.15, 0.1), lo: int = 1, hi: int = 1 << 20,
+                   n_sources: int = 16, query_pool: int = 1 << 21, insert_pool: int = 1 << 22,
+                   seed: int = 3000) -> Batch:
+    """Mixed request stream for the serving workload (seed `seed`).
+
+    kinds: 0 query, 1 insert, 2 delete, 3 incremental SSSP with probabilities
+    `mix`; sizes log-uniform in [lo, hi] (update and query requests);
+    SSSP sources drawn from a fixed pool of n_sources random vertices (so a
+    source recurs and its tree is kept incrementally); `gaps`: unit-rate
+    exponential inter-arrival times (scale by 1 / rate).  Request inputs are
+    slices of pools: queries at a random offset of a query pool, inserts at
+    a random offset of an insert pool, deletes at consecutive offsets of a
+    fixed permutation of the initial edges (so they hit live edges until it
+    wraps around)."""
+    u = np.frombuffer(np.ascontiguousarray(weights(n_req, substream(seed, TAG_PAIRS), 0, 999999)).tobytes(),
+                      np.uint32).astype(np.float64) / 1e6
+    cum = np.cumsum(mix)
+    kind = np.searchsorted(cum, u, side="right").astype(np.uint8)
+    kind = np.minimum(kind, 3)
+    size = log_uniform(n_req, lo, hi, substream(seed, TAG_W)).astype(np.int64)
+    srcs = uniform_pairs(V, n_sources, substream(seed, TAG_LONG))[0]
+    pick = weights(n_req, substream(seed, TAG_LOCAL), 0, n_sources - 1)
+    source = srcs[pick]
+    off_raw = uniform_pairs(0xFFFFFFFF, n_req, substream(seed, TAG_QRY))[0].astype(np.int64)
+    offset = np.zeros(n_req, np.int64)
+    q = kind == 0
+    offset[q] = off_raw[q] % np.maximum(query_pool - size[q], 1)
+    ins = kind == 1
+    offset[ins] = off_raw[ins] % np.maximum(insert_pool - size[ins], 1)
+    dl = kind == 2
+    offset[dl] = (np.cumsum(np.where(dl, size, 0)) - size)[dl] % max(1, n_edges)
+    size[kind == 3] = 0
+    gaps = exponential_gaps(n_req, 1.0, substream(seed, TAG_QPERM))
+    return Batch(kind=kind, size=size, source=source, offset=offset, gaps=gaps, sources=srcs)
