@@ -54,10 +54,11 @@ def parse_args(argv=None):
     p.add_argument("--draws", type=int, default=1 << 24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", choices=["powerlaw", "growth", "served"], default="powerlaw",
+    p.add_argument("--workload", choices=["powerlaw", "growth", "served", "road"], default="powerlaw",
                    help="powerlaw: the benchmark line; growth: the learned-sizing study on the R-MAT "
                         "scale-22 growth stream; served: plain vs continuous-batching serving on the R-MAT "
-                        "scale-21 request stream (each prints its own JSON line)")
+                        "scale-21 request stream; road: incremental SSSP on the 4096^2 road-like grid "
+                        "(each prints its own JSON line)")
     return p.parse_args(argv)
 
 
@@ -785,6 +786,65 @@ def run_served(args):
     return res
 
 
+def run_road(args):
+    """Road-like workload: 4,096 x 4,096 grid + 0.1% long-range edges, 64
+    mixed batches of 2^16 (half deletes of grid links, half inserts), the
+    incremental SSSP from the corner vertex after each batch."""
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+    import synth
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    R = synth.road_graph(4096, 4096)
+    batches = [synth.road_batch(R, k) for k in range(64)]
+    gen_s = time.time() - t0
+    g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + 64 * (1 << 16), buckets=1)
+    chunk = 1 << 22
+    for i in range(0, len(R.src), chunk):
+        g.insert(R.src[i:i + chunk], R.dst[i:i + chunk], R.w[i:i + chunk], flags=False)
+    g.commit()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    g.sssp(0)
+    ev[1].record()
+    torch.cuda.synchronize()
+    static_ms = ev[0].elapsed_time(ev[1])
+    g.commit()
+    dev = [{k: mk.to_device_u32(b[k]) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst")} for b in batches]
+    sssp_ms, del_ms, ins_ms = [], [], []
+    for k in range(64):
+        b = dev[k]
+        ev[0].record()
+        g.delete(b["del_src"], b["del_dst"], flags=False)
+        ev[1].record()
+        g.insert(b["ins_src"], b["ins_dst"], b["ins_w"], flags=False)
+        ev[2].record()
+        g.sssp(0)
+        ev[3].record()
+        g.commit()
+        torch.cuda.synchronize()
+        del_ms.append(ev[0].elapsed_time(ev[1]))
+        ins_ms.append(ev[1].elapsed_time(ev[2]))
+        sssp_ms.append(ev[2].elapsed_time(ev[3]))
+    if g.last_error() != mk.MK_OK:
+        raise RuntimeError("device status in the road run")
+    nd, ni = len(batches[0]["del_src"]), len(batches[0]["ins_src"])
+    g.close()
+    return {"workload": "4,096 x 4,096 road-like grid (67,092,480 grid edges + 67,092 long-range edges, weights "
+                        "U[1,1000]); 64 mixed batches of 2^16 (2^15 deletes of grid links, 2^15 inserts); "
+                        "incremental SSSP from vertex 0 after each batch",
+            "static_sssp_ms": round(static_ms, 2),
+            "incr_sssp_ms_mean": round(statistics.mean(sssp_ms), 3),
+            "incr_sssp_ms_p50": round(statistics.median(sssp_ms), 3),
+            "incr_sssp_ms_max": round(max(sssp_ms), 3),
+            "delete_medges_s": round(nd / statistics.mean(del_ms) / 1e3, 1),
+            "insert_medges_s": round(ni / statistics.mean(ins_ms) / 1e3, 1),
+            "gen_s": round(gen_s, 1)}
+
+
 def run_growth(args):
     import torch
 
@@ -805,9 +865,9 @@ def run_growth(args):
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
-    if args.workload in ("growth", "served"):
+    if args.workload in ("growth", "served", "road"):
         if rank == 0:
-            res = run_growth(args) if args.workload == "growth" else run_served(args)
+            res = {"growth": run_growth, "served": run_served, "road": run_road}[args.workload](args)
             print(json.dumps(res), flush=True)
         return 0
     if args.impl == "reference":

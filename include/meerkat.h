@@ -380,6 +380,10 @@ mk_status mk_graph_export(mk_graph *g, uint64_t cap, uint32_t *d_src, uint32_t *
 /* Fills *out (host memory).  Synchronises `stream`. */
 mk_status mk_graph_stats(mk_graph *g, mk_stats *out, void *stream);
 
+/* Free slabs of the pool (an exact device counter kept with the bitmap:
+ * one word is read).  Synchronises `stream`. */
+mk_status mk_pool_free(mk_graph *g, uint64_t *out, void *stream);
+
 /* Synchronises the device, returns the sticky device status (MK_OK or an
  * MK_ERR_* code) and clears it. */
 mk_status mk_last_error(mk_graph *g);

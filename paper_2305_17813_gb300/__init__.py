@@ -186,6 +186,11 @@ class Graph:
         check(self._lib.mk_graph_stats(self._h, ctypes.byref(st), _stream(stream)), "mk_graph_stats")
         return {f: getattr(st, f) for f, _ in mk_stats._fields_}
 
+    def pool_free(self, stream=None) -> int:
+        v = ctypes.c_uint64()
+        check(self._lib.mk_pool_free(self._h, ctypes.byref(v), _stream(stream)), "mk_pool_free")
+        return v.value
+
     def last_error(self) -> int:
         return int(self._lib.mk_last_error(self._h))
 

@@ -116,6 +116,7 @@ SIGNATURES = {
     "mk_graph_export": (_INT, [_P, _U64, _P, _P, _P, _P, _P]),
     "mk_graph_stats": (_INT, [_P, ctypes.POINTER(mk_stats), _P]),
     "mk_last_error": (_INT, [_P]),
+    "mk_pool_free": (_INT, [_P, ctypes.POINTER(_U64), _P]),
     "mk_list_marker": (_INT, [_P, _U32, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32), ctypes.POINTER(_U32), _P]),
     "mk_counters": (_INT, [_P, ctypes.POINTER(_U64), _INT, _INT, _P]),
     "mk_profile_enable": (_INT, [_P, _INT]),

@@ -671,6 +671,18 @@ mk_status mk_counters(mk_graph *g, uint64_t *out, int n, int reset, void *stream
     return MK_OK;
 }
 
+mk_status mk_pool_free(mk_graph *g, uint64_t *out, void *stream)
+{
+    if (!g || !out)
+        return MK_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long used = 0;
+    MK_CUDA(cudaMemcpyAsync(&used, &g->d_state->pool_used, 8, cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    *out = used >= g->v.P ? 0 : g->v.P - used;
+    return MK_OK;
+}
+
 mk_status mk_profile_enable(mk_graph *g, int on)
 {
     if (!g)

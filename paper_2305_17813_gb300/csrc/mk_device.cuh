@@ -55,10 +55,9 @@ enum Counter {
 
 // Mutable device-side state of one graph (one allocation).
 struct DevState {
-    int status;            // sticky error word
-    uint32_t reserved;
-    uint32_t dlog_count;   // entries in the delete log
-    uint32_t pad0;
+    int status;                    // sticky error word
+    uint32_t dlog_count;           // entries in the delete log
+    unsigned long long pool_used;  // pool slabs allocated (kept with the bitmap)
     unsigned long long ctr[kNumCounters];
 };
 
@@ -194,6 +193,8 @@ __device__ __forceinline__ uint32_t alloc_slab(const GView &g, uint32_t salt)
                 else
                     word = old | (1u << b);
             }
+            if (got != kNil)
+                atomicAdd(&g.st->pool_used, 1ull);
             got = __shfl_sync(kFull, got, l);
             if (got != kNil)
                 return got;
@@ -207,6 +208,7 @@ __device__ __forceinline__ void free_slab(const GView &g, uint32_t s)
 {
     const uint32_t i = s - g.H;
     atomicAnd(&g.bitmap[i >> 5], ~(1u << (i & 31)));
+    atomicAdd(&g.st->pool_used, ~0ull);
 }
 
 } // namespace mk

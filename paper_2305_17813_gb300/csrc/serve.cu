@@ -69,9 +69,9 @@ bool is_read(int kind) { return kind == MK_REQ_QUERY || kind == MK_REQ_SSSP || k
 // Free pool slabs, read exactly (synchronises).
 mk_status refresh_pool(mk_server *s)
 {
-    mk_stats st;
-    MK_TRY(mk_graph_stats(s->g, &st, s->su));
-    s->pool_free_est = st.pool_slabs - st.pool_used;
+    uint64_t free_slabs = 0;
+    MK_TRY(mk_pool_free(s->g, &free_slabs, s->su));
+    s->pool_free_est = free_slabs;
     return MK_OK;
 }
 
@@ -79,41 +79,53 @@ mk_status refresh_pool(mk_server *s)
 mk_status launch_reads(mk_server *s, uint32_t room)
 {
     Group grp;
-    bool any_q = false, any_s = false;
-    if (s->have_update) {
-        MK_CUDA(cudaStreamWaitEvent(s->sq, s->last_update, 0));
-        MK_CUDA(cudaStreamWaitEvent(s->ss, s->last_update, 0));
-    }
+    // the group: the reads at the head of the queue
+    std::vector<mk_request> reqs;
+    uint32_t n_query = 0;
     while (room && !s->queue.empty() && is_read(s->queue.front().kind)) {
-        const mk_request r = s->queue.front();
+        reqs.push_back(s->queue.front());
+        n_query += reqs.back().kind == MK_REQ_QUERY;
         s->queue.pop_front();
         --room;
+    }
+    const bool any_q = n_query > 0, any_s = reqs.size() > n_query;
+    if (s->have_update) {
+        if (any_q)
+            MK_CUDA(cudaStreamWaitEvent(s->sq, s->last_update, 0));
+        if (any_s)
+            MK_CUDA(cudaStreamWaitEvent(s->ss, s->last_update, 0));
+    }
+    for (const mk_request &r : reqs) {
         int st = MK_OK;
-        if (r.kind == MK_REQ_QUERY) {
+        if (r.kind == MK_REQ_QUERY && n_query == 1) {
+            // a lone query needs no merging: one direct launch
+            st = mk_query_batch(s->g, r.d_src, r.d_dst, r.n, r.d_out0, r.d_out1, s->sq);
+        } else if (r.kind == MK_REQ_QUERY) {
             st = mk_batcher_add_query(s->batcher, r.d_src, r.d_dst, r.n, r.d_out0, r.d_out1);
             if (st == MK_ERR_INVALID_ARG && r.n) { // batcher full: flush and retry
                 MK_TRY(mk_batcher_launch(s->batcher, s->sq));
                 st = mk_batcher_add_query(s->batcher, r.d_src, r.d_dst, r.n, r.d_out0, r.d_out1);
             }
-            any_q = true;
             s->merged_queries++;
         } else {
             st = r.kind == MK_REQ_SSSP ? mk_incr_sssp(s->g, r.source, r.d_out0, r.d_out1, s->ss)
                                        : mk_incr_bfs(s->g, r.source, r.d_out0, r.d_out1, s->ss);
-            any_s = true;
         }
         grp.tags.push_back(r.tag);
         grp.status.push_back(st);
     }
-    if (any_q)
+    if (n_query > 1)
         MK_TRY(mk_batcher_launch(s->batcher, s->sq));
-    grp.done_q = ev(s);
-    grp.done_s = ev(s);
-    MK_CUDA(cudaEventRecord(grp.done_q, s->sq));
-    MK_CUDA(cudaEventRecord(grp.done_s, s->ss));
-    (void)any_s;
-    s->reads_since_update.push_back(grp.done_q);
-    s->reads_since_update.push_back(grp.done_s);
+    if (any_q) {
+        grp.done_q = ev(s);
+        MK_CUDA(cudaEventRecord(grp.done_q, s->sq));
+        s->reads_since_update.push_back(grp.done_q);
+    }
+    if (any_s) {
+        grp.done_s = ev(s);
+        MK_CUDA(cudaEventRecord(grp.done_s, s->ss));
+        s->reads_since_update.push_back(grp.done_s);
+    }
     s->inflight += (uint32_t)grp.tags.size();
     s->flight.push_back(std::move(grp));
     s->groups++;

@@ -45,9 +45,15 @@ enum {
     kInvTotal = 4,
     kRoundsDone = 5,
     kClearWords = 8,  // words [0, 8) are cleared at the start of every call
+    kSoloR = 6,       // round index reached by a solo phase of block 0
     kRid = 8,         // last round stamp used (kept across calls)
     kBar = 10         // grid barrier: arrival count, generation
 };
+// A frontier of at most kSoloLists lists is processed by block 0 alone, with
+// block-level barriers between rounds, for at most kSoloRounds rounds in a
+// row (so the other blocks' bounded wait at the grid barrier never expires).
+constexpr uint32_t kSoloLists = 1024;
+constexpr uint32_t kSoloRounds = 4096;
 
 __device__ __forceinline__ uint32_t node_dist(unsigned long long d) { return (uint32_t)(d >> 32); }
 __device__ __forceinline__ uint32_t node_parent(unsigned long long d) { return (uint32_t)d; }
@@ -104,17 +110,22 @@ __device__ void relax_body(const RoundArgs &a, const uint32_t *F, uint32_t n, ui
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
     for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
         const uint64_t i = base + lane;
-        const bool todo = i < n;
+        bool todo = i < n;
+        // each lane fetches its own list's source and distance up front
         const uint32_t mine = todo ? F[i] : 0;
+        const uint32_t my_x = todo ? g.list_src[mine] : 0;
+        const uint32_t my_dx = todo ? node_dist(__ldcg(&a.D[my_x])) : kInf32;
+        lists += __popc(__ballot_sync(kFull, todo));
+        todo = todo && my_dx != kInf32;
         const uint32_t q = __ballot_sync(kFull, todo);
-        lists += __popc(q);
         for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
             const uint32_t owner = group_item(q, pass, gi);
             const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
             const bool has = owner < 32;
-            const uint32_t x = has ? g.list_src[L] : 0;
-            const uint32_t dx = has ? node_dist(__ldcg(&a.D[x])) : kInf32;
-            slabs += walk_lists_g8(g, dx != kInf32 ? L : kNil, 0, a.max_hops,
+            const uint32_t x = __shfl_sync(kFull, my_x, owner & 31);
+            const uint32_t dx0 = __shfl_sync(kFull, my_dx, owner & 31);
+            const uint32_t dx = has ? dx0 : kInf32;
+            slabs += walk_lists_g8(g, has ? L : kNil, 0, a.max_hops,
                                    [&](uint32_t y, uint32_t w, bool live) {
                                        edges += __popc(__ballot_sync(kFull, live));
                                        bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
@@ -144,12 +155,13 @@ __device__ void invalidate_body(const RoundArgs &a, const uint32_t *F, uint32_t 
         const uint64_t i = base + lane;
         const bool todo = i < n;
         const uint32_t mine = todo ? F[i] : 0;
+        const uint32_t my_x = todo ? g.list_src[mine] : 0;
         const uint32_t q = __ballot_sync(kFull, todo);
         for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
             const uint32_t owner = group_item(q, pass, gi);
             const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
             const bool has = owner < 32;
-            const uint32_t x = has ? g.list_src[L] : 0;
+            const uint32_t x = __shfl_sync(kFull, my_x, owner & 31);
             slabs += walk_lists_g8(g, has ? L : kNil, 0, a.max_hops, [&](uint32_t y, uint32_t, bool live) {
                 bool hit = false;
                 if (live && y != a.source) {
@@ -168,16 +180,17 @@ __device__ void invalidate_body(const RoundArgs &a, const uint32_t *F, uint32_t 
     count_add(g.st, kCtrInvalidSlabs, slabs);
 }
 
-// Round r of a phase: reads the size in ctr[kCnt0 + r % 3], appends to
-// ctr[kCnt0 + (r+1) % 3] and clears ctr[kCnt0 + (r+2) % 3] for round r+1.
+// Round r of a phase: reads the size in cnts[r % 3], appends to
+// cnts[(r+1) % 3] and clears cnts[(r+2) % 3] for round r+1 (cnts: the three
+// global counters, or block 0's shared copies during a solo phase).
 // Frontier r is front[r & 1].
-__device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t r, uint32_t n, uint64_t warp0, uint64_t nwarps,
-                                           uint32_t rid)
+__device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t *cnts, uint32_t r, uint32_t n, uint64_t warp0,
+                                           uint64_t nwarps, uint32_t rid)
 {
     const uint32_t in = r & 1;
     if (blockIdx.x == 0 && threadIdx.x == 0)
-        a.ctr[kCnt0 + (r + 2) % 3] = 0;
-    uint32_t *cnt = a.ctr + kCnt0 + (r + 1) % 3;
+        cnts[(r + 2) % 3] = 0;
+    uint32_t *cnt = cnts + (r + 1) % 3;
     if (a.mode == 0)
         relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps);
     else
@@ -219,23 +232,70 @@ __device__ bool grid_barrier(uint32_t *bar)
 } // namespace
 
 // All rounds of one phase in one cooperative launch.  The phase input is
-// front[0] with its size in ctr[kCnt0]; ctr[kCnt0 + 1] must be zero.
+// front[0] with its size in ctr[kCnt0]; ctr[kCnt0 + 1] must be zero.  Large
+// frontiers are processed by the whole grid, one grid barrier per round.
+// While the frontier stays small, block 0 runs the rounds alone (its warps
+// striding over the frontier, its frontier sizes in shared memory,
+// __syncthreads between rounds) for at most kSoloRounds rounds; the solo
+// phase sits between two grid barriers, so no block reads a global size
+// while block 0 changes them, and the others wait at one barrier instead of
+// one per round.
 __global__ void __launch_bounds__(256) k_rounds(RoundArgs a)
 {
+    __shared__ uint32_t solo_cnt[3];
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t rid = ld_volatile(a.ctr + kRid);
+    uint32_t *gcnt = a.ctr + kCnt0;
     uint32_t r = 0;
     bool ok = true;
-    for (; r < a.max_rounds; ++r) {
-        const uint32_t n = ld_volatile(a.ctr + kCnt0 + r % 3);
+    while (r < a.max_rounds) {
+        uint32_t n = ld_volatile(gcnt + r % 3);
         if (n == 0)
             break;
-        round_step(a, r, n, warp0, nwarps, rid);
+        if (n > kSoloLists) {
+            round_step(a, gcnt, r, n, warp0, nwarps, rid);
+            if (!grid_barrier(a.ctr + kBar)) {
+                ok = false;
+                break;
+            }
+            ++r;
+            continue;
+        }
+        // every block has read n: block 0 may now change the global sizes
         if (!grid_barrier(a.ctr + kBar)) {
             ok = false;
             break;
         }
+        if (blockIdx.x == 0) {
+            const uint64_t bw0 = threadIdx.x >> 5, bnw = blockDim.x >> 5;
+            if (threadIdx.x == 0) {
+                solo_cnt[r % 3] = n;
+                solo_cnt[(r + 1) % 3] = 0;
+                solo_cnt[(r + 2) % 3] = 0;
+            }
+            __syncthreads();
+            uint32_t steps = 0;
+            do {
+                round_step(a, solo_cnt, r, n, bw0, bnw, rid);
+                __syncthreads();
+                ++r;
+                ++steps;
+                n = *(volatile uint32_t *)&solo_cnt[r % 3];
+                __syncthreads();
+            } while (n > 0 && n <= kSoloLists && steps < kSoloRounds && r < a.max_rounds);
+            if (threadIdx.x == 0) {
+                gcnt[r % 3] = n;
+                gcnt[(r + 1) % 3] = 0;
+                gcnt[(r + 2) % 3] = 0;
+                a.ctr[kSoloR] = r;
+            }
+        }
+        if (!grid_barrier(a.ctr + kBar)) {
+            ok = false;
+            break;
+        }
+        r = ld_volatile(a.ctr + kSoloR);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr[kRoundsDone] = r;
@@ -249,7 +309,7 @@ __global__ void __launch_bounds__(256) k_round_once(RoundArgs a, uint32_t r, uin
 {
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    round_step(a, r, n, warp0, nwarps, ld_volatile(a.ctr + kRid));
+    round_step(a, a.ctr + kCnt0, r, n, warp0, nwarps, ld_volatile(a.ctr + kRid));
     if (blockIdx.x == 0 && threadIdx.x == 0)
         a.ctr[kRoundsDone] = r + 1;
 }
@@ -359,11 +419,13 @@ __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
     int *overflow = (int *)(a.ctr + kOverflow);
     const uint64_t l = base + lane;
     bool todo = false;
-    uint32_t x = 0, dx = kInf32;
+    uint32_t x = 0, dx = kInf32, my_first = 0, my_start = kNil;
     if (l < g.H && g.lupd[l]) {
         x = g.list_src[l];
         dx = node_dist(__ldcg(&a.D[x]));
         todo = dx != kInf32;
+        if (todo)
+            my_start = update_begin(g, (uint32_t)l, &my_first);
     }
     const uint32_t q = __ballot_sync(kFull, todo);
     unsigned long long slabs = 0, edges = 0, improved = 0;
@@ -372,9 +434,9 @@ __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
         const bool has = owner < 32;
         const uint32_t src = __shfl_sync(kFull, x, owner & 31);
         const uint32_t dsrc = __shfl_sync(kFull, dx, owner & 31);
-        uint32_t first_lane = 0, start = kNil;
-        if (has)
-            start = update_begin(g, (uint32_t)(base + owner), &first_lane);
+        const uint32_t first_lane = __shfl_sync(kFull, my_first, owner & 31);
+        const uint32_t start0 = __shfl_sync(kFull, my_start, owner & 31);
+        const uint32_t start = has ? start0 : kNil;
         slabs += walk_lists_g8(g, start, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
             edges += __popc(__ballot_sync(kFull, live));
             bool up = live && relax(a.D, src, dsrc, y, a.unit ? 1u : w);

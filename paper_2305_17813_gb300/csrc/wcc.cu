@@ -97,16 +97,21 @@ __global__ void __launch_bounds__(256) k_uf_hook(GView g, uint32_t *p, int all_l
         return;
     const uint64_t l = base + lane;
     const bool todo = l < g.H && (all_lists || g.lupd[l]);
+    // each lane fetches its own list's source and walk start up front
+    uint32_t my_src = 0, my_first = 0, my_start = kNil;
+    if (todo) {
+        my_src = g.list_src[l];
+        my_start = all_lists ? (uint32_t)l : update_begin(g, (uint32_t)l, &my_first);
+    }
     const uint32_t q = __ballot_sync(kFull, todo);
     unsigned long long slabs = 0, edges = 0;
     for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
         const uint32_t owner = group_item(q, pass, gi);
         const bool has = owner < 32;
-        const uint32_t L = (uint32_t)(base + (owner & 31));
-        const uint32_t src = has ? g.list_src[L] : 0;
-        uint32_t first_lane = 0, slab = kNil;
-        if (has)
-            slab = all_lists ? L : update_begin(g, L, &first_lane);
+        const uint32_t src = __shfl_sync(kFull, my_src, owner & 31);
+        uint32_t first_lane = __shfl_sync(kFull, my_first, owner & 31);
+        const uint32_t start0 = __shfl_sync(kFull, my_start, owner & 31);
+        uint32_t slab = has ? start0 : kNil;
         bool active = slab != kNil;
         for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
             uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);

@@ -151,3 +151,34 @@ def test_power_law_with_bucket_rule(cuda_lib):
     g.commit()
     bm, _ = g.query(B.q_src, B.q_dst)
     assert np.array_equal(mk.to_numpy_u32(bm), o.query(B.q_src, B.q_dst)[0])
+
+
+def test_long_path_and_mixed_frontier_sizes(cuda_lib):
+    """A 9,000-vertex path (thousands of one-list rounds, more than one
+    solo phase of the round kernel) feeding a dense random block (frontiers
+    of thousands of lists), then a delete that cuts the path in the middle."""
+    mk = _mk()
+    P = 9000
+    B = 4000
+    rng = np.random.default_rng(5)
+    V = P + B
+    ps = np.arange(P - 1, dtype=np.uint32)
+    pd = ps + 1
+    bs = rng.integers(P, V, 120000).astype(np.uint32)
+    bd = rng.integers(P, V, 120000).astype(np.uint32)
+    s = np.concatenate([ps, [P - 1], bs]).astype(np.uint32)
+    d = np.concatenate([pd, [P], bd]).astype(np.uint32)
+    w = rng.integers(1, 9, len(s)).astype(np.uint32)
+    g = mk.Graph(V, edge_capacity_hint=len(s) * 2, buckets=1)
+    o = oracle.OracleGraph(V)
+    g.insert(s, d, w)
+    o.insert(s, d, w)
+    check_algos(g, o, [0], wcc=True)
+    g.commit()
+    for x in (g, o):
+        x.delete([P // 2], [P // 2 + 1])
+    check_algos(g, o, [0], wcc=True)
+    g.commit()
+    for x in (g, o):
+        x.insert([P // 2], [P // 2 + 1], [3])
+    check_algos(g, o, [0], wcc=True)

@@ -115,6 +115,8 @@ def test_hub_list_appended_by_many_warps(cuda_lib):
                    ("ins", (hub, d, w)), ("qry", (s, dd))])
     st = g.stats()
     assert st["chain_max"] >= 3000 // 15
+    # the device pool counter agrees with the bitmap after CAS-link races
+    assert g.pool_free() == st["pool_slabs"] - st["pool_used"]
 
 
 def test_duplicates_first_occurrence_and_repeated_deletes(cuda_lib):
@@ -189,6 +191,7 @@ def test_pool_exhaustion_applies_flagged_edges_only(cuda_lib):
     st = g.stats()
     assert st["live_edges"] == int(f.sum())
     assert st["pool_used"] <= 32
+    assert g.pool_free() == st["pool_slabs"] - st["pool_used"]
 
 
 def test_update_slab_pointers_figure_cases(cuda_lib):
