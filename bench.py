@@ -190,11 +190,13 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
         return launches * n_per_launch * (12 + 32 + 32) + 128 * (ctr["insert_slabs"] + ctr["insert_new_slabs"])
     if family == "delete":
         return launches * n_per_launch * (8 + 32 + 32) + 128 * ctr["delete_slabs"]
-    if family == "sssp_round":
+    if family == "sssp_rounds":
         return (ctr["relax_lists"] * (4 + 4 + 8) + 128 * ctr["relax_slabs"] + 16 * ctr["relax_edges"]
                 + ctr["relax_improved"] * (8 + 4 + 8))
-    if family in ("wcc_hook_all", "wcc_hook_updated"):
+    if family == "wcc_hook_all":
         return 128 * ctr["wcc_slabs"] + 16 * ctr["wcc_edges"]
+    if family == "wcc_hook_updated":
+        return 128 * ctr["wcc_upd_slabs"] + 16 * ctr["wcc_upd_edges"]
     return None
 
 

@@ -397,10 +397,14 @@ mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *sla
 
 /* Work counters accumulated by the kernels since the last reset, in this
  * order: query slabs loaded, insert slabs loaded, insert slabs linked,
- * delete slabs loaded, relaxed lists, relaxation slabs loaded, live edges
- * relaxed, improved vertices, invalidation slabs loaded, WCC slabs loaded,
- * WCC edges united, commit slabs loaded (then 4 reserved).  Copies up to n
- * (<= 16) values to out (host); reset != 0 zeroes them.  Synchronises
+ * delete slabs loaded; BFS/SSSP rounds: relaxed lists, slabs loaded, live
+ * edges relaxed, improved vertices; vertices invalidated by deletions; WCC
+ * slabs loaded, WCC edges united, commit slabs loaded; BFS/SSSP prologue
+ * kernels (inserted-edge and invalidated-target seeds): lists, slabs loaded,
+ * live edges relaxed, improved vertices; incremental WCC pass: slabs loaded,
+ * edges united; BFS/SSSP rounds and grid barriers of the round kernel (then
+ * reserved words up to 32).  Copies up to n
+ * (<= 32) values to out (host); reset != 0 zeroes them.  Synchronises
  * `stream`. */
 mk_status mk_counters(mk_graph *g, uint64_t *out, int n, int reset, void *stream);
 

@@ -203,8 +203,8 @@ class Graph:
     def counters(self, reset: bool = False, stream=None) -> dict:
         from ._native import COUNTER_NAMES
 
-        buf = (ctypes.c_uint64 * 16)()
-        check(self._lib.mk_counters(self._h, buf, 16, 1 if reset else 0, _stream(stream)), "mk_counters")
+        buf = (ctypes.c_uint64 * 32)()
+        check(self._lib.mk_counters(self._h, buf, 32, 1 if reset else 0, _stream(stream)), "mk_counters")
         return {name: int(buf[i]) for i, name in enumerate(COUNTER_NAMES)}
 
     # ----------------------------------------------- batching and tuning

@@ -25,7 +25,9 @@ MK_NOALLOC_MAX_BATCH = 65536
 MK_MLP_NPARAMS = 4801
 
 COUNTER_NAMES = ["query_slabs", "insert_slabs", "insert_new_slabs", "delete_slabs", "relax_lists", "relax_slabs",
-                 "relax_edges", "relax_improved", "invalidate_slabs", "wcc_slabs", "wcc_edges", "commit_slabs"]
+                 "relax_edges", "relax_improved", "invalidated", "wcc_slabs", "wcc_edges", "commit_slabs",
+                 "seed_lists", "seed_slabs", "seed_edges", "seed_improved", "wcc_upd_slabs", "wcc_upd_edges",
+                 "rounds", "grid_barriers"]
 
 STATUS_NAMES = {
     MK_OK: "MK_OK",

@@ -316,12 +316,13 @@ static uint32_t bits_for(uint32_t V)
 
 static void destroy_consumer(mk_graph *g, Consumer *c)
 {
-    size_t V = g->v.V;
+    const size_t V = g->v.V, H = g->v.H;
     device_free(g, c->D, V * 8);
-    device_free(g, c->front[0], V * 4);
-    device_free(g, c->front[1], V * 4);
+    device_free(g, c->front[0], H * 8);
+    device_free(g, c->front[1], H * 8);
     device_free(g, c->stamp, V * 4);
     device_free(g, c->inv, (V + 31) / 32 * 4);
+    device_free(g, c->anc, V * 4);
     device_free(g, c->uf, V * 4);
     device_free(g, c->counters, 64);
     delete c;

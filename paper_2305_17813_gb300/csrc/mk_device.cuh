@@ -46,11 +46,19 @@ enum Counter {
     kCtrRelaxSlabs = 5,
     kCtrRelaxEdges = 6,
     kCtrRelaxImproved = 7,
-    kCtrInvalidSlabs = 8,
+    kCtrInvalidated = 8,   // vertices invalidated by deletions
     kCtrWccSlabs = 9,
     kCtrWccEdges = 10,
     kCtrCommitSlabs = 11,
-    kNumCounters = 16
+    kCtrSeedLists = 12,    // prologue kernels (incremental / decremental seeds)
+    kCtrSeedSlabs = 13,
+    kCtrSeedEdges = 14,
+    kCtrSeedImproved = 15,
+    kCtrWccUpdSlabs = 16,  // incremental WCC pass (updated lists only)
+    kCtrWccUpdEdges = 17,
+    kCtrRounds = 18,       // BFS/SSSP rounds run by the persistent round kernel
+    kCtrGridBarriers = 19, // grid barriers it crossed
+    kNumCounters = 32
 };
 
 // Mutable device-side state of one graph (one allocation).

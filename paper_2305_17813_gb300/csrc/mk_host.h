@@ -23,9 +23,10 @@ struct Consumer {
     uint64_t epoch = ~0ull;     // graph epoch whose change log this state has applied
     uint64_t seq = ~0ull;       // graph change counter at the last update
     unsigned long long *D = nullptr; // BFS/SSSP: V packed <distance, parent>
-    uint32_t *front[2] = {nullptr, nullptr}; // BFS/SSSP frontiers (V each)
+    uint2 *front[2] = {nullptr, nullptr}; // BFS/SSSP list frontiers (H entries <list, source> each)
     uint32_t *stamp = nullptr;  // BFS/SSSP: round in which a vertex was last enqueued
     uint32_t *inv = nullptr;    // BFS/SSSP: bitmap of vertices invalidated by this call's deletes
+    uint32_t *anc = nullptr;    // BFS/SSSP: tree ancestors for the invalidation (pointer jumping)
     uint32_t round = 0;         // last stamp value used
     uint32_t *uf = nullptr;     // WCC: union-find parents (V)
     uint32_t *counters = nullptr; // device: frontier sizes etc. (16 words)

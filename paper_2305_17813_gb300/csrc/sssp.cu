@@ -13,11 +13,10 @@
 // BucketIterator, Algorithm "Iteration Scheme 2").
 //
 // Decremental prologue: deleted tree edges (parent(v) = u) invalidate v; the
-// invalidation then spreads down the tree through the children of every
-// invalidated vertex (a top-down traversal of the affected subtrees instead
-// of the paper's per-vertex walk up to the source, so the cost follows the
-// invalidated region); then every edge from a valid vertex into an
-// invalidated one is relaxed.  Incremental prologue: the edges inserted since
+// invalidation then spreads to every tree descendant of such a v (the
+// paper's per-vertex walk up the parent chain, done here as a union-find
+// style find with path halving so that the walks share their work); then
+// every edge from a valid vertex into an invalidated one is relaxed.  Incremental prologue: the edges inserted since
 // the last commit, read with the UpdateIterator, are relaxed.  Common
 // epilogue: rounds until no distance improves.
 //
@@ -85,7 +84,7 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *(vo
 struct RoundArgs {
     GView g;
     unsigned long long *D;
-    uint32_t *front[2];
+    uint2 *front[2];      // list frontiers: <list, source of the list>
     uint32_t *ctr;        // consumer counter words
     uint32_t *stamp;
     uint32_t *inv;
@@ -94,14 +93,15 @@ struct RoundArgs {
     uint32_t max_rounds;
     uint32_t source;
     int unit;
-    int mode;             // 0 = relax rounds, 1 = invalidation rounds
+    uint32_t *anc;        // decremental prologue: tree ancestor of each vertex (pointer jumping)
 };
 
 namespace {
 
 // One round over frontier F[0, n): warps stride over groups of 32 lists and
-// walk them four at a time (8-lane groups, walk_lists_g8).
-__device__ void relax_body(const RoundArgs &a, const uint32_t *F, uint32_t n, uint32_t *Fn, uint32_t *cnt,
+// walk them four at a time (8-lane groups, walk_lists_g8_from), the head
+// slabs of the next four loaded before the current four are walked.
+__device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2 *Fn, uint32_t *cnt,
                            uint32_t round, uint64_t warp0, uint64_t nwarps)
 {
     const GView &g = a.g;
@@ -111,73 +111,43 @@ __device__ void relax_body(const RoundArgs &a, const uint32_t *F, uint32_t n, ui
     for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
         const uint64_t i = base + lane;
         bool todo = i < n;
-        // each lane fetches its own list's source and distance up front
-        const uint32_t mine = todo ? F[i] : 0;
-        const uint32_t my_x = todo ? g.list_src[mine] : 0;
+        // each lane fetches its own entry and the source's distance up front
+        const uint2 e = todo ? F[i] : make_uint2(0, 0);
+        const uint32_t mine = e.x, my_x = e.y;
         const uint32_t my_dx = todo ? node_dist(__ldcg(&a.D[my_x])) : kInf32;
         lists += __popc(__ballot_sync(kFull, todo));
         todo = todo && my_dx != kInf32;
         const uint32_t q = __ballot_sync(kFull, todo);
-        for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
-            const uint32_t owner = group_item(q, pass, gi);
+        const uint32_t np = ((uint32_t)__popc(q) + 3) / 4;
+        uint32_t owner = group_item(q, 0, gi);
+        const uint32_t L0 = __shfl_sync(kFull, mine, owner & 31);
+        uint4 x0 = group_load(g, owner < 32 ? L0 : kNil);
+        for (uint32_t pass = 0; pass < np; ++pass) {
             const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
             const bool has = owner < 32;
             const uint32_t x = __shfl_sync(kFull, my_x, owner & 31);
             const uint32_t dx0 = __shfl_sync(kFull, my_dx, owner & 31);
             const uint32_t dx = has ? dx0 : kInf32;
-            slabs += walk_lists_g8(g, has ? L : kNil, 0, a.max_hops,
-                                   [&](uint32_t y, uint32_t w, bool live) {
-                                       edges += __popc(__ballot_sync(kFull, live));
-                                       bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
-                                       up = up && first_this_round(a.stamp, y, round);
-                                       improved += __popc(__ballot_sync(kFull, up));
-                                       enqueue_lists(g, y, up, Fn, cnt, a.cap, overflow);
-                                   });
+            // the next pass's head slabs
+            const uint32_t nowner = group_item(q, pass + 1, gi);
+            const uint32_t nL = __shfl_sync(kFull, mine, nowner & 31);
+            const uint4 nx0 = group_load(g, nowner < 32 ? nL : kNil);
+            slabs += walk_lists_g8_from(g, has ? L : kNil, true, x0, 0, a.max_hops,
+                                        [&](uint32_t y, uint32_t w, bool live) {
+                                            edges += __popc(__ballot_sync(kFull, live));
+                                            bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
+                                            up = up && first_this_round(a.stamp, y, round);
+                                            improved += __popc(__ballot_sync(kFull, up));
+                                            enqueue_lists(g, y, up, Fn, cnt, a.cap, overflow);
+                                        });
+            owner = nowner;
+            x0 = nx0;
         }
     }
     count_add(g.st, kCtrRelaxLists, lists);
     count_add(g.st, kCtrRelaxSlabs, slabs);
     count_add(g.st, kCtrRelaxEdges, edges);
     count_add(g.st, kCtrRelaxImproved, improved);
-}
-
-// One round of invalidation: the tree children of the invalidated vertices
-// whose lists are in F become invalid too (lists walked four at a time).
-__device__ void invalidate_body(const RoundArgs &a, const uint32_t *F, uint32_t n, uint32_t *Fn, uint32_t *cnt,
-                                uint64_t warp0, uint64_t nwarps)
-{
-    const GView &g = a.g;
-    const uint32_t lane = lane_id(), gi = lane >> 3;
-    int *overflow = (int *)(a.ctr + kOverflow);
-    uint32_t *total = a.ctr + kInvTotal;
-    unsigned long long slabs = 0;
-    for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
-        const uint64_t i = base + lane;
-        const bool todo = i < n;
-        const uint32_t mine = todo ? F[i] : 0;
-        const uint32_t my_x = todo ? g.list_src[mine] : 0;
-        const uint32_t q = __ballot_sync(kFull, todo);
-        for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
-            const uint32_t owner = group_item(q, pass, gi);
-            const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
-            const bool has = owner < 32;
-            const uint32_t x = __shfl_sync(kFull, my_x, owner & 31);
-            slabs += walk_lists_g8(g, has ? L : kNil, 0, a.max_hops, [&](uint32_t y, uint32_t, bool live) {
-                bool hit = false;
-                if (live && y != a.source) {
-                    const unsigned long long dy = __ldcg(&a.D[y]);
-                    if (dy != kInfNode && node_parent(dy) == x)
-                        hit = atomicCAS(&a.D[y], dy, kInfNode) == dy;
-                }
-                if (hit) {
-                    atomicAdd(total, 1u);
-                    atomicOr(&a.inv[y >> 5], 1u << (y & 31));
-                }
-                enqueue_lists(g, y, hit, Fn, cnt, a.cap, overflow);
-            });
-        }
-    }
-    count_add(g.st, kCtrInvalidSlabs, slabs);
 }
 
 // Round r of a phase: reads the size in cnts[r % 3], appends to
@@ -191,10 +161,7 @@ __device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t *cnts, u
     if (blockIdx.x == 0 && threadIdx.x == 0)
         cnts[(r + 2) % 3] = 0;
     uint32_t *cnt = cnts + (r + 1) % 3;
-    if (a.mode == 0)
-        relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps);
-    else
-        invalidate_body(a, a.front[in], n, a.front[in ^ 1], cnt, warp0, nwarps);
+    relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps);
 }
 
 // Bounded sense-counting grid barrier for a co-resident (cooperative) grid.
@@ -240,14 +207,14 @@ __device__ bool grid_barrier(uint32_t *bar)
 // phase sits between two grid barriers, so no block reads a global size
 // while block 0 changes them, and the others wait at one barrier instead of
 // one per round.
-__global__ void __launch_bounds__(256) k_rounds(RoundArgs a)
+__global__ void __launch_bounds__(256, 3) k_rounds(RoundArgs a)
 {
     __shared__ uint32_t solo_cnt[3];
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t rid = ld_volatile(a.ctr + kRid);
     uint32_t *gcnt = a.ctr + kCnt0;
-    uint32_t r = 0;
+    uint32_t r = 0, bars = 0;
     bool ok = true;
     while (r < a.max_rounds) {
         uint32_t n = ld_volatile(gcnt + r % 3);
@@ -255,6 +222,7 @@ __global__ void __launch_bounds__(256) k_rounds(RoundArgs a)
             break;
         if (n > kSoloLists) {
             round_step(a, gcnt, r, n, warp0, nwarps, rid);
+            ++bars;
             if (!grid_barrier(a.ctr + kBar)) {
                 ok = false;
                 break;
@@ -263,6 +231,7 @@ __global__ void __launch_bounds__(256) k_rounds(RoundArgs a)
             continue;
         }
         // every block has read n: block 0 may now change the global sizes
+        bars += 2;
         if (!grid_barrier(a.ctr + kBar)) {
             ok = false;
             break;
@@ -299,6 +268,8 @@ __global__ void __launch_bounds__(256) k_rounds(RoundArgs a)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr[kRoundsDone] = r;
+        atomicAdd(&a.g.st->ctr[kCtrRounds], (unsigned long long)r);
+        atomicAdd(&a.g.st->ctr[kCtrGridBarriers], (unsigned long long)bars);
         if (!ok || r >= a.max_rounds)
             set_status(a.g.st, kErrTimeout);
     }
@@ -314,7 +285,7 @@ __global__ void __launch_bounds__(256) k_round_once(RoundArgs a, uint32_t r, uin
         a.ctr[kRoundsDone] = r + 1;
 }
 
-__global__ void k_sssp_init(unsigned long long *D, uint32_t V, uint32_t source, uint32_t *front, uint32_t *count,
+__global__ void k_sssp_init(unsigned long long *D, uint32_t V, uint32_t source, uint2 *front, uint32_t *count,
                             const uint2 *vinfo)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -323,34 +294,89 @@ __global__ void k_sssp_init(unsigned long long *D, uint32_t V, uint32_t source, 
     if (v == 0) {
         const uint2 vi = vinfo[source];
         for (uint32_t b = 0; b < vi.y; ++b)
-            front[b] = vi.x + b;
+            front[b] = make_uint2(vi.x + b, source);
         *count = vi.y;
     }
 }
 
-// Decremental seeds: a deleted edge (u, v) that is v's tree edge invalidates v.
+// Decremental seeds: a deleted edge (u, v) that is v's tree edge invalidates
+// v (its tree node becomes <INF, INVALID> and its bit is set in `inv`).
 __global__ void k_invalidate(const unsigned long long *dlog, const DevState *st, RoundArgs a)
 {
     const uint32_t n = st->dlog_count;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t lim = ((uint64_t)n + 31) & ~31ull;
-    if ((uint64_t)(i & ~31u) >= lim)
+    if (i >= n)
         return;
-    bool hit = false;
-    uint32_t v = 0;
-    if (i < n) {
-        const unsigned long long e = dlog[i];
-        const uint32_t u = (uint32_t)(e >> 32);
-        v = (uint32_t)e;
-        const unsigned long long dv = __ldcg(&a.D[v]);
-        if (v != a.source && dv != kInfNode && node_parent(dv) == u)
-            hit = atomicCAS(&a.D[v], dv, kInfNode) == dv;
-    }
-    if (hit) {
+    const unsigned long long e = dlog[i];
+    const uint32_t u = (uint32_t)(e >> 32), v = (uint32_t)e;
+    const unsigned long long dv = __ldcg(&a.D[v]);
+    if (v != a.source && dv != kInfNode && node_parent(dv) == u && atomicCAS(&a.D[v], dv, kInfNode) == dv) {
         atomicAdd(a.ctr + kInvTotal, 1u);
         atomicOr(&a.inv[v >> 5], 1u << (v & 31));
+        atomicAdd(&a.g.st->ctr[kCtrInvalidated], 1ull);
     }
-    enqueue_lists(a.g, v, hit, a.front[0], a.ctr + kCnt0, a.cap, (int *)(a.ctr + kOverflow));
+}
+
+// The invalidation spreads to every tree descendant of the seeds: a vertex
+// is invalid iff the path from it up the shortest-path tree reaches a seed
+// before the source.  The paper walks each vertex up to the source; here the
+// walks share their work by pointer jumping on a copy of the parent pointers
+// (the union-find "find" with path halving): anc[v] starts as v's tree
+// parent, and as v itself at the source, at the seeds and at unreached
+// vertices, which are the roots of the forest.  Tree parents have strictly
+// smaller distances (weights are >= 1), so the forest has no cycles.
+__global__ void k_inv_anc_init(RoundArgs a)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.g.V)
+        return;
+    const unsigned long long d = __ldcg(&a.D[v]);
+    a.anc[v] = (v == a.source || d == kInfNode) ? v : node_parent(d);
+}
+
+// Each reached vertex finds its root (path halving on anc) and is invalidated
+// when the root is not the source.  The invalidated vertices of one warp set
+// their bits with one atomicOr (32 consecutive vertices share a bitmap word).
+__global__ void k_inv_jump(RoundArgs a)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((v & ~31u) >= a.g.V)
+        return;
+    bool bad = false;
+    if (v < a.g.V && v != a.source && __ldcg(&a.D[v]) != kInfNode) {
+        uint32_t x = v, hops = 0;
+        bool ok = true;
+        // plain (L1-cacheable) loads: a stale anc value is an older ancestor,
+        // and roots never change, so every walk still ends at v's root
+        // while the source's line, where most walks end, stays in L1
+        for (;;) {
+            const uint32_t px = a.anc[x];
+            if (px == x)
+                break;
+            const uint32_t ppx = a.anc[px];
+            if (ppx == px) {
+                x = px;
+                break;
+            }
+            a.anc[x] = ppx; // path halving: ppx is an ancestor of x
+            x = ppx;
+            if (++hops > a.max_rounds) { // parent pointers not a forest: corrupted state
+                ok = false;
+                break;
+            }
+        }
+        if (!ok)
+            set_status(a.g.st, kErrTimeout);
+        bad = ok && x != a.source;
+    }
+    if (bad)
+        a.D[v] = kInfNode;
+    const uint32_t mask = __ballot_sync(kFull, bad);
+    if (lane_id() == 0 && mask) {
+        atomicOr(&a.inv[v >> 5], mask);
+        atomicAdd(a.ctr + kInvTotal, (uint32_t)__popc(mask));
+        count_add(a.g.st, kCtrInvalidated, __popc(mask));
+    }
 }
 
 // After invalidation: relax every edge out of a valid vertex into a vertex
@@ -358,52 +384,69 @@ __global__ void k_invalidate(const unsigned long long *dlog, const DevState *st,
 // which stays fixed during the pass, so every such edge is relaxed even after
 // another in-neighbour has already given its target a finite distance; does
 // nothing if nothing was invalidated.  A streaming scan over every slab in
-// use (through the per-slab owner array): a warp reads four consecutive
-// slabs per step and the owner's tree node and the slab load independently.
+// use (through the per-slab owner array): a warp takes 32 consecutive slabs,
+// reads their owners in one coalesced load and the owners' tree nodes in one
+// gather, compacts the slabs whose source has a finite distance, and reads
+// those four per step, one per 8-lane group, loading the next step's slabs
+// before relaxing this step's edges.
 __global__ void __launch_bounds__(256) k_relax_into_invalid_slabs(RoundArgs a)
 {
+    __shared__ uint8_t comp[8][32];
     const GView &g = a.g;
     if (ld_volatile(a.ctr + kInvTotal) == 0)
         return;
-    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
+    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, w = threadIdx.x >> 5;
     const uint64_t total = (uint64_t)g.H + g.P;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
     int *overflow = (int *)(a.ctr + kOverflow);
-    unsigned long long slabs = 0, edges = 0, improved = 0, lists = 0;
-    for (uint64_t base = warp0 * 4; base < total; base += nwarps * 4) {
-        const uint64_t s = base + gi;
-        const uint32_t own = s < total ? g.owner[s] : kNil;
-        bool active = own != kNil;
-        uint32_t dx = kInf32;
-        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
-        if (active) {
-            if (sub == 0)
-                dx = node_dist(__ldcg(&a.D[own]));
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s) + sub * 4));
-        }
-        dx = __shfl_sync(kFull, dx, gbase);
-        slabs += __popc(__ballot_sync(kFull, active && sub == 0));
-        active = active && dx != kInf32;
-        lists += __popc(__ballot_sync(kFull, active && sub == 0));
-        const bool last = sub == 7u;
+    const uint4 none = make_uint4(kEmptyKey, kFull, kFull, kFull);
+    unsigned long long slabs = 0, edges = 0, improved = 0;
+    for (uint64_t c = warp0 * 32; c < total; c += nwarps * 32) {
+        // 32 consecutive slabs: owners (one coalesced load), then the owners'
+        // distances; only slabs of reachable, valid sources are read
+        const uint32_t own_l = c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil;
+        const uint32_t dx_l = own_l != kNil ? node_dist(__ldcg(&a.D[own_l])) : kInf32;
+        const uint32_t live = __ballot_sync(kFull, dx_l != kInf32);
+        const uint32_t n = __popc(live);
+        if (dx_l != kInf32)
+            comp[w][__popc(live & ((1u << lane) - 1))] = (uint8_t)lane;
+        __syncwarp();
+        uint32_t it = gi < n ? comp[w][gi] : 32u;
+        uint4 x = none;
+        if (it < 32)
+            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + it)) + sub * 4));
+        for (uint32_t k = gi; k - gi < n; k += 4) {
+            const uint32_t nit = k + 4 < n ? comp[w][k + 4] : 32u;
+            uint4 nx = none;
+            if (nit < 32)
+                nx = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + nit)) + sub * 4));
+            const bool active = it < 32;
+            const uint32_t own = __shfl_sync(kFull, own_l, it & 31);
+            const uint32_t dx = __shfl_sync(kFull, dx_l, it & 31);
+            slabs += __popc(__ballot_sync(kFull, active && sub == 0));
+            const bool last = sub == 7u;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const uint32_t y = k ? x.z : x.x, w = k ? x.w : x.y;
-            const bool live = active && !(k && last) && y < kTombKey;
-            edges += __popc(__ballot_sync(kFull, live));
-            const bool target = live && ((a.inv[y >> 5] >> (y & 31)) & 1u);
-            bool up = target && relax(a.D, own, dx, y, a.unit ? 1u : w);
-            up = up && first_this_round(a.stamp, y, round);
-            improved += __popc(__ballot_sync(kFull, up));
-            enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+            for (int k2 = 0; k2 < 2; ++k2) {
+                const uint32_t y = k2 ? x.z : x.x, wt = k2 ? x.w : x.y;
+                const bool live_e = active && !(k2 && last) && y < kTombKey;
+                edges += __popc(__ballot_sync(kFull, live_e));
+                const bool target = live_e && ((__ldg(&a.inv[y >> 5]) >> (y & 31)) & 1u); // fixed during the pass
+                bool up = target && relax(a.D, own, dx, y, a.unit ? 1u : wt);
+                up = up && first_this_round(a.stamp, y, round);
+                improved += __popc(__ballot_sync(kFull, up));
+                enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+            }
+            x = nx;
+            it = nit;
         }
+        __syncwarp();
     }
-    count_add(g.st, kCtrRelaxLists, lists);
-    count_add(g.st, kCtrRelaxSlabs, slabs);
-    count_add(g.st, kCtrRelaxEdges, edges);
-    count_add(g.st, kCtrRelaxImproved, improved);
+    count_add(g.st, kCtrSeedLists, slabs);
+    count_add(g.st, kCtrSeedSlabs, slabs);
+    count_add(g.st, kCtrSeedEdges, edges);
+    count_add(g.st, kCtrSeedImproved, improved);
 }
 
 // Incremental seeds: relax the entries inserted since the last commit
@@ -428,27 +471,36 @@ __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
             my_start = update_begin(g, (uint32_t)l, &my_first);
     }
     const uint32_t q = __ballot_sync(kFull, todo);
+    const uint32_t np = ((uint32_t)__popc(q) + 3) / 4;
     unsigned long long slabs = 0, edges = 0, improved = 0;
-    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
-        const uint32_t owner = group_item(q, pass, gi);
+    // the first slab of each walk is loaded one pass ahead
+    uint32_t owner = group_item(q, 0, gi);
+    const uint32_t s0 = __shfl_sync(kFull, my_start, owner & 31);
+    uint4 x0 = group_load(g, owner < 32 ? s0 : kNil);
+    for (uint32_t pass = 0; pass < np; ++pass) {
         const bool has = owner < 32;
         const uint32_t src = __shfl_sync(kFull, x, owner & 31);
         const uint32_t dsrc = __shfl_sync(kFull, dx, owner & 31);
         const uint32_t first_lane = __shfl_sync(kFull, my_first, owner & 31);
         const uint32_t start0 = __shfl_sync(kFull, my_start, owner & 31);
         const uint32_t start = has ? start0 : kNil;
-        slabs += walk_lists_g8(g, start, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
+        const uint32_t nowner = group_item(q, pass + 1, gi);
+        const uint32_t ns = __shfl_sync(kFull, my_start, nowner & 31);
+        const uint4 nx0 = group_load(g, nowner < 32 ? ns : kNil);
+        slabs += walk_lists_g8_from(g, start, true, x0, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
             edges += __popc(__ballot_sync(kFull, live));
             bool up = live && relax(a.D, src, dsrc, y, a.unit ? 1u : w);
             up = up && first_this_round(a.stamp, y, round);
             improved += __popc(__ballot_sync(kFull, up));
             enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
         });
+        owner = nowner;
+        x0 = nx0;
     }
-    count_add(g.st, kCtrRelaxLists, __popc(q));
-    count_add(g.st, kCtrRelaxSlabs, slabs);
-    count_add(g.st, kCtrRelaxEdges, edges);
-    count_add(g.st, kCtrRelaxImproved, improved);
+    count_add(g.st, kCtrSeedLists, __popc(q));
+    count_add(g.st, kCtrSeedSlabs, slabs);
+    count_add(g.st, kCtrSeedEdges, edges);
+    count_add(g.st, kCtrSeedImproved, improved);
 }
 
 // Ends a call: advances the round stamp past every id used, reports an
@@ -490,23 +542,26 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
     const size_t V = g->v.V, H = g->v.H;
     mk_status st = device_alloc(g, (void **)&c->D, V * 8);
     if (st == MK_OK)
-        st = device_alloc(g, (void **)&c->front[0], H * 4);
+        st = device_alloc(g, (void **)&c->front[0], H * 8);
     if (st == MK_OK)
-        st = device_alloc(g, (void **)&c->front[1], H * 4);
+        st = device_alloc(g, (void **)&c->front[1], H * 8);
     if (st == MK_OK)
         st = device_alloc(g, (void **)&c->stamp, V * 4);
     if (st == MK_OK)
         st = device_alloc(g, (void **)&c->inv, (V + 31) / 32 * 4);
+    if (st == MK_OK)
+        st = device_alloc(g, (void **)&c->anc, V * 4);
     if (st == MK_OK)
         st = device_alloc(g, (void **)&c->counters, 64);
     if (st == MK_OK && (cudaMemset(c->stamp, 0, V * 4) != cudaSuccess || cudaMemset(c->counters, 0, 64) != cudaSuccess))
         st = MK_ERR_CUDA;
     if (st != MK_OK) {
         device_free(g, c->D, V * 8);
-        device_free(g, c->front[0], H * 4);
-        device_free(g, c->front[1], H * 4);
+        device_free(g, c->front[0], H * 8);
+        device_free(g, c->front[1], H * 8);
         device_free(g, c->stamp, V * 4);
         device_free(g, c->inv, (V + 31) / 32 * 4);
+        device_free(g, c->anc, V * 4);
         device_free(g, c->counters, 64);
         delete c;
         return st;
@@ -592,6 +647,7 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     a.ctr = c->counters;
     a.stamp = c->stamp;
     a.inv = c->inv;
+    a.anc = c->anc;
     a.cap = H;
     a.max_hops = g->v.P + 2;
     a.max_rounds = V + 2;
@@ -616,12 +672,13 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
                                                                                                  g->d_state, a);
                 return cudaSuccess;
             }));
-            a.mode = 1;
-            MK_TRY(run_phase(g, a, "sssp_invalidate_rounds", s));
-            a.mode = 0;
-            MK_CUDA(cudaMemsetAsync(c->counters + kCnt0, 0, 12, s));
+            MK_TRY(timed(g, "sssp_invalidate_jump", s, 2, [&]() {
+                k_inv_anc_init<<<grid_for(V, 256), 256, 0, s>>>(a);
+                k_inv_jump<<<grid_for(V, 256), 256, 0, s>>>(a);
+                return cudaSuccess;
+            }));
             MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
-                const uint64_t warps = ((uint64_t)H + g->v.P + 3) / 4;
+                const uint64_t warps = ((uint64_t)H + g->v.P + 31) / 32;
                 const uint32_t grid = (uint32_t)std::min<uint64_t>(grid_for(warps * 32, 256), (uint64_t)num_sms() * 16);
                 k_relax_into_invalid_slabs<<<grid, 256, 0, s>>>(a);
                 return cudaSuccess;
@@ -634,7 +691,6 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
         }));
     }
     // common epilogue: rounds until no distance improves
-    a.mode = 0;
     MK_TRY(run_phase(g, a, "sssp_rounds", s));
     MK_TRY(timed(g, "sssp_unpack", s, 2, [&]() {
         k_sssp_finish<<<1, 1, 0, s>>>(c->counters, g->d_state);

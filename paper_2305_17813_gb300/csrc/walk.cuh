@@ -45,11 +45,12 @@ __device__ __forceinline__ uint32_t update_begin(const GView &g, uint32_t L, uin
 }
 
 // Appends the slab lists of vertex y (for every lane with pred) to the list
-// frontier `out`: lanes with few buckets write their own ids after one
-// warp-aggregated atomicAdd; a vertex with many buckets is written by the
-// whole warp.  Must be called by the full warp.  Sets *overflow on a lane
-// whose entries would not fit in `cap`.
-__device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool pred, uint32_t *out, uint32_t *count,
+// frontier `out` as <list, y> entries (the source travels with the list, so
+// a consumer needs no list_src lookup): lanes with few buckets write their
+// own entries after one warp-aggregated atomicAdd; a vertex with many
+// buckets is written by the whole warp.  Must be called by the full warp.
+// Sets *overflow on a lane whose entries would not fit in `cap`.
+__device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool pred, uint2 *out, uint32_t *count,
                                               uint32_t cap, int *overflow)
 {
     constexpr uint32_t kSmall = 8;
@@ -77,7 +78,7 @@ __device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool p
         const uint32_t at = base + incl - c;
         for (uint32_t k = 0; k < c; ++k) {
             if (at + k < cap)
-                out[at + k] = vi.x + k;
+                out[at + k] = make_uint2(vi.x + k, y);
             else
                 *overflow = 1;
         }
@@ -89,13 +90,14 @@ __device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool p
         big &= big - 1;
         const uint32_t first = __shfl_sync(kFull, vi.x, l);
         const uint32_t nb = __shfl_sync(kFull, vi.y, l);
+        const uint32_t yl = __shfl_sync(kFull, y, l);
         uint32_t base = 0;
         if (lane == 0)
             base = atomicAdd(count, nb);
         base = __shfl_sync(kFull, base, 0);
         for (uint32_t k = lane; k < nb; k += 32) {
             if (base + k < cap)
-                out[base + k] = first + k;
+                out[base + k] = make_uint2(first + k, yl);
             else
                 *overflow = 1;
         }
@@ -106,26 +108,22 @@ __device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool p
 
 namespace mk {
 
-// Tiled walk: each 8-lane group of the warp walks its own slab list (so a
-// warp has four 128-byte slab loads in flight instead of one); lane `sub` of
-// a group loads words 4*sub .. 4*sub+3 of the slab as one 16-byte vector,
-// i.e. pairs 2*sub and 2*sub+1 (lane 7: pair 14, the unused lane 30 and the
-// next-slab lane).  `slab` and `first_lane` are per group (kNil = the group
-// has no list).  Per slab, f(key, weight, live) is called twice by every
-// lane of the warp (convergent), once for each pair the lane holds; `live`
-// is false for free / deleted keys, for key words below first_lane on the
-// first slab, and for groups without a list.  Returns the number of slabs
-// loaded by the warp.
+// walk_lists_g8 whose first slab may already be loaded: with have_first,
+// x0 holds the lane's part of `slab` (group_load), so the caller can issue
+// that load early (for example one step ahead, while the previous list is
+// processed).
 template <typename F>
-__device__ __forceinline__ uint32_t walk_lists_g8(const GView &g, uint32_t slab, uint32_t first_lane,
-                                                  uint32_t max_hops, F &&f)
+__device__ __forceinline__ uint32_t walk_lists_g8_from(const GView &g, uint32_t slab, bool have_first, uint4 x0,
+                                                       uint32_t first_lane, uint32_t max_hops, F &&f)
 {
     const uint32_t lane = lane_id(), sub = lane & 7u, gbase = lane & ~7u;
     bool active = slab != kNil;
     uint32_t loads = 0;
     for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
         uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
-        if (active)
+        if (hop == 0 && have_first)
+            x = x0;
+        else if (active)
             x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
         loads += __popc(__ballot_sync(kFull, active && sub == 0));
         const bool last = sub == 7u;
@@ -143,6 +141,33 @@ __device__ __forceinline__ uint32_t walk_lists_g8(const GView &g, uint32_t slab,
         first_lane = 0;
     }
     return loads;
+}
+
+// Tiled walk: each 8-lane group of the warp walks its own slab list (so a
+// warp has four 128-byte slab loads in flight instead of one); lane `sub` of
+// a group loads words 4*sub .. 4*sub+3 of the slab as one 16-byte vector,
+// i.e. pairs 2*sub and 2*sub+1 (lane 7: pair 14, the unused lane 30 and the
+// next-slab lane).  `slab` and `first_lane` are per group (kNil = the group
+// has no list).  Per slab, f(key, weight, live) is called twice by every
+// lane of the warp (convergent), once for each pair the lane holds; `live`
+// is false for free / deleted keys, for key words below first_lane on the
+// first slab, and for groups without a list.  Returns the number of slabs
+// loaded by the warp.
+template <typename F>
+__device__ __forceinline__ uint32_t walk_lists_g8(const GView &g, uint32_t slab, uint32_t first_lane,
+                                                  uint32_t max_hops, F &&f)
+{
+    return walk_lists_g8_from(g, slab, false, make_uint4(0, 0, 0, 0), first_lane, max_hops, f);
+}
+
+// The lane's 16-byte part of slab s (words 4*sub .. 4*sub+3), for a group
+// that starts a walk at s; an empty part for s == kNil.
+__device__ __forceinline__ uint4 group_load(const GView &g, uint32_t s)
+{
+    uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+    if (s != kNil)
+        x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, s) + (lane_id() & 7u) * 4));
+    return x;
 }
 
 // The k-th set bit of q handed to 8-lane group `gi` in pass `pass` (four

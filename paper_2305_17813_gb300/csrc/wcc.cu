@@ -31,41 +31,118 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *p, uint32_t x)
         if (px == x)
             return x;
         const uint32_t ppx = __ldcg(&p[px]);
-        if (ppx != px)
-            p[x] = ppx; // path halving: ppx is an ancestor of x
+        if (ppx == px)
+            return px; // px is the root: no third load
+        p[x] = ppx;    // path halving: ppx is an ancestor of x
         x = ppx;
+    }
+}
+
+// Parent loads.  The coherent form reads L2 (the point of coherence); the
+// cached form may also hit a stale line in the SM's L1.  A stale parent is
+// still a correct one from an earlier moment: parents only ever move to
+// smaller ids of the same set (a hook replaces a root's self-link, path
+// halving replaces a parent by an ancestor), and a vertex that is not a root
+// never becomes one again.  So a find on cached loads returns a vertex that
+// is, or was, the root of the element's set -- always a member of that set.
+// Path halving may then store a parent older than the current one, which
+// is still an ancestor in the same set.  The union below only acts on a
+// found root through a CAS that succeeds while it is still a root, and
+// retries on coherent loads.  The cached form
+// keeps the roots that every find ends at (above all the giant component's
+// vertex 0) in L1 instead of sending every find's last load to the same L2
+// line.
+template <bool kCached>
+__device__ __forceinline__ uint32_t uf_load(const uint32_t *p, uint32_t x)
+{
+    return kCached ? p[x] : __ldcg(&p[x]);
+}
+
+// Two finds in lockstep, so that their dependent loads overlap; kNil
+// entries are left alone.  Parents strictly decrease along every path
+// (p[x] < x except at roots), so both walks end.
+template <bool kCached>
+__device__ __forceinline__ void uf_find2(uint32_t *p, uint32_t &x, uint32_t &y)
+{
+    bool dx = x == kNil, dy = y == kNil;
+    while (!(dx && dy)) {
+        uint32_t px = x, py = y;
+        if (!dx)
+            px = uf_load<kCached>(p, x);
+        if (!dy)
+            py = uf_load<kCached>(p, y);
+        dx = dx || px == x;
+        dy = dy || py == y;
+        uint32_t ppx = px, ppy = py;
+        if (!dx)
+            ppx = uf_load<kCached>(p, px);
+        if (!dy)
+            ppy = uf_load<kCached>(p, py);
+        if (!dx) {
+            if (ppx == px) {
+                x = px;
+                dx = true;
+            } else {
+                p[x] = ppx; // path halving: ppx is an ancestor of x
+                x = ppx;
+            }
+        }
+        if (!dy) {
+            if (ppy == py) {
+                y = py;
+                dy = true;
+            } else {
+                p[y] = ppy;
+                y = ppy;
+            }
+        }
     }
 }
 
 // Union of the sets of up to 16 elements held by one 8-lane group, two per
 // lane: all roots are found in parallel, the group's smallest root m is the
-// anchor, and every other root is hooked under it with one CAS on its parent
-// (m is smaller, so parents keep decreasing).  An element whose CAS loses
-// (its root was hooked by another warp meanwhile) retries with fresh roots
-// of itself and of the anchor, hooking the larger under the smaller.
-// Returns false if the retry bound was hit.  Must be called by the full warp.
+// anchor, and every other root r is hooked under it with one CAS on p[r]
+// from r to m.  The CAS succeeds only while r is still a root; m need not be
+// one any more, because any vertex with a smaller id lies in another tree
+// (ids never increase towards a root), so the hook joins the two sets and
+// keeps parents decreasing.  An element whose CAS loses (its root was
+// hooked by another warp meanwhile) retries with fresh roots of itself and
+// of the anchor, hooking the larger under the smaller.  Returns false if the
+// retry bound was hit.  Must be called by the full warp.
 __device__ __forceinline__ bool group_union2(uint32_t *p, uint32_t e0, bool a0, uint32_t e1, bool a1,
                                              uint32_t limit)
 {
-    uint32_t r0 = a0 ? uf_find(p, e0) : kNil;
-    uint32_t r1 = a1 ? uf_find(p, e1) : kNil;
+    uint32_t r0 = a0 ? e0 : kNil;
+    uint32_t r1 = a1 ? e1 : kNil;
+    uf_find2<true>(p, r0, r1);
     uint32_t m = min(r0, r1);
     m = min(m, __shfl_xor_sync(kFull, m, 4));
     m = min(m, __shfl_xor_sync(kFull, m, 2));
     m = min(m, __shfl_xor_sync(kFull, m, 1));
     bool p0 = a0 && r0 != m, p1 = a1 && r1 != m;
+    // first attempt with the roots just found (r > m for every pending r)
+    if (p0 && atomicCAS(&p[r0], r0, m) == r0)
+        p0 = false;
+    if (p1) {
+        if (a0 && r1 == r0)
+            p1 = p0; // the same root: decided by the CAS above
+        else if (atomicCAS(&p[r1], r1, m) == r1)
+            p1 = false;
+    }
     for (uint32_t it = 0; it < limit; ++it) {
         if (!__any_sync(kFull, p0 || p1))
             return true;
+        uint32_t a = (p0 || p1) ? m : kNil, unused = kNil;
+        uf_find2<false>(p, a, unused);
+        uint32_t x0 = p0 ? r0 : kNil, x1 = p1 ? r1 : kNil;
+        uf_find2<false>(p, x0, x1);
         if (p0) {
-            const uint32_t a = uf_find(p, m);
-            r0 = uf_find(p, r0);
+            r0 = x0;
             if (r0 == a || atomicCAS(&p[max(r0, a)], max(r0, a), min(r0, a)) == max(r0, a))
                 p0 = false;
         }
         if (p1) {
-            const uint32_t a = uf_find(p, m);
-            r1 = uf_find(p, r1);
+            r1 = x1;
             if (r1 == a || atomicCAS(&p[max(r1, a)], max(r1, a), min(r1, a)) == max(r1, a))
                 p1 = false;
         }
@@ -89,7 +166,7 @@ __global__ void k_uf_init(uint32_t *p, uint32_t V)
 // slab's source and destinations are united in one group_union2.
 // all_lists: every list from its head; otherwise only updated lists from
 // their UpdateIterator start.
-__global__ void __launch_bounds__(256) k_uf_hook(GView g, uint32_t *p, int all_lists, uint32_t max_hops, int *failed)
+__global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, int all_lists, uint32_t max_hops, int *failed)
 {
     const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
     const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
@@ -134,37 +211,57 @@ __global__ void __launch_bounds__(256) k_uf_hook(GView g, uint32_t *p, int all_l
             first_lane = 0;
         }
     }
-    count_add(g.st, kCtrWccSlabs, slabs);
-    count_add(g.st, kCtrWccEdges, edges);
+    count_add(g.st, all_lists ? kCtrWccSlabs : kCtrWccUpdSlabs, slabs);
+    count_add(g.st, all_lists ? kCtrWccEdges : kCtrWccUpdEdges, edges);
 }
 
 // Static pass as a streaming scan over every slab in use (heads and linked
 // pool slabs, found through the per-slab owner array) instead of chain
-// walks: each 8-lane group takes one slab, so a warp reads four consecutive
-// slabs (512 contiguous bytes) per step and no load waits on a next pointer.
-// The slab's owner and its live destinations are united in one
-// group_union2, exactly as in the list walk.
-__global__ void __launch_bounds__(256) k_uf_hook_slabs(GView g, uint32_t *p, int *failed)
+// walks.  A warp takes 32 consecutive slabs at a time: one coalesced load of
+// their owners, the slabs in use compacted in shared memory, then four slabs
+// per step, one per 8-lane group (16-byte loads), with the next step's slabs
+// loaded before this step's finds so that the slab stream overlaps the
+// union-find latency.  Each slab's owner and its live destinations are
+// united in one group_union2, exactly as in the list walk.
+__global__ void __launch_bounds__(256, 6) k_uf_hook_slabs(GView g, uint32_t *p, int *failed)
 {
-    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u;
+    __shared__ uint8_t comp[8][32];
+    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, w = threadIdx.x >> 5;
     const uint64_t total = (uint64_t)g.H + g.P;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint4 none = make_uint4(kEmptyKey, kFull, kFull, kFull);
     unsigned long long slabs = 0, edges = 0;
-    for (uint64_t base = warp0 * 4; base < total; base += nwarps * 4) {
-        const uint64_t s = base + gi;
-        const uint32_t own = s < total ? g.owner[s] : kNil;
-        const bool active = own != kNil;
-        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
-        if (active)
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s) + sub * 4));
-        slabs += __popc(__ballot_sync(kFull, active && sub == 0));
-        const bool last = sub == 7u;
-        const bool a0 = active && x.x < kTombKey;
-        const bool a1 = last ? active : (active && x.z < kTombKey);
-        edges += __popc(__ballot_sync(kFull, a0)) + __popc(__ballot_sync(kFull, a1 && !last));
-        if (!group_union2(p, x.x, a0, last ? own : x.z, a1, 1u << 20) && lane == 0)
-            *failed = 1;
+    for (uint64_t c = warp0 * 32; c < total; c += nwarps * 32) {
+        const uint32_t own_l = c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil;
+        const uint32_t live = __ballot_sync(kFull, own_l != kNil);
+        const uint32_t n = __popc(live);
+        if (own_l != kNil)
+            comp[w][__popc(live & ((1u << lane) - 1))] = (uint8_t)lane;
+        __syncwarp();
+        uint32_t it = gi < n ? comp[w][gi] : 32u;
+        uint4 x = none;
+        if (it < 32)
+            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + it)) + sub * 4));
+        for (uint32_t k = gi; k - gi < n; k += 4) {
+            // prefetch the next step's slab
+            const uint32_t nit = k + 4 < n ? comp[w][k + 4] : 32u;
+            uint4 nx = none;
+            if (nit < 32)
+                nx = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + nit)) + sub * 4));
+            const bool active = it < 32;
+            const uint32_t own = __shfl_sync(kFull, own_l, it & 31);
+            slabs += __popc(__ballot_sync(kFull, active && sub == 0));
+            const bool last = sub == 7u;
+            const bool a0 = active && x.x < kTombKey;
+            const bool a1 = last ? active : (active && x.z < kTombKey);
+            edges += __popc(__ballot_sync(kFull, a0)) + __popc(__ballot_sync(kFull, a1 && !last));
+            if (!group_union2(p, x.x, a0, last ? own : x.z, a1, 1u << 20) && lane == 0)
+                *failed = 1;
+            x = nx;
+            it = nit;
+        }
+        __syncwarp();
     }
     count_add(g.st, kCtrWccSlabs, slabs);
     count_add(g.st, kCtrWccEdges, edges);
@@ -230,7 +327,7 @@ extern "C" mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream)
         }));
     } else {
         MK_TRY(timed(g, "wcc_hook_all", s, 1, [&]() {
-            const uint64_t warps = ((uint64_t)H + g->v.P + 3) / 4;
+            const uint64_t warps = ((uint64_t)H + g->v.P + 31) / 32;
             const uint32_t grid = (uint32_t)std::min<uint64_t>(grid_for(warps * 32, 256), (uint64_t)num_sms() * 16);
             k_uf_hook_slabs<<<grid, 256, 0, s>>>(g->v, c->uf, failed);
             return cudaSuccess;

@@ -65,4 +65,6 @@ def test_algorithmic_bytes_model():
            "relax_slabs": 4, "relax_edges": 50, "relax_improved": 7, "wcc_slabs": 9, "wcc_edges": 100}
     assert bench.algorithmic_bytes("query", ctr, 800, 1) == pytest.approx(800 * 40.125 + 128000)
     assert bench.algorithmic_bytes("insert", ctr, 10, 2) == 2 * 10 * 76 + 128 * 12
+    assert bench.algorithmic_bytes("sssp_rounds", ctr, 1, 1) == 3 * 16 + 128 * 4 + 16 * 50 + 7 * 20
+    assert bench.algorithmic_bytes("wcc_hook_all", ctr, 1, 1) == 128 * 9 + 16 * 100
     assert bench.algorithmic_bytes("unknown", ctr, 1, 1) is None
