@@ -193,6 +193,14 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
     if family == "sssp_rounds":
         return (ctr["relax_lists"] * (4 + 4 + 8) + 128 * ctr["relax_slabs"] + 16 * ctr["relax_edges"]
                 + ctr["relax_improved"] * (8 + 4 + 8))
+    if family == "sssp_relax_into_invalid":
+        return (4 * ctr["scan_owners"] + (128 + 8) * ctr["scan_slabs"] + 16 * ctr["scan_targets"]
+                + ctr["scan_improved"] * (8 + 8 + 8))
+    if family == "sssp_relax_updated":
+        return (ctr["seed_lists"] * (4 + 8 + 8) + 128 * ctr["seed_slabs"] + 16 * ctr["seed_edges"]
+                + ctr["seed_improved"] * (8 + 4 + 8))
+    if family == "sssp_invalidate_jump":
+        return ctr["jump_vertices"] * (8 + 4 + 8 + 4)
     if family == "wcc_hook_all":
         return 128 * ctr["wcc_slabs"] + 16 * ctr["wcc_edges"]
     if family == "wcc_hook_updated":

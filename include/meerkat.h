@@ -402,8 +402,11 @@ mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *sla
  * slabs loaded, WCC edges united, commit slabs loaded; BFS/SSSP prologue
  * kernels (inserted-edge and invalidated-target seeds): lists, slabs loaded,
  * live edges relaxed, improved vertices; incremental WCC pass: slabs loaded,
- * edges united; BFS/SSSP rounds and grid barriers of the round kernel (then
- * reserved words up to 32).  Copies up to n
+ * edges united; BFS/SSSP rounds and grid barriers of the round kernel;
+ * decremental scan: slabs in use copied, slabs relaxed, live edges examined, edges
+ * into invalidated vertices, invalidated vertices given a finite distance;
+ * vertices visited by the invalidation pass (then reserved words up to 32).
+ * The BFS/SSSP prologue words above count the inserted-edge prologue only.  Copies up to n
  * (<= 32) values to out (host); reset != 0 zeroes them.  Synchronises
  * `stream`. */
 mk_status mk_counters(mk_graph *g, uint64_t *out, int n, int reset, void *stream);

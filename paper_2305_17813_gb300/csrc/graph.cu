@@ -160,38 +160,43 @@ __global__ void k_rule(uint32_t *deg, uint32_t V, float per_bucket)
 // UpdateSlabPointers (paper, Sec. "Graph Primitives", Fig.
 // "UpdateSlabPointers()"): for every updated list, walk from its marker slab
 // to the last slab; the new marker is that slab and the first free key lane
-// in it, or kInvalidLane when it is full; the updated flag is cleared.
-// Warp-cooperative: each warp owns 32 consecutive lists and dequeues the
-// updated ones one at a time (paper, Algorithm "Iteration Scheme 1").
-__global__ void k_update_slab_pointers(GView g, uint32_t max_hops)
+// in it, or kInvalidLane when it is full; the updated flag is cleared.  The
+// updated lists are read from the updated-list log; every 8-lane group of
+// every warp takes one logged list at a time and walks it with 16-byte loads
+// (lane sub holds words 4*sub .. 4*sub+3).
+__global__ void __launch_bounds__(256) k_update_slab_pointers(GView g, uint32_t max_hops)
 {
-    const uint32_t lane = lane_id();
-    const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
-    if (base >= g.H)
-        return;
-    const uint64_t l = base + lane;
-    bool todo = l < g.H && g.lupd[l];
+    const uint32_t lane = lane_id(), sub = lane & 7u, gi = lane >> 3, gbase = lane & ~7u;
+    const uint32_t n = min(*(volatile const uint32_t *)&g.st->ulog_count, g.H);
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
     unsigned long long loads = 0;
-    uint32_t q;
-    while ((q = __ballot_sync(kFull, todo)) != 0) {
-        const uint32_t leader = __ffs(q) - 1;
-        if (lane == leader)
-            todo = false;
-        const uint32_t list = (uint32_t)(base + leader);
-        uint32_t slab = (uint32_t)(g.lmark[list] >> 32);
-        uint32_t v = 0, nxt = kNil;
-        for (uint32_t hop = 0; hop < max_hops; ++hop) {
-            v = slab_ptr(g, slab)[lane];
-            ++loads;
-            nxt = __shfl_sync(kFull, v, kNextLane);
-            if (nxt == kNil)
-                break;
-            slab = nxt;
+    for (uint64_t base = warp0 * 4; base < n; base += gs) {
+        const uint64_t i = base + gi;
+        const uint32_t list = i < n ? g.ulog[i] : kNil;
+        uint32_t slab = list != kNil ? (uint32_t)(g.lmark[list] >> 32) : kNil;
+        bool active = slab != kNil;
+        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+        for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+            if (active)
+                x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
+            loads += __popc(__ballot_sync(kFull, active && sub == 0));
+            const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
+            if (active) {
+                if (nxt == kNil || hop + 1 >= max_hops)
+                    active = false; // x keeps the last slab
+                else
+                    slab = nxt;
+            }
         }
-        const uint32_t em = __ballot_sync(kFull, is_key_lane(lane) && v == kEmptyKey);
-        if (lane == 0) {
-            const uint32_t mlane = em ? (uint32_t)(__ffs(em) - 1) : (uint32_t)kInvalidLane;
-            g.lmark[list] = ((unsigned long long)slab << 32) | mlane;
+        // first free key lane of the last slab: key words 4*sub and 4*sub+2
+        // (word 30, lane 7's third word, is not a key lane)
+        uint32_t fl = x.x == kEmptyKey ? 4 * sub : ((sub != 7u && x.z == kEmptyKey) ? 4 * sub + 2 : 32u);
+        fl = min(fl, __shfl_xor_sync(kFull, fl, 4));
+        fl = min(fl, __shfl_xor_sync(kFull, fl, 2));
+        fl = min(fl, __shfl_xor_sync(kFull, fl, 1));
+        if (sub == 0 && list != kNil) {
+            g.lmark[list] = ((unsigned long long)slab << 32) | (fl < 32 ? fl : (uint32_t)kInvalidLane);
             g.lupd[list] = 0;
         }
     }
@@ -302,7 +307,11 @@ __global__ void k_decode_export(const uint64_t *keys, const uint32_t *wts, uint6
         w[i] = wts[i];
 }
 
-__global__ void k_clear_dlog(DevState *st) { st->dlog_count = 0; }
+__global__ void k_clear_logs(DevState *st)
+{
+    st->dlog_count = 0;
+    st->ulog_count = 0;
+}
 
 // ---------------------------------------------------------------- host API
 
@@ -437,7 +446,9 @@ mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out)
     if (st == MK_OK)
         st = device_alloc(g, (void **)&v.lmark, (size_t)H * 8);
     if (st == MK_OK)
-        st = device_alloc(g, (void **)&v.lupd, (size_t)H);
+        st = device_alloc(g, (void **)&v.lupd, ((size_t)H + 3) & ~(size_t)3);
+    if (st == MK_OK)
+        st = device_alloc(g, (void **)&v.ulog, (size_t)H * 4);
     if (st == MK_OK)
         st = device_alloc(g, (void **)&v.owner, (size_t)(H + P) * 4);
     if (st == MK_OK)
@@ -452,6 +463,7 @@ mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out)
     k_set_vinfo<<<grid_for(V, 256), 256, 0, s>>>((uint2 *)v.vinfo, d_b, d_off, V);
     k_init_slabs<<<std::min<uint64_t>(grid_for(H * 32, 256), 152 * 64), 256, 0, s>>>(v.slabs, 0, H);
     cudaMemsetAsync(v.owner + H, 0xFF, (size_t)P * 4, s);
+    cudaMemsetAsync(v.lupd, 0, ((size_t)H + 3) & ~(size_t)3, s);
     k_init_lists<<<grid_for(V, 256), 256, 0, s>>>(v.vinfo, V, (uint32_t *)v.list_src, v.lmark, v.lupd, v.owner);
     k_init_bitmap<<<grid_for(v.pool_words, 256), 256, 0, s>>>(v.bitmap, v.pool_words, v.P);
     cudaMemsetAsync(g->d_state, 0, sizeof(DevState), s);
@@ -490,6 +502,7 @@ mk_status mk_graph_destroy(mk_graph *g)
     cudaFree((void *)v.list_src);
     cudaFree(v.lmark);
     cudaFree(v.lupd);
+    cudaFree(v.ulog);
     cudaFree(v.owner);
     cudaFree(g->d_state);
     cudaFree(g->d_kin);
@@ -517,8 +530,10 @@ mk_status mk_commit_batch(mk_graph *g, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t max_hops = g->v.P + 2;
     MK_TRY(timed(g, "update_slab_pointers", s, 2, [&]() {
-        k_update_slab_pointers<<<grid_for((uint64_t)g->v.H, 256), 256, 0, s>>>(g->v, max_hops);
-        k_clear_dlog<<<1, 1, 0, s>>>(g->d_state);
+        // one 8-lane group per logged list
+        const uint32_t grid = std::min<uint32_t>(grid_for(std::max<uint64_t>(g->ulog_bound, 1) * 8, 256), num_sms() * 16);
+        k_update_slab_pointers<<<grid, 256, 0, s>>>(g->v, max_hops);
+        k_clear_logs<<<1, 1, 0, s>>>(g->d_state);
         return cudaSuccess;
     }));
     // states that have applied every batch of this epoch stay incremental
@@ -529,6 +544,7 @@ mk_status mk_commit_batch(mk_graph *g, void *stream)
     }
     g->epoch++;
     g->dlog_bound = 0;
+    g->ulog_bound = 0;
     g->epoch_has_deletes = false;
     return MK_OK;
 }

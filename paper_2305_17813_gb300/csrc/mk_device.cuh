@@ -58,6 +58,12 @@ enum Counter {
     kCtrWccUpdEdges = 17,
     kCtrRounds = 18,       // BFS/SSSP rounds run by the persistent round kernel
     kCtrGridBarriers = 19, // grid barriers it crossed
+    kCtrScanOwners = 20,   // relax-into-invalid scan: slabs in use (copied)
+    kCtrScanSlabs = 21,    //   slabs read (source reached and valid)
+    kCtrScanEdges = 22,    //   live edges examined
+    kCtrScanTargets = 23,  //   edges into invalidated vertices (relaxed)
+    kCtrScanImproved = 24, //   invalidated vertices given a finite distance
+    kCtrJumpVertices = 25, // vertices visited by the invalidation pass
     kNumCounters = 32
 };
 
@@ -66,6 +72,8 @@ struct DevState {
     int status;                    // sticky error word
     uint32_t dlog_count;           // entries in the delete log
     unsigned long long pool_used;  // pool slabs allocated (kept with the bitmap)
+    uint32_t ulog_count;           // entries in the updated-list log
+    uint32_t pad;
     unsigned long long ctr[kNumCounters];
 };
 
@@ -81,7 +89,8 @@ struct GView {
     const uint32_t *list_src; // source vertex of each list
     uint32_t *owner;       // per slab (heads and pool): source vertex of its list, kNil if unused
     unsigned long long *lmark; // per list: marker slab << 32 | marker lane
-    uint8_t *lupd;         // per list: updated since the last commit
+    uint8_t *lupd;         // per list: updated since the last commit (H bytes, rounded up to whole words)
+    uint32_t *ulog;        // the lists updated since the last commit, in order of their first update
     DevState *st;
 };
 
@@ -129,6 +138,34 @@ __device__ __forceinline__ unsigned long long pack_pair(uint32_t key, uint32_t w
 __device__ __forceinline__ void set_status(DevState *st, int code)
 {
     atomicCAS(&st->status, 0, code);
+}
+
+// Warp-collective: every lane with `want` flags its list L as updated since
+// the last commit; the first flagging of a list in an epoch also appends it
+// to the updated-list log (one atomicAdd per warp for the whole warp's
+// appends), so later passes over the updated lists (UpdateIterator
+// consumers, UpdateSlabPointers) read the log instead of testing every
+// list's flag.  A flag is set with a 32-bit atomicOr on the word holding its
+// byte.
+__device__ __forceinline__ void mark_updated_warp(const GView &g, uint32_t L, bool want)
+{
+    if (want && *(volatile const uint8_t *)&g.lupd[L])
+        want = false;
+    if (want) {
+        uint32_t *word = reinterpret_cast<uint32_t *>(g.lupd + (L & ~3u));
+        const uint32_t bit = 1u << ((L & 3u) * 8);
+        want = !(atomicOr(word, bit) & bit);
+    }
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+    if (!m)
+        return;
+    uint32_t base = 0;
+    if (lane_id() == 0)
+        base = atomicAdd(&g.st->ulog_count, (uint32_t)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const uint32_t at = base + __popc(m & ((1u << lane_id()) - 1));
+    if (want && at < g.H) // always: a list is logged once per epoch
+        g.ulog[at] = L;
 }
 
 // Adds a per-warp count to a work counter (lane 0 only; v must be

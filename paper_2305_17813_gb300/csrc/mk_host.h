@@ -74,6 +74,7 @@ struct mk_graph {
     // change log of the current epoch: deleted (src << 32 | dst)
     unsigned long long *d_dlog = nullptr;
     uint64_t dlog_cap = 0, dlog_bound = 0;
+    uint64_t ulog_bound = 0;      // upper bound on the updated-list log's entries (<= H)
     uint64_t epoch = 0, change_seq = 0;
     bool epoch_has_deletes = false;
     std::map<std::pair<int, uint32_t>, mk::Consumer *> consumers;
@@ -149,6 +150,17 @@ inline int num_sms()
             sms = 1;
     }
     return sms;
+}
+
+// A persistent grid for `kernel` launched with `block` threads and no
+// dynamic shared memory: every SM filled to its occupancy limit.
+template <typename K>
+inline uint32_t resident_grid(K kernel, int block)
+{
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0) != cudaSuccess || per < 1)
+        per = 1;
+    return (uint32_t)(num_sms() * per);
 }
 
 inline uint32_t grid_for(uint64_t threads, uint32_t block)

@@ -14,6 +14,7 @@
 // kNoAllocMaxBatch edges.
 #include "mk_host.h"
 
+#include <algorithm>
 #include <mutex>
 
 using namespace mk;
@@ -114,6 +115,7 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
         size_t tb = kSortWorkspace;
         return sort_pairs_u64_u32(work, tb, kin, kout, iin, iout, n, bits, s);
     }));
+    g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 1, [&]() {
         k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, kout, iout, d_w, n, g->vbits, d_inserted, max_hops);

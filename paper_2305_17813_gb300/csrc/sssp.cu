@@ -26,6 +26,7 @@
 // host loop reads it every round).  If the cooperative launch is refused, the
 // same round body runs as one launch per round driven by the host.
 #include "mk_host.h"
+#include "tma.cuh"
 #include "walk.cuh"
 
 #include <algorithm>
@@ -98,51 +99,59 @@ struct RoundArgs {
 
 namespace {
 
-// One round over frontier F[0, n): warps stride over groups of 32 lists and
-// walk them four at a time (8-lane groups, walk_lists_g8_from), the head
-// slabs of the next four loaded before the current four are walked.
+// Relaxes edge (x, y, w) for every lane with `live` and enqueues the lists of
+// each vertex whose distance this lane lowered first in this round.  y's
+// vinfo entry is loaded before the stamp exchange so both are in flight
+// together.  Must be called by the full warp.
+__device__ __forceinline__ void relax_edge(const RoundArgs &a, uint32_t x, uint32_t dx, uint32_t y, uint32_t w,
+                                           bool live, uint32_t round, uint2 *Fn, uint32_t *cnt, int *overflow,
+                                           unsigned long long &edges, unsigned long long &improved)
+{
+    edges += __popc(__ballot_sync(kFull, live));
+    bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
+    uint2 vi = make_uint2(0, 0);
+    if (up)
+        vi = a.g.vinfo[y];
+    up = up && first_this_round(a.stamp, y, round);
+    improved += __popc(__ballot_sync(kFull, up));
+    enqueue_lists_vi(y, up, vi, Fn, cnt, a.cap, overflow);
+}
+
+// One round over frontier F[0, n): every 8-lane group of every warp takes
+// one list at a time (group index + k * groups in the grid), so a round's
+// lists are spread over all warps; each group's entry, source distance and
+// head slab are loaded one step ahead (the entry two steps ahead) while the
+// current list is relaxed.
 __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2 *Fn, uint32_t *cnt,
                            uint32_t round, uint64_t warp0, uint64_t nwarps)
 {
     const GView &g = a.g;
-    const uint32_t lane = lane_id(), gi = lane >> 3;
+    const uint32_t sub = lane_id() & 7u, gi = lane_id() >> 3;
     int *overflow = (int *)(a.ctr + kOverflow);
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
-    for (uint64_t base = warp0 * 32; base < n; base += nwarps * 32) {
-        const uint64_t i = base + lane;
-        bool todo = i < n;
-        // each lane fetches its own entry and the source's distance up front
-        const uint2 e = todo ? F[i] : make_uint2(0, 0);
-        const uint32_t mine = e.x, my_x = e.y;
-        const uint32_t my_dx = todo ? node_dist(__ldcg(&a.D[my_x])) : kInf32;
-        lists += __popc(__ballot_sync(kFull, todo));
-        todo = todo && my_dx != kInf32;
-        const uint32_t q = __ballot_sync(kFull, todo);
-        const uint32_t np = ((uint32_t)__popc(q) + 3) / 4;
-        uint32_t owner = group_item(q, 0, gi);
-        const uint32_t L0 = __shfl_sync(kFull, mine, owner & 31);
-        uint4 x0 = group_load(g, owner < 32 ? L0 : kNil);
-        for (uint32_t pass = 0; pass < np; ++pass) {
-            const uint32_t L = __shfl_sync(kFull, mine, owner & 31);
-            const bool has = owner < 32;
-            const uint32_t x = __shfl_sync(kFull, my_x, owner & 31);
-            const uint32_t dx0 = __shfl_sync(kFull, my_dx, owner & 31);
-            const uint32_t dx = has ? dx0 : kInf32;
-            // the next pass's head slabs
-            const uint32_t nowner = group_item(q, pass + 1, gi);
-            const uint32_t nL = __shfl_sync(kFull, mine, nowner & 31);
-            const uint4 nx0 = group_load(g, nowner < 32 ? nL : kNil);
-            slabs += walk_lists_g8_from(g, has ? L : kNil, true, x0, 0, a.max_hops,
-                                        [&](uint32_t y, uint32_t w, bool live) {
-                                            edges += __popc(__ballot_sync(kFull, live));
-                                            bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
-                                            up = up && first_this_round(a.stamp, y, round);
-                                            improved += __popc(__ballot_sync(kFull, up));
-                                            enqueue_lists(g, y, up, Fn, cnt, a.cap, overflow);
-                                        });
-            owner = nowner;
-            x0 = nx0;
-        }
+    const uint64_t gs = nwarps * 4; // groups in the grid
+    const uint2 none = make_uint2(kNil, 0);
+    uint64_t i = warp0 * 4 + gi;
+    // pipeline: entry e with its distance dx and head slab x0 (this step),
+    // entry ne (next step)
+    uint2 e = i < n ? F[i] : none;
+    uint2 ne = i + gs < n ? F[i + gs] : none;
+    uint32_t dx = e.x != kNil ? node_dist(__ldcg(&a.D[e.y])) : kInf32;
+    uint4 x0 = group_load(g, e.x);
+    for (uint64_t base = warp0 * 4; base < n; base += gs, i += gs) {
+        const uint2 nne = i + 2 * gs < n ? F[i + 2 * gs] : none;
+        const uint32_t ndx = ne.x != kNil ? node_dist(__ldcg(&a.D[ne.y])) : kInf32;
+        const uint4 nx0 = group_load(g, ne.x);
+        lists += __popc(__ballot_sync(kFull, e.x != kNil && sub == 0));
+        const uint32_t L = dx != kInf32 ? e.x : kNil;
+        const uint32_t x = e.y, d = dx;
+        slabs += walk_lists_g8_from(g, L, true, x0, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
+            relax_edge(a, x, d, y, w, live, round, Fn, cnt, overflow, edges, improved);
+        });
+        e = ne;
+        ne = nne;
+        dx = ndx;
+        x0 = nx0;
     }
     count_add(g.st, kCtrRelaxLists, lists);
     count_add(g.st, kCtrRelaxSlabs, slabs);
@@ -207,7 +216,7 @@ __device__ bool grid_barrier(uint32_t *bar)
 // phase sits between two grid barriers, so no block reads a global size
 // while block 0 changes them, and the others wait at one barrier instead of
 // one per round.
-__global__ void __launch_bounds__(256, 3) k_rounds(RoundArgs a)
+__global__ void __launch_bounds__(256, 4) k_rounds(RoundArgs a)
 {
     __shared__ uint32_t solo_cnt[3];
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -342,6 +351,7 @@ __global__ void k_inv_jump(RoundArgs a)
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if ((v & ~31u) >= a.g.V)
         return;
+    count_add(a.g.st, kCtrJumpVertices, __popc(__ballot_sync(kFull, v < a.g.V)));
     bool bad = false;
     if (v < a.g.V && v != a.source && __ldcg(&a.D[v]) != kInfNode) {
         uint32_t x = v, hops = 0;
@@ -383,121 +393,150 @@ __global__ void k_inv_jump(RoundArgs a)
 // invalidated by this call.  The target test reads the invalidation bitmap,
 // which stays fixed during the pass, so every such edge is relaxed even after
 // another in-neighbour has already given its target a finite distance; does
-// nothing if nothing was invalidated.  A streaming scan over every slab in
-// use (through the per-slab owner array): a warp takes 32 consecutive slabs,
-// reads their owners in one coalesced load and the owners' tree nodes in one
-// gather, compacts the slabs whose source has a finite distance, and reads
-// those four per step, one per 8-lane group, loading the next step's slabs
-// before relaxing this step's edges.
-__global__ void __launch_bounds__(256) k_relax_into_invalid_slabs(RoundArgs a)
+// nothing if nothing was invalidated.  A streaming scan over the whole slab
+// array (scan_slab_chunks: the slabs in use, 32-slab chunks staged in shared
+// memory by bulk copies, the owners' tree nodes gathered a chunk ahead); the
+// slabs whose source has a finite distance are relaxed, one per lane.  Only
+// distances change here (64-bit atomic minima whose results are not needed);
+// the improved targets are enqueued by k_enqueue_invalid.
+__global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(RoundArgs a)
 {
-    __shared__ uint8_t comp[8][32];
+    __shared__ ScanSmem sm;
     const GView &g = a.g;
     if (ld_volatile(a.ctr + kInvTotal) == 0)
         return;
-    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, w = threadIdx.x >> 5;
-    const uint64_t total = (uint64_t)g.H + g.P;
-    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
-    int *overflow = (int *)(a.ctr + kOverflow);
-    const uint4 none = make_uint4(kEmptyKey, kFull, kFull, kFull);
-    unsigned long long slabs = 0, edges = 0, improved = 0;
-    for (uint64_t c = warp0 * 32; c < total; c += nwarps * 32) {
-        // 32 consecutive slabs: owners (one coalesced load), then the owners'
-        // distances; only slabs of reachable, valid sources are read
-        const uint32_t own_l = c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil;
-        const uint32_t dx_l = own_l != kNil ? node_dist(__ldcg(&a.D[own_l])) : kInf32;
-        const uint32_t live = __ballot_sync(kFull, dx_l != kInf32);
-        const uint32_t n = __popc(live);
-        if (dx_l != kInf32)
-            comp[w][__popc(live & ((1u << lane) - 1))] = (uint8_t)lane;
-        __syncwarp();
-        uint32_t it = gi < n ? comp[w][gi] : 32u;
-        uint4 x = none;
-        if (it < 32)
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + it)) + sub * 4));
-        for (uint32_t k = gi; k - gi < n; k += 4) {
-            const uint32_t nit = k + 4 < n ? comp[w][k + 4] : 32u;
-            uint4 nx = none;
-            if (nit < 32)
-                nx = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + nit)) + sub * 4));
-            const bool active = it < 32;
-            const uint32_t own = __shfl_sync(kFull, own_l, it & 31);
-            const uint32_t dx = __shfl_sync(kFull, dx_l, it & 31);
-            slabs += __popc(__ballot_sync(kFull, active && sub == 0));
-            const bool last = sub == 7u;
+    const uint32_t lane = lane_id();
+    unsigned long long slabs = 0, edges = 0, owners = 0, targets = 0;
+    const bool ok = scan_slab_chunks(
+        g, sm,
+        [&](uint32_t own) {
+            owners += __popc(__ballot_sync(kFull, own != kNil));
+            return own != kNil ? node_dist(__ldcg(&a.D[own])) : kInf32;
+        },
+        [&](const uint4 *buf, const uint8_t *comp, uint32_t n, uint32_t own_l, uint32_t dx_l) {
+            // lane j takes the chunk's j-th slab in use whole: first the
+            // bitmap words of all its 15 destinations (loads in flight
+            // together), then the relaxations.  The slab's 16-byte parts are
+            // read in a lane-rotated order, so the eight lanes of each
+            // shared-memory phase hit distinct banks.
+            const bool has = lane < n;
+            const uint32_t it = has ? comp[lane] : 0u;
+            const uint32_t own = __shfl_sync(kFull, own_l, it);
+            const uint32_t dx = __shfl_sync(kFull, dx_l, it);
+            const bool active = has && dx != kInf32;
+            slabs += __popc(__ballot_sync(kFull, active));
+            if (!__any_sync(kFull, active))
+                return;
+            const uint4 *mine = buf + (active ? lane : 0) * 8;
+            uint32_t word[16];
 #pragma unroll
-            for (int k2 = 0; k2 < 2; ++k2) {
-                const uint32_t y = k2 ? x.z : x.x, wt = k2 ? x.w : x.y;
-                const bool live_e = active && !(k2 && last) && y < kTombKey;
-                edges += __popc(__ballot_sync(kFull, live_e));
-                const bool target = live_e && ((__ldg(&a.inv[y >> 5]) >> (y & 31)) & 1u); // fixed during the pass
-                bool up = target && relax(a.D, own, dx, y, a.unit ? 1u : wt);
-                up = up && first_this_round(a.stamp, y, round);
-                improved += __popc(__ballot_sync(kFull, up));
-                enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t qq = (q + lane) & 7u;
+                const uint4 v = mine[qq];
+                const bool l0 = active && v.x < kTombKey, l1 = active && qq != 7u && v.z < kTombKey;
+                word[2 * q] = l0 ? __ldg(&a.inv[v.x >> 5]) : 0u; // the bitmap is fixed during the pass
+                word[2 * q + 1] = l1 ? __ldg(&a.inv[v.z >> 5]) : 0u;
             }
-            x = nx;
-            it = nit;
-        }
-        __syncwarp();
-    }
-    count_add(g.st, kCtrSeedLists, slabs);
-    count_add(g.st, kCtrSeedSlabs, slabs);
-    count_add(g.st, kCtrSeedEdges, edges);
-    count_add(g.st, kCtrSeedImproved, improved);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t qq = (q + lane) & 7u;
+                const uint4 v = mine[qq];
+                const bool l0 = active && v.x < kTombKey, l1 = active && qq != 7u && v.z < kTombKey;
+                edges += __popc(__ballot_sync(kFull, l0)) + __popc(__ballot_sync(kFull, l1));
+                const bool t0 = l0 && ((word[2 * q] >> (v.x & 31)) & 1u);
+                const bool t1 = l1 && ((word[2 * q + 1] >> (v.z & 31)) & 1u);
+                targets += __popc(__ballot_sync(kFull, t0)) + __popc(__ballot_sync(kFull, t1));
+                if (t0) {
+                    const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : v.y);
+                    if (nd < kInf32)
+                        atomicMin(&a.D[v.x], (nd << 32) | own);
+                }
+                if (t1) {
+                    const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : v.w);
+                    if (nd < kInf32)
+                        atomicMin(&a.D[v.z], (nd << 32) | own);
+                }
+            }
+        });
+    if (!ok)
+        set_status(g.st, kErrTimeout);
+    count_add(g.st, kCtrScanOwners, owners);
+    count_add(g.st, kCtrScanSlabs, slabs);
+    count_add(g.st, kCtrScanEdges, edges);
+    count_add(g.st, kCtrScanTargets, targets);
 }
 
-// Incremental seeds: relax the entries inserted since the last commit
-// (UpdateIterator over the lists flagged as updated).
+// Enqueues the lists of every vertex invalidated by this call that the pass
+// above gave a finite distance (one warp per 32-vertex word of the bitmap),
+// stamped with the prologue's round so that the incremental prologue does
+// not enqueue it again.
+__global__ void k_enqueue_invalid(RoundArgs a)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t word = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    if (word >= ((uint64_t)a.g.V + 31) / 32 || ld_volatile(a.ctr + kInvTotal) == 0)
+        return;
+    const uint32_t bits = __ldcg(&a.inv[word]);
+    if (bits == 0)
+        return;
+    const uint32_t y = (uint32_t)word * 32 + lane;
+    bool pred = (bits >> lane) & 1u;
+    uint2 vi = make_uint2(0, 0);
+    if (pred) {
+        pred = __ldcg(&a.D[y]) != kInfNode;
+        if (pred) {
+            vi = a.g.vinfo[y];
+            a.stamp[y] = ld_volatile(a.ctr + kRid) + 1;
+        }
+    }
+    count_add(a.g.st, kCtrScanImproved, __popc(__ballot_sync(kFull, pred)));
+    enqueue_lists_vi(y, pred, vi, a.front[0], a.ctr + kCnt0, a.cap, (int *)(a.ctr + kOverflow));
+}
+
+// Incremental seeds: relax the entries inserted since the last commit.
+// Every list in the updated-list log is walked from its UpdateIterator start
+// (the marker slab, skipping its lanes before the marker lane, or all of it
+// when it is full).  Every 8-lane group of every warp takes one list at a
+// time (group index + k * groups in the grid); the next list's log entry,
+// source and marker are loaded a step ahead.
 __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
 {
     const GView &g = a.g;
-    const uint32_t lane = lane_id(), gi = lane >> 3;
-    const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
-    if (base >= g.H)
+    const uint32_t sub = lane_id() & 7u, gi = lane_id() >> 3;
+    const uint32_t n = min(ld_volatile(&g.st->ulog_count), g.H);
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
+    if (warp0 * 4 >= n)
         return;
     const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
     int *overflow = (int *)(a.ctr + kOverflow);
-    const uint64_t l = base + lane;
-    bool todo = false;
-    uint32_t x = 0, dx = kInf32, my_first = 0, my_start = kNil;
-    if (l < g.H && g.lupd[l]) {
-        x = g.list_src[l];
-        dx = node_dist(__ldcg(&a.D[x]));
-        todo = dx != kInf32;
-        if (todo)
-            my_start = update_begin(g, (uint32_t)l, &my_first);
-    }
-    const uint32_t q = __ballot_sync(kFull, todo);
-    const uint32_t np = ((uint32_t)__popc(q) + 3) / 4;
-    unsigned long long slabs = 0, edges = 0, improved = 0;
-    // the first slab of each walk is loaded one pass ahead
-    uint32_t owner = group_item(q, 0, gi);
-    const uint32_t s0 = __shfl_sync(kFull, my_start, owner & 31);
-    uint4 x0 = group_load(g, owner < 32 ? s0 : kNil);
-    for (uint32_t pass = 0; pass < np; ++pass) {
-        const bool has = owner < 32;
-        const uint32_t src = __shfl_sync(kFull, x, owner & 31);
-        const uint32_t dsrc = __shfl_sync(kFull, dx, owner & 31);
-        const uint32_t first_lane = __shfl_sync(kFull, my_first, owner & 31);
-        const uint32_t start0 = __shfl_sync(kFull, my_start, owner & 31);
-        const uint32_t start = has ? start0 : kNil;
-        const uint32_t nowner = group_item(q, pass + 1, gi);
-        const uint32_t ns = __shfl_sync(kFull, my_start, nowner & 31);
-        const uint4 nx0 = group_load(g, nowner < 32 ? ns : kNil);
+    unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
+    uint64_t i = warp0 * 4 + gi;
+    uint32_t L = i < n ? g.ulog[i] : kNil;
+    uint32_t nL = i + gs < n ? g.ulog[i + gs] : kNil;
+    uint32_t src = L != kNil ? g.list_src[L] : 0;
+    unsigned long long mk = L != kNil ? g.lmark[L] : 0;
+    for (uint64_t base = warp0 * 4; base < n; base += gs, i += gs) {
+        const uint32_t nnL = i + 2 * gs < n ? g.ulog[i + 2 * gs] : kNil;
+        const uint32_t nsrc = nL != kNil ? g.list_src[nL] : 0;
+        const unsigned long long nmk = nL != kNil ? g.lmark[nL] : 0;
+        const uint32_t dx = L != kNil ? node_dist(__ldcg(&a.D[src])) : kInf32;
+        const uint32_t mlane = (uint32_t)(mk & 0xFF);
+        const uint32_t first_lane = mlane == kInvalidLane ? 32u : mlane;
+        const bool go = L != kNil && dx != kInf32;
+        const uint32_t start = go ? (uint32_t)(mk >> 32) : kNil;
+        const uint4 x0 = group_load(g, start);
+        lists += __popc(__ballot_sync(kFull, go && sub == 0));
+        const uint32_t x = src;
         slabs += walk_lists_g8_from(g, start, true, x0, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            edges += __popc(__ballot_sync(kFull, live));
-            bool up = live && relax(a.D, src, dsrc, y, a.unit ? 1u : w);
-            up = up && first_this_round(a.stamp, y, round);
-            improved += __popc(__ballot_sync(kFull, up));
-            enqueue_lists(g, y, up, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+            relax_edge(a, x, dx, y, w, live, round, a.front[0], a.ctr + kCnt0, overflow, edges, improved);
         });
-        owner = nowner;
-        x0 = nx0;
+        L = nL;
+        nL = nnL;
+        src = nsrc;
+        mk = nmk;
     }
-    count_add(g.st, kCtrSeedLists, __popc(q));
+    count_add(g.st, kCtrSeedLists, lists);
     count_add(g.st, kCtrSeedSlabs, slabs);
     count_add(g.st, kCtrSeedEdges, edges);
     count_add(g.st, kCtrSeedImproved, improved);
@@ -677,18 +716,22 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
                 k_inv_jump<<<grid_for(V, 256), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
-            MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
-                const uint64_t warps = ((uint64_t)H + g->v.P + 31) / 32;
-                const uint32_t grid = (uint32_t)std::min<uint64_t>(grid_for(warps * 32, 256), (uint64_t)num_sms() * 16);
-                k_relax_into_invalid_slabs<<<grid, 256, 0, s>>>(a);
+            MK_TRY(timed(g, "sssp_relax_into_invalid", s, 2, [&]() {
+                static const uint32_t grid = resident_grid(k_relax_into_invalid_slabs, kScanWarps * 32);
+                k_relax_into_invalid_slabs<<<grid, kScanWarps * 32, 0, s>>>(a);
+                k_enqueue_invalid<<<grid_for(((uint64_t)V + 31) / 32 * 32, 256), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
         }
         // incremental prologue: edges inserted since the last commit
-        MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
-            k_relax_updated<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(a);
-            return cudaSuccess;
-        }));
+        if (g->ulog_bound) {
+            MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
+                // one 8-lane group per logged list
+                const uint64_t threads = g->ulog_bound * 8;
+                k_relax_updated<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 10), 256, 0, s>>>(a);
+                return cudaSuccess;
+            }));
+        }
     }
     // common epilogue: rounds until no distance improves
     MK_TRY(run_phase(g, a, "sssp_rounds", s));

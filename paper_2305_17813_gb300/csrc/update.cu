@@ -12,6 +12,8 @@
 // 64-bit atomicCAS and new slabs are linked with a CAS on the next lane.
 #include "mk_host.h"
 
+#include <algorithm>
+
 using namespace mk;
 
 // Validates the batch and writes sort keys and original positions.
@@ -102,6 +104,8 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
     const uint32_t w = (e.first && w_in) ? w_in[e.idx] : 1u;
     uint8_t done = 0;
     unsigned long long loads = 0, linked = 0;
+    uint32_t mark_list = 0; // the list this lane leads, if it received an insert
+    bool mark = false;
     uint32_t todo = __ballot_sync(kFull, e.first);
     while (todo) {
         const uint32_t leader = __ffs(todo) - 1;
@@ -132,8 +136,10 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
                 set_status(g.st, kErrTimeout);
             break;
         }
-        if (lane == leader)
-            g.lupd[L] = 1;
+        if (lane == leader) {
+            mark = true;
+            mark_list = L;
+        }
         // append at the tail
         uint32_t tail = slab;
         for (uint64_t guard = 0;; ++guard) {
@@ -225,6 +231,7 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
             }
         }
     }
+    mark_updated_warp(g, mark_list, mark);
     if (e.inb && flags)
         flags[e.idx] = done;
     count_add(g.st, kCtrInsertSlabs, loads);
@@ -318,6 +325,7 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     if (d_inserted)
         MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
     MK_TRY(stage(g, d_src, d_dst, d_w, n, s));
+    g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 1, [&]() {
         k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_kout, g->d_iout, d_w, n, g->vbits, d_inserted, max_hops);

@@ -29,37 +29,21 @@ __device__ __forceinline__ uint32_t walk_list(const GView &g, uint32_t slab, uin
     return hop;
 }
 
-// Start of the UpdateIterator of list L: the marker slab and lane, or the
-// slab after a full marker slab.  Returns kNil when nothing follows.
-__device__ __forceinline__ uint32_t update_begin(const GView &g, uint32_t L, uint32_t *first_lane)
-{
-    const unsigned long long m = g.lmark[L];
-    const uint32_t slab = (uint32_t)(m >> 32);
-    const uint32_t lane = (uint32_t)(m & 0xFF);
-    if (lane == kInvalidLane) {
-        *first_lane = 0;
-        return __ldcg(slab_ptr(g, slab) + kNextLane);
-    }
-    *first_lane = lane;
-    return slab;
-}
-
 // Appends the slab lists of vertex y (for every lane with pred) to the list
 // frontier `out` as <list, y> entries (the source travels with the list, so
 // a consumer needs no list_src lookup): lanes with few buckets write their
 // own entries after one warp-aggregated atomicAdd; a vertex with many
 // buckets is written by the whole warp.  Must be called by the full warp.
 // Sets *overflow on a lane whose entries would not fit in `cap`.
-__device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool pred, uint2 *out, uint32_t *count,
-                                              uint32_t cap, int *overflow)
+// enqueue_lists with y's vinfo entry already loaded by the caller (valid
+// where pred holds), so that load can overlap the caller's own atomics.
+__device__ __forceinline__ void enqueue_lists_vi(uint32_t y, bool pred, uint2 vi, uint2 *out, uint32_t *count,
+                                                 uint32_t cap, int *overflow)
 {
     constexpr uint32_t kSmall = 8;
     const uint32_t lane = lane_id();
     if (!__any_sync(kFull, pred))
         return;
-    uint2 vi = make_uint2(0, 0);
-    if (pred)
-        vi = g.vinfo[y];
     const bool small = pred && vi.y <= kSmall;
     // small vertices: exclusive scan of bucket counts across the warp
     uint32_t c = small ? vi.y : 0, incl = c;
@@ -102,6 +86,15 @@ __device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool p
                 *overflow = 1;
         }
     }
+}
+
+__device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool pred, uint2 *out, uint32_t *count,
+                                              uint32_t cap, int *overflow)
+{
+    uint2 vi = make_uint2(0, 0);
+    if (pred)
+        vi = g.vinfo[y];
+    enqueue_lists_vi(y, pred, vi, out, count, cap, overflow);
 }
 
 } // namespace mk

@@ -58,96 +58,128 @@ __device__ __forceinline__ uint32_t uf_load(const uint32_t *p, uint32_t x)
     return kCached ? p[x] : __ldcg(&p[x]);
 }
 
-// Two finds in lockstep, so that their dependent loads overlap; kNil
-// entries are left alone.  Parents strictly decrease along every path
-// (p[x] < x except at roots), so both walks end.
-template <bool kCached>
-__device__ __forceinline__ void uf_find2(uint32_t *p, uint32_t &x, uint32_t &y)
+// N finds in lockstep, so that their dependent loads overlap; kNil entries
+// are left alone.  Parents strictly decrease along every path (p[x] < x
+// except at roots), so every walk ends.
+template <int N, bool kCached>
+__device__ __forceinline__ void uf_find_n(uint32_t *p, uint32_t (&x)[N])
 {
-    bool dx = x == kNil, dy = y == kNil;
-    while (!(dx && dy)) {
-        uint32_t px = x, py = y;
-        if (!dx)
-            px = uf_load<kCached>(p, x);
-        if (!dy)
-            py = uf_load<kCached>(p, y);
-        dx = dx || px == x;
-        dy = dy || py == y;
-        uint32_t ppx = px, ppy = py;
-        if (!dx)
-            ppx = uf_load<kCached>(p, px);
-        if (!dy)
-            ppy = uf_load<kCached>(p, py);
-        if (!dx) {
-            if (ppx == px) {
-                x = px;
-                dx = true;
-            } else {
-                p[x] = ppx; // path halving: ppx is an ancestor of x
-                x = ppx;
-            }
+    bool done[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        done[i] = x[i] == kNil;
+    for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            all = all && done[i];
+        if (all)
+            return;
+        uint32_t px[N], ppx[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            px[i] = done[i] ? x[i] : uf_load<kCached>(p, x[i]);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            done[i] = done[i] || px[i] == x[i];
+            ppx[i] = done[i] ? px[i] : uf_load<kCached>(p, px[i]);
         }
-        if (!dy) {
-            if (ppy == py) {
-                y = py;
-                dy = true;
-            } else {
-                p[y] = ppy;
-                y = ppy;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (!done[i]) {
+                if (ppx[i] == px[i]) {
+                    x[i] = px[i]; // px is the root: no third load
+                    done[i] = true;
+                } else {
+                    p[x[i]] = ppx[i]; // path halving: ppx is an ancestor of x
+                    x[i] = ppx[i];
+                }
             }
         }
     }
 }
 
-// Union of the sets of up to 16 elements held by one 8-lane group, two per
-// lane: all roots are found in parallel, the group's smallest root m is the
-// anchor, and every other root r is hooked under it with one CAS on p[r]
-// from r to m.  The CAS succeeds only while r is still a root; m need not be
-// one any more, because any vertex with a smaller id lies in another tree
-// (ids never increase towards a root), so the hook joins the two sets and
-// keeps parents decreasing.  An element whose CAS loses (its root was
-// hooked by another warp meanwhile) retries with fresh roots of itself and
-// of the anchor, hooking the larger under the smaller.  Returns false if the
-// retry bound was hit.  Must be called by the full warp.
-__device__ __forceinline__ bool group_union2(uint32_t *p, uint32_t e0, bool a0, uint32_t e1, bool a1,
-                                             uint32_t limit)
+// Union of the sets of the elements held by one group of G lanes, N per lane
+// (act[i] says which are present): all roots are found in parallel, the
+// group's smallest root m is the anchor, and every other root r is hooked
+// under it with one CAS on p[r] from r to m.  The CAS succeeds only while r
+// is still a root; m need not be one any more, because any vertex with a
+// smaller id lies in another tree (ids never increase towards a root), so
+// the hook joins the two sets and keeps parents decreasing.  Elements of one
+// lane with the same root share one CAS.  An element whose CAS loses (its
+// root was hooked by another warp meanwhile) retries with fresh roots of
+// itself and of the anchor, hooking the larger under the smaller.  Returns
+// false if the retry bound was hit.  Must be called by the full warp.
+template <int G, int N>
+__device__ __forceinline__ bool group_union(uint32_t *p, const uint32_t (&e)[N], const bool (&act)[N],
+                                            uint32_t limit)
 {
-    uint32_t r0 = a0 ? e0 : kNil;
-    uint32_t r1 = a1 ? e1 : kNil;
-    uf_find2<true>(p, r0, r1);
-    uint32_t m = min(r0, r1);
-    m = min(m, __shfl_xor_sync(kFull, m, 4));
-    m = min(m, __shfl_xor_sync(kFull, m, 2));
-    m = min(m, __shfl_xor_sync(kFull, m, 1));
-    bool p0 = a0 && r0 != m, p1 = a1 && r1 != m;
-    // first attempt with the roots just found (r > m for every pending r)
-    if (p0 && atomicCAS(&p[r0], r0, m) == r0)
-        p0 = false;
-    if (p1) {
-        if (a0 && r1 == r0)
-            p1 = p0; // the same root: decided by the CAS above
-        else if (atomicCAS(&p[r1], r1, m) == r1)
-            p1 = false;
+    uint32_t r[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        r[i] = act[i] ? e[i] : kNil;
+    uf_find_n<N, true>(p, r);
+    uint32_t m = kNil;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        m = min(m, r[i]);
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1)
+        m = min(m, __shfl_xor_sync(kFull, m, o));
+    bool pend[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        pend[i] = act[i] && r[i] != m;
+        if (!pend[i])
+            continue;
+        // first attempt with the roots just found (r > m for every pending r)
+        bool decided = false, val = false;
+#pragma unroll
+        for (int j = 0; j < i; ++j)
+            if (!decided && act[j] && r[j] == r[i]) {
+                decided = true;
+                val = pend[j];
+            }
+        if (decided)
+            pend[i] = val;
+        else if (atomicCAS(&p[r[i]], r[i], m) == r[i])
+            pend[i] = false;
     }
     for (uint32_t it = 0; it < limit; ++it) {
-        if (!__any_sync(kFull, p0 || p1))
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            any = any || pend[i];
+        if (!__any_sync(kFull, any))
             return true;
-        uint32_t a = (p0 || p1) ? m : kNil, unused = kNil;
-        uf_find2<false>(p, a, unused);
-        uint32_t x0 = p0 ? r0 : kNil, x1 = p1 ? r1 : kNil;
-        uf_find2<false>(p, x0, x1);
-        if (p0) {
-            r0 = x0;
-            if (r0 == a || atomicCAS(&p[max(r0, a)], max(r0, a), min(r0, a)) == max(r0, a))
-                p0 = false;
-        }
-        if (p1) {
-            r1 = x1;
-            if (r1 == a || atomicCAS(&p[max(r1, a)], max(r1, a), min(r1, a)) == max(r1, a))
-                p1 = false;
+        uint32_t anc[1] = {any ? m : kNil};
+        uf_find_n<1, false>(p, anc);
+        const uint32_t a = anc[0];
+        uint32_t x[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            x[i] = pend[i] ? r[i] : kNil;
+        uf_find_n<N, false>(p, x);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (pend[i]) {
+                r[i] = x[i];
+                const uint32_t hi = max(r[i], a), lo = min(r[i], a);
+                if (r[i] == a || atomicCAS(&p[hi], hi, lo) == hi)
+                    pend[i] = false;
+            }
         }
     }
     return false;
+}
+
+// The two elements of one lane of an 8-lane group.
+__device__ __forceinline__ bool group_union2(uint32_t *p, uint32_t e0, bool a0, uint32_t e1, bool a1,
+                                             uint32_t limit)
+{
+    const uint32_t e[2] = {e0, e1};
+    const bool act[2] = {a0, a1};
+    return group_union<8, 2>(p, e, act, limit);
 }
 
 } // namespace
@@ -159,36 +191,35 @@ __global__ void k_uf_init(uint32_t *p, uint32_t V)
         p[v] = v;
 }
 
-// Unites src with every live destination of the selected lists.  Each warp
-// owns 32 consecutive lists and walks the selected ones four at a time, one
-// per 8-lane group with 16-byte loads (pairs 2*sub and 2*sub+1 per lane); the
-// unused slot of lane 7 (slab lane 30) carries the list's source, so each
-// slab's source and destinations are united in one group_union2.
-// all_lists: every list from its head; otherwise only updated lists from
-// their UpdateIterator start.
-__global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, int all_lists, uint32_t max_hops, int *failed)
+// Incremental pass: unites the source of every list in the updated-list log
+// with the destinations inserted since the last commit, read with the
+// UpdateIterator from the list's marker (the marker slab's lanes before the
+// marker lane are skipped; a full marker slab is skipped entirely).  Every
+// 8-lane group of every warp takes one list at a time (group index + k *
+// groups in the grid) and walks it with 16-byte loads (pairs 2*sub and
+// 2*sub+1 per lane); the unused slot of lane 7 (slab lane 30) carries the
+// list's source, so each slab's source and destinations are united in one
+// group_union2.  The next list's log entry, source and marker are loaded a
+// step ahead.
+__global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, uint32_t max_hops, int *failed)
 {
     const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
-    const uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull;
-    if (base >= g.H)
-        return;
-    const uint64_t l = base + lane;
-    const bool todo = l < g.H && (all_lists || g.lupd[l]);
-    // each lane fetches its own list's source and walk start up front
-    uint32_t my_src = 0, my_first = 0, my_start = kNil;
-    if (todo) {
-        my_src = g.list_src[l];
-        my_start = all_lists ? (uint32_t)l : update_begin(g, (uint32_t)l, &my_first);
-    }
-    const uint32_t q = __ballot_sync(kFull, todo);
+    const uint32_t n = min(*(volatile const uint32_t *)&g.st->ulog_count, g.H);
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
     unsigned long long slabs = 0, edges = 0;
-    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(q); ++pass) {
-        const uint32_t owner = group_item(q, pass, gi);
-        const bool has = owner < 32;
-        const uint32_t src = __shfl_sync(kFull, my_src, owner & 31);
-        uint32_t first_lane = __shfl_sync(kFull, my_first, owner & 31);
-        const uint32_t start0 = __shfl_sync(kFull, my_start, owner & 31);
-        uint32_t slab = has ? start0 : kNil;
+    uint64_t i = warp0 * 4 + gi;
+    uint32_t L = i < n ? g.ulog[i] : kNil;
+    uint32_t nL = i + gs < n ? g.ulog[i + gs] : kNil;
+    uint32_t src = L != kNil ? g.list_src[L] : 0;
+    unsigned long long mk = L != kNil ? g.lmark[L] : 0;
+    for (uint64_t base = warp0 * 4; base < n; base += gs, i += gs) {
+        const uint32_t nnL = i + 2 * gs < n ? g.ulog[i + 2 * gs] : kNil;
+        const uint32_t nsrc = nL != kNil ? g.list_src[nL] : 0;
+        const unsigned long long nmk = nL != kNil ? g.lmark[nL] : 0;
+        const uint32_t mlane = (uint32_t)(mk & 0xFF);
+        uint32_t first_lane = mlane == kInvalidLane ? 32u : mlane;
+        uint32_t slab = L != kNil ? (uint32_t)(mk >> 32) : kNil;
         bool active = slab != kNil;
         for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
             uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
@@ -210,55 +241,76 @@ __global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, int al
             }
             first_lane = 0;
         }
+        L = nL;
+        nL = nnL;
+        src = nsrc;
+        mk = nmk;
     }
-    count_add(g.st, all_lists ? kCtrWccSlabs : kCtrWccUpdSlabs, slabs);
-    count_add(g.st, all_lists ? kCtrWccEdges : kCtrWccUpdEdges, edges);
+    count_add(g.st, kCtrWccUpdSlabs, slabs);
+    count_add(g.st, kCtrWccUpdEdges, edges);
 }
 
-// Static pass as a streaming scan over every slab in use (heads and linked
-// pool slabs, found through the per-slab owner array) instead of chain
+// Static pass as a streaming scan over the whole slab array instead of chain
 // walks.  A warp takes 32 consecutive slabs at a time: one coalesced load of
-// their owners, the slabs in use compacted in shared memory, then four slabs
-// per step, one per 8-lane group (16-byte loads), with the next step's slabs
-// loaded before this step's finds so that the slab stream overlaps the
-// union-find latency.  Each slab's owner and its live destinations are
-// united in one group_union2, exactly as in the list walk.
-__global__ void __launch_bounds__(256, 6) k_uf_hook_slabs(GView g, uint32_t *p, int *failed)
+// their owners (per-slab source, kNil for an unused pool slab; read a chunk
+// ahead), the slabs in use compacted in shared memory, then eight slabs per
+// step, one per 4-lane group (lane s4 holds words 8*s4 .. 8*s4+7, i.e. pairs
+// 4*s4 .. 4*s4+3, as two 16-byte loads), the next step's slabs loaded before
+// this step's finds.  Each slab's owner (in the last lane's fourth slot: the
+// unused lane and the next lane) and its live destinations are united with
+// one group_union (four elements per lane, found in lockstep).  The scan
+// keeps the slabs in registers rather than staging them in shared memory:
+// the finds' parent loads depend on L1, which shared-memory buffers would
+// take away.
+__global__ void __launch_bounds__(256) k_uf_hook_slabs(GView g, uint32_t *p, int *failed)
 {
     __shared__ uint8_t comp[8][32];
-    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id(), g4 = lane >> 2, s4 = lane & 3u, w = threadIdx.x >> 5;
     const uint64_t total = (uint64_t)g.H + g.P;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 32;
     const uint4 none = make_uint4(kEmptyKey, kFull, kFull, kFull);
+    auto part = [&](uint64_t s, int h) {
+        return __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s) + s4 * 8 + h * 4));
+    };
     unsigned long long slabs = 0, edges = 0;
-    for (uint64_t c = warp0 * 32; c < total; c += nwarps * 32) {
-        const uint32_t own_l = c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil;
+    uint64_t c = warp0 * 32;
+    uint32_t own_next = c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil;
+    for (; c < total; c += stride) {
+        const uint32_t own_l = own_next;
+        own_next = c + stride + lane < total ? __ldcg(&g.owner[c + stride + lane]) : kNil;
         const uint32_t live = __ballot_sync(kFull, own_l != kNil);
         const uint32_t n = __popc(live);
         if (own_l != kNil)
             comp[w][__popc(live & ((1u << lane) - 1))] = (uint8_t)lane;
         __syncwarp();
-        uint32_t it = gi < n ? comp[w][gi] : 32u;
-        uint4 x = none;
-        if (it < 32)
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + it)) + sub * 4));
-        for (uint32_t k = gi; k - gi < n; k += 4) {
-            // prefetch the next step's slab
-            const uint32_t nit = k + 4 < n ? comp[w][k + 4] : 32u;
-            uint4 nx = none;
-            if (nit < 32)
-                nx = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)(c + nit)) + sub * 4));
+        uint32_t it = g4 < n ? comp[w][g4] : 32u;
+        uint4 lo = none, hi = none;
+        if (it < 32) {
+            lo = part(c + it, 0);
+            hi = part(c + it, 1);
+        }
+        for (uint32_t j = g4; j - g4 < n; j += 8) {
+            // the next step's slabs
+            const uint32_t nit = j + 8 < n ? comp[w][j + 8] : 32u;
+            uint4 nlo = none, nhi = none;
+            if (nit < 32) {
+                nlo = part(c + nit, 0);
+                nhi = part(c + nit, 1);
+            }
             const bool active = it < 32;
             const uint32_t own = __shfl_sync(kFull, own_l, it & 31);
-            slabs += __popc(__ballot_sync(kFull, active && sub == 0));
-            const bool last = sub == 7u;
-            const bool a0 = active && x.x < kTombKey;
-            const bool a1 = last ? active : (active && x.z < kTombKey);
-            edges += __popc(__ballot_sync(kFull, a0)) + __popc(__ballot_sync(kFull, a1 && !last));
-            if (!group_union2(p, x.x, a0, last ? own : x.z, a1, 1u << 20) && lane == 0)
+            slabs += __popc(__ballot_sync(kFull, active && s4 == 0));
+            const bool last = s4 == 3u;
+            const uint32_t e[4] = {lo.x, lo.z, hi.x, last ? own : hi.z};
+            const bool act[4] = {active && lo.x < kTombKey, active && lo.z < kTombKey, active && hi.x < kTombKey,
+                                 last ? active : (active && hi.z < kTombKey)};
+            edges += __popc(__ballot_sync(kFull, act[0])) + __popc(__ballot_sync(kFull, act[1])) +
+                     __popc(__ballot_sync(kFull, act[2])) + __popc(__ballot_sync(kFull, act[3] && !last));
+            if (!group_union<4, 4>(p, e, act, 1u << 20) && lane == 0)
                 *failed = 1;
-            x = nx;
+            lo = nlo;
+            hi = nhi;
             it = nit;
         }
         __syncwarp();
@@ -322,13 +374,15 @@ extern "C" mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream)
     }
     if (incremental) {
         MK_TRY(timed(g, "wcc_hook_updated", s, 1, [&]() {
-            k_uf_hook<<<grid_for((uint64_t)H, 256), 256, 0, s>>>(g->v, c->uf, 0, max_hops, failed);
+            // one 8-lane group per logged list
+            const uint64_t threads = std::max<uint64_t>(g->ulog_bound, 1) * 8;
+            k_uf_hook<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 12), 256, 0, s>>>(g->v, c->uf, max_hops,
+                                                                                               failed);
             return cudaSuccess;
         }));
     } else {
         MK_TRY(timed(g, "wcc_hook_all", s, 1, [&]() {
-            const uint64_t warps = ((uint64_t)H + g->v.P + 31) / 32;
-            const uint32_t grid = (uint32_t)std::min<uint64_t>(grid_for(warps * 32, 256), (uint64_t)num_sms() * 16);
+            static const uint32_t grid = resident_grid(k_uf_hook_slabs, 256);
             k_uf_hook_slabs<<<grid, 256, 0, s>>>(g->v, c->uf, failed);
             return cudaSuccess;
         }));
