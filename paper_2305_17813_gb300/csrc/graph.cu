@@ -2,6 +2,8 @@
 // per-list update metadata, UpdateSlabPointers, export and statistics.
 #include "mk_host.h"
 
+#include <vector>
+
 #include <algorithm>
 #include <cstring>
 
@@ -167,7 +169,7 @@ __global__ void k_rule(uint32_t *deg, uint32_t V, float per_bucket)
 __global__ void __launch_bounds__(256) k_update_slab_pointers(GView g, uint32_t max_hops)
 {
     const uint32_t lane = lane_id(), sub = lane & 7u, gi = lane >> 3, gbase = lane & ~7u;
-    const uint32_t n = min(*(volatile const uint32_t *)&g.st->ulog_count, g.H);
+    const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
     unsigned long long loads = 0;
@@ -678,13 +680,18 @@ mk_status mk_counters(mk_graph *g, uint64_t *out, int n, int reset, void *stream
     if (!g || n < 0 || (n > 0 && !out))
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long c[kNumCounters];
-    MK_CUDA(cudaMemcpyAsync(c, g->d_state->ctr, sizeof c, cudaMemcpyDeviceToHost, s));
+    std::vector<unsigned long long> c((size_t)kNumCounters * kSlots);
+    const size_t bytes = c.size() * sizeof(unsigned long long);
+    MK_CUDA(cudaMemcpyAsync(c.data(), g->d_state->ctr, bytes, cudaMemcpyDeviceToHost, s));
     if (reset)
-        MK_CUDA(cudaMemsetAsync(g->d_state->ctr, 0, sizeof c, s));
+        MK_CUDA(cudaMemsetAsync(g->d_state->ctr, 0, bytes, s));
     MK_CUDA(cudaStreamSynchronize(s));
-    for (int i = 0; i < n && i < (int)kNumCounters; ++i)
-        out[i] = c[i];
+    for (int i = 0; i < n && i < (int)kNumCounters; ++i) {
+        unsigned long long sum = 0;
+        for (uint32_t k = 0; k < kSlots; ++k)
+            sum += c[(size_t)i * kSlots + k];
+        out[i] = sum;
+    }
     return MK_OK;
 }
 
@@ -693,10 +700,13 @@ mk_status mk_pool_free(mk_graph *g, uint64_t *out, void *stream)
     if (!g || !out)
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long used = 0;
-    MK_CUDA(cudaMemcpyAsync(&used, &g->d_state->pool_used, 8, cudaMemcpyDeviceToHost, s));
+    long long slots[kSlots];
+    MK_CUDA(cudaMemcpyAsync(slots, g->d_state->pool_used, sizeof slots, cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaStreamSynchronize(s));
-    *out = used >= g->v.P ? 0 : g->v.P - used;
+    long long used = 0;
+    for (uint32_t k = 0; k < kSlots; ++k)
+        used += slots[k];
+    *out = used >= (long long)g->v.P ? 0 : g->v.P - (uint64_t)(used > 0 ? used : 0);
     return MK_OK;
 }
 

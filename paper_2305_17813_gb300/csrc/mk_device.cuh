@@ -67,15 +67,23 @@ enum Counter {
     kNumCounters = 32
 };
 
+// Tallies that many warps bump (work counters, pool slabs in use) are kept
+// in kSlots copies, the copy picked by block index, and summed when read:
+// one shared word bumped by every warp of a large launch serialises tens of
+// thousands of atomics on one L2 line.
+constexpr uint32_t kSlots = 64;
+
 // Mutable device-side state of one graph (one allocation).
 struct DevState {
     int status;                    // sticky error word
     uint32_t dlog_count;           // entries in the delete log
-    unsigned long long pool_used;  // pool slabs allocated (kept with the bitmap)
     uint32_t ulog_count;           // entries in the updated-list log
     uint32_t pad;
-    unsigned long long ctr[kNumCounters];
+    long long pool_used[kSlots];   // pool slabs allocated minus freed (kept with the bitmap), per slot
+    unsigned long long ctr[kNumCounters][kSlots];
 };
+
+__device__ __forceinline__ uint32_t slot_of_block() { return blockIdx.x & (kSlots - 1); }
 
 // Read-only view of one graph passed to kernels by value.
 struct GView {
@@ -140,14 +148,45 @@ __device__ __forceinline__ void set_status(DevState *st, int code)
     atomicCAS(&st->status, 0, code);
 }
 
-// Warp-collective: every lane with `want` flags its list L as updated since
-// the last commit; the first flagging of a list in an epoch also appends it
-// to the updated-list log (one atomicAdd per warp for the whole warp's
-// appends), so later passes over the updated lists (UpdateIterator
-// consumers, UpdateSlabPointers) read the log instead of testing every
-// list's flag.  A flag is set with a 32-bit atomicOr on the word holding its
-// byte.
-__device__ __forceinline__ void mark_updated_warp(const GView &g, uint32_t L, bool want)
+// Block-collective (every thread of the block calls it, converged):
+// appends `value` for every thread with pred to arr (capacity cap) at slots
+// reserved with one global atomicAdd per block.  This is the paper's
+// warp-aggregated enqueue (Algorithm "Warp device APIs") lifted to the
+// block: one atomic per warp on the single count word serialises when tens
+// of thousands of warps append.
+// `s2` is two words of shared memory.  Returns false for a thread whose slot
+// was at or past cap.
+template <typename T>
+__device__ __forceinline__ bool block_enqueue(T *arr, uint32_t *count, uint32_t cap, T value, bool pred, uint32_t *s2)
+{
+    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, pred);
+    if (threadIdx.x == 0)
+        s2[0] = 0;
+    __syncthreads();
+    uint32_t woff = 0;
+    if (lane_id() == 0 && mask)
+        woff = atomicAdd(&s2[0], (uint32_t)__popc(mask));
+    __syncthreads();
+    if (threadIdx.x == 0 && s2[0])
+        s2[1] = atomicAdd(count, s2[0]);
+    __syncthreads();
+    woff = __shfl_sync(0xFFFFFFFFu, woff, 0);
+    if (!pred)
+        return true;
+    const uint32_t at = s2[1] + woff + __popc(mask & ((1u << lane_id()) - 1));
+    if (at >= cap)
+        return false;
+    arr[at] = value;
+    return true;
+}
+
+// Block-collective: every thread with `want` flags its list L as updated
+// since the last commit; the first flagging of a list in an epoch also
+// appends it to the updated-list log (block_enqueue), so later passes over
+// the updated lists (UpdateIterator consumers, UpdateSlabPointers) read the
+// log instead of testing every list's flag.  A flag is set with a 32-bit
+// atomicOr on the word holding its byte.
+__device__ __forceinline__ void mark_updated_block(const GView &g, uint32_t L, bool want, uint32_t *s2)
 {
     if (want && *(volatile const uint8_t *)&g.lupd[L])
         want = false;
@@ -156,16 +195,7 @@ __device__ __forceinline__ void mark_updated_warp(const GView &g, uint32_t L, bo
         const uint32_t bit = 1u << ((L & 3u) * 8);
         want = !(atomicOr(word, bit) & bit);
     }
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
-    if (!m)
-        return;
-    uint32_t base = 0;
-    if (lane_id() == 0)
-        base = atomicAdd(&g.st->ulog_count, (uint32_t)__popc(m));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    const uint32_t at = base + __popc(m & ((1u << lane_id()) - 1));
-    if (want && at < g.H) // always: a list is logged once per epoch
-        g.ulog[at] = L;
+    block_enqueue(g.ulog, &g.st->ulog_count, g.H, L, want, s2); // a list is logged once per epoch: fits
 }
 
 // Adds a per-warp count to a work counter (lane 0 only; v must be
@@ -173,7 +203,7 @@ __device__ __forceinline__ void mark_updated_warp(const GView &g, uint32_t L, bo
 __device__ __forceinline__ void count_add(DevState *st, int which, unsigned long long v)
 {
     if ((threadIdx.x & 31) == 0 && v)
-        atomicAdd(&st->ctr[which], v);
+        atomicAdd(&st->ctr[which][slot_of_block()], v);
 }
 
 __device__ __forceinline__ int read_status(const DevState *st)
@@ -181,32 +211,11 @@ __device__ __forceinline__ int read_status(const DevState *st)
     return *((volatile const int *)&st->status);
 }
 
-// Warp-aggregated append of one element per participating lane into a
-// compact array: one atomicAdd per warp, each lane writes at base + rank
-// (paper, Algorithm "Warp device APIs: broadcast, and frontier enqueue").
-// Must be called by the full warp.  Returns false (and writes nothing) for a
-// lane whose slot would be at or beyond `cap`.
-template <typename T>
-__device__ __forceinline__ bool warp_enqueue(T *arr, uint32_t *count, uint32_t cap, T value, bool pred)
-{
-    const uint32_t mask = __ballot_sync(kFull, pred);
-    if (mask == 0)
-        return true;
-    uint32_t base = 0;
-    const uint32_t leader = __ffs(mask) - 1;
-    if (lane_id() == leader)
-        base = atomicAdd(count, (uint32_t)__popc(mask));
-    base = __shfl_sync(kFull, base, leader);
-    if (pred) {
-        const uint32_t at = base + __popc(mask & lanemask_lt());
-        if (at < cap) {
-            arr[at] = value;
-            return true;
-        }
-        return false;
-    }
-    return true;
-}
+// The status word through the read-only path: one cached copy per SM
+// instead of one request per warp to a single L2 line.  A stale 0 only
+// delays an early exit.
+__device__ __forceinline__ int status_hint(const DevState *st) { return __ldg(&st->status); }
+
 
 // Warp-cooperative claim of one pool slab from the occupancy bitmap.  The
 // warp probes 32 consecutive words at once, starting at a word chosen by
@@ -239,7 +248,7 @@ __device__ __forceinline__ uint32_t alloc_slab(const GView &g, uint32_t salt)
                     word = old | (1u << b);
             }
             if (got != kNil)
-                atomicAdd(&g.st->pool_used, 1ull);
+                atomicAdd((unsigned long long *)&g.st->pool_used[slot_of_block()], 1ull);
             got = __shfl_sync(kFull, got, l);
             if (got != kNil)
                 return got;
@@ -253,7 +262,7 @@ __device__ __forceinline__ void free_slab(const GView &g, uint32_t s)
 {
     const uint32_t i = s - g.H;
     atomicAnd(&g.bitmap[i >> 5], ~(1u << (i & 31)));
-    atomicAdd(&g.st->pool_used, ~0ull);
+    atomicAdd((unsigned long long *)&g.st->pool_used[slot_of_block()], ~0ull);
 }
 
 } // namespace mk

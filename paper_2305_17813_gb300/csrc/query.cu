@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(512) k_query(GView g, const uint32_t *__restri
 {
     const unsigned long long warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t base = warp * 32;
-    if (base >= n || read_status(g.st) != 0)
+    if (base >= n || status_hint(g.st) != 0)
         return;
     unsigned long long loads = 0;
     query_chunk<G>(g, src, dst, n, base, bitmap + warp, w_out, max_hops, loads);
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(512) k_query_multi(GView g, const QueryReq *__
                                                      const uint64_t *__restrict__ prefix, uint32_t nreq_max,
                                                      const uint64_t *__restrict__ total, uint32_t max_hops)
 {
-    if (read_status(g.st) != 0)
+    if (status_hint(g.st) != 0)
         return;
     const uint64_t nchunks = total[0];
     const uint32_t nreq = total[1] < nreq_max ? (uint32_t)total[1] : nreq_max;

@@ -42,7 +42,7 @@ constexpr uint32_t kBarrierSpins = 1u << 24;
 enum {
     kCnt0 = 0,        // kCnt0..kCnt0+2: rotating frontier sizes
     kOverflow = 3,
-    kInvTotal = 4,
+    kInvTotal = 4,    // nonzero once this call invalidated a vertex
     kRoundsDone = 5,
     kClearWords = 8,  // words [0, 8) are cleared at the start of every call
     kSoloR = 6,       // round index reached by a solo phase of block 0
@@ -100,12 +100,12 @@ struct RoundArgs {
 namespace {
 
 // Relaxes edge (x, y, w) for every lane with `live` and enqueues the lists of
-// each vertex whose distance this lane lowered first in this round.  y's
-// vinfo entry is loaded before the stamp exchange so both are in flight
-// together.  Must be called by the full warp.
+// each vertex whose distance this lane lowered first in this round (staged in
+// the block's frontier buffer).  y's vinfo entry is loaded before the stamp
+// exchange so both are in flight together.  Must be called by the full warp.
 __device__ __forceinline__ void relax_edge(const RoundArgs &a, uint32_t x, uint32_t dx, uint32_t y, uint32_t w,
-                                           bool live, uint32_t round, uint2 *Fn, uint32_t *cnt, int *overflow,
-                                           unsigned long long &edges, unsigned long long &improved)
+                                           bool live, uint32_t round, BlockFrontier &bq, uint2 *Fn, uint32_t *cnt,
+                                           int *overflow, unsigned long long &edges, unsigned long long &improved)
 {
     edges += __popc(__ballot_sync(kFull, live));
     bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
@@ -114,44 +114,47 @@ __device__ __forceinline__ void relax_edge(const RoundArgs &a, uint32_t x, uint3
         vi = a.g.vinfo[y];
     up = up && first_this_round(a.stamp, y, round);
     improved += __popc(__ballot_sync(kFull, up));
-    enqueue_lists_vi(y, up, vi, Fn, cnt, a.cap, overflow);
+    enqueue_lists_block(bq, y, up, vi, Fn, cnt, a.cap, overflow);
 }
 
-// One round over frontier F[0, n): every 8-lane group of every warp takes
-// one list at a time (group index + k * groups in the grid), so a round's
-// lists are spread over all warps; each group's entry, source distance and
-// head slab are loaded one step ahead (the entry two steps ahead) while the
-// current list is relaxed.
+// One round over frontier F[0, n): every 4-lane group of every warp takes
+// one list at a time (group index + k * groups in the grid; eight lists per
+// warp in flight), so a round's lists are spread over all warps; each
+// group's entry, source distance and head slab are loaded one step ahead
+// (the entry two steps ahead) while the current list is relaxed.
 __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2 *Fn, uint32_t *cnt,
-                           uint32_t round, uint64_t warp0, uint64_t nwarps)
+                           uint32_t round, uint64_t warp0, uint64_t nwarps, BlockFrontier &bq)
 {
     const GView &g = a.g;
-    const uint32_t sub = lane_id() & 7u, gi = lane_id() >> 3;
+    const uint32_t s4 = lane_id() & 3u, g4 = lane_id() >> 2;
     int *overflow = (int *)(a.ctr + kOverflow);
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
-    const uint64_t gs = nwarps * 4; // groups in the grid
+    const uint64_t gs = nwarps * 8; // groups in the grid
     const uint2 none = make_uint2(kNil, 0);
-    uint64_t i = warp0 * 4 + gi;
-    // pipeline: entry e with its distance dx and head slab x0 (this step),
-    // entry ne (next step)
+    uint64_t i = warp0 * 8 + g4;
+    // pipeline: entry e with its distance dx and head slab (lo, hi) (this
+    // step), entry ne (next step)
     uint2 e = i < n ? F[i] : none;
     uint2 ne = i + gs < n ? F[i + gs] : none;
     uint32_t dx = e.x != kNil ? node_dist(__ldcg(&a.D[e.y])) : kInf32;
-    uint4 x0 = group_load(g, e.x);
-    for (uint64_t base = warp0 * 4; base < n; base += gs, i += gs) {
+    uint4 lo, hi;
+    group4_load(g, e.x, lo, hi);
+    for (uint64_t base = warp0 * 8; base < n; base += gs, i += gs) {
         const uint2 nne = i + 2 * gs < n ? F[i + 2 * gs] : none;
         const uint32_t ndx = ne.x != kNil ? node_dist(__ldcg(&a.D[ne.y])) : kInf32;
-        const uint4 nx0 = group_load(g, ne.x);
-        lists += __popc(__ballot_sync(kFull, e.x != kNil && sub == 0));
+        uint4 nlo, nhi;
+        group4_load(g, ne.x, nlo, nhi);
+        lists += __popc(__ballot_sync(kFull, e.x != kNil && s4 == 0));
         const uint32_t L = dx != kInf32 ? e.x : kNil;
         const uint32_t x = e.y, d = dx;
-        slabs += walk_lists_g8_from(g, L, true, x0, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            relax_edge(a, x, d, y, w, live, round, Fn, cnt, overflow, edges, improved);
+        slabs += walk_lists_g4_from(g, L, true, lo, hi, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
+            relax_edge(a, x, d, y, w, live, round, bq, Fn, cnt, overflow, edges, improved);
         });
         e = ne;
         ne = nne;
         dx = ndx;
-        x0 = nx0;
+        lo = nlo;
+        hi = nhi;
     }
     count_add(g.st, kCtrRelaxLists, lists);
     count_add(g.st, kCtrRelaxSlabs, slabs);
@@ -162,15 +165,17 @@ __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2
 // Round r of a phase: reads the size in cnts[r % 3], appends to
 // cnts[(r+1) % 3] and clears cnts[(r+2) % 3] for round r+1 (cnts: the three
 // global counters, or block 0's shared copies during a solo phase).
-// Frontier r is front[r & 1].
+// Frontier r is front[r & 1].  Called by whole blocks: the block's staged
+// entries are flushed at the end.
 __device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t *cnts, uint32_t r, uint32_t n, uint64_t warp0,
-                                           uint64_t nwarps, uint32_t rid)
+                                           uint64_t nwarps, uint32_t rid, BlockFrontier &bq)
 {
     const uint32_t in = r & 1;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         cnts[(r + 2) % 3] = 0;
     uint32_t *cnt = cnts + (r + 1) % 3;
-    relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps);
+    relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps, bq);
+    bq_flush(bq, a.front[in ^ 1], cnt, a.cap, (int *)(a.ctr + kOverflow));
 }
 
 // Bounded sense-counting grid barrier for a co-resident (cooperative) grid.
@@ -216,21 +221,29 @@ __device__ bool grid_barrier(uint32_t *bar)
 // phase sits between two grid barriers, so no block reads a global size
 // while block 0 changes them, and the others wait at one barrier instead of
 // one per round.
-__global__ void __launch_bounds__(256, 4) k_rounds(RoundArgs a)
+__global__ void __launch_bounds__(256, 3) k_rounds(RoundArgs a)
 {
     __shared__ uint32_t solo_cnt[3];
+    __shared__ BlockFrontier bq;
+    bq_init(bq);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t rid = ld_volatile(a.ctr + kRid);
+    const uint32_t rid = __ldg(a.ctr + kRid);
     uint32_t *gcnt = a.ctr + kCnt0;
     uint32_t r = 0, bars = 0;
     bool ok = true;
+    __shared__ uint32_t s_word;
     while (r < a.max_rounds) {
-        uint32_t n = ld_volatile(gcnt + r % 3);
+        // one read of the frontier size per block (the grid's warps would
+        // otherwise all read the same word)
+        if (threadIdx.x == 0)
+            s_word = ld_volatile(gcnt + r % 3);
+        __syncthreads();
+        uint32_t n = s_word;
         if (n == 0)
             break;
         if (n > kSoloLists) {
-            round_step(a, gcnt, r, n, warp0, nwarps, rid);
+            round_step(a, gcnt, r, n, warp0, nwarps, rid, bq);
             ++bars;
             if (!grid_barrier(a.ctr + kBar)) {
                 ok = false;
@@ -255,7 +268,7 @@ __global__ void __launch_bounds__(256, 4) k_rounds(RoundArgs a)
             __syncthreads();
             uint32_t steps = 0;
             do {
-                round_step(a, solo_cnt, r, n, bw0, bnw, rid);
+                round_step(a, solo_cnt, r, n, bw0, bnw, rid, bq);
                 __syncthreads();
                 ++r;
                 ++steps;
@@ -273,12 +286,16 @@ __global__ void __launch_bounds__(256, 4) k_rounds(RoundArgs a)
             ok = false;
             break;
         }
-        r = ld_volatile(a.ctr + kSoloR);
+        if (threadIdx.x == 0)
+            s_word = ld_volatile(a.ctr + kSoloR);
+        __syncthreads();
+        r = s_word;
+        __syncthreads(); // every thread has read s_word before thread 0 rewrites it
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr[kRoundsDone] = r;
-        atomicAdd(&a.g.st->ctr[kCtrRounds], (unsigned long long)r);
-        atomicAdd(&a.g.st->ctr[kCtrGridBarriers], (unsigned long long)bars);
+        atomicAdd(&a.g.st->ctr[kCtrRounds][0], (unsigned long long)r);
+        atomicAdd(&a.g.st->ctr[kCtrGridBarriers][0], (unsigned long long)bars);
         if (!ok || r >= a.max_rounds)
             set_status(a.g.st, kErrTimeout);
     }
@@ -287,9 +304,11 @@ __global__ void __launch_bounds__(256, 4) k_rounds(RoundArgs a)
 // One round, for the host-driven fallback.
 __global__ void __launch_bounds__(256) k_round_once(RoundArgs a, uint32_t r, uint32_t n)
 {
+    __shared__ BlockFrontier bq;
+    bq_init(bq);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    round_step(a, a.ctr + kCnt0, r, n, warp0, nwarps, ld_volatile(a.ctr + kRid));
+    round_step(a, a.ctr + kCnt0, r, n, warp0, nwarps, __ldg(a.ctr + kRid), bq);
     if (blockIdx.x == 0 && threadIdx.x == 0)
         a.ctr[kRoundsDone] = r + 1;
 }
@@ -314,16 +333,23 @@ __global__ void k_invalidate(const unsigned long long *dlog, const DevState *st,
 {
     const uint32_t n = st->dlog_count;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
+    if ((i & ~31u) >= n)
         return;
-    const unsigned long long e = dlog[i];
-    const uint32_t u = (uint32_t)(e >> 32), v = (uint32_t)e;
-    const unsigned long long dv = __ldcg(&a.D[v]);
-    if (v != a.source && dv != kInfNode && node_parent(dv) == u && atomicCAS(&a.D[v], dv, kInfNode) == dv) {
-        atomicAdd(a.ctr + kInvTotal, 1u);
-        atomicOr(&a.inv[v >> 5], 1u << (v & 31));
-        atomicAdd(&a.g.st->ctr[kCtrInvalidated], 1ull);
+    bool hit = false;
+    uint32_t v = 0;
+    if (i < n) {
+        const unsigned long long e = dlog[i];
+        const uint32_t u = (uint32_t)(e >> 32);
+        v = (uint32_t)e;
+        const unsigned long long dv = __ldcg(&a.D[v]);
+        hit = v != a.source && dv != kInfNode && node_parent(dv) == u && atomicCAS(&a.D[v], dv, kInfNode) == dv;
     }
+    if (hit)
+        atomicOr(&a.inv[v >> 5], 1u << (v & 31));
+    const uint32_t m = __ballot_sync(kFull, hit);
+    if (m && lane_id() == 0)
+        a.ctr[kInvTotal] = 1; // a flag: something was invalidated
+    count_add(a.g.st, kCtrInvalidated, __popc(m));
 }
 
 // The invalidation spreads to every tree descendant of the seeds: a vertex
@@ -343,9 +369,14 @@ __global__ void k_inv_anc_init(RoundArgs a)
     a.anc[v] = (v == a.source || d == kInfNode) ? v : node_parent(d);
 }
 
-// Each reached vertex finds its root (path halving on anc) and is invalidated
-// when the root is not the source.  The invalidated vertices of one warp set
-// their bits with one atomicOr (32 consecutive vertices share a bitmap word).
+// Each reached vertex walks anc up to its root and is invalidated when the
+// root is not the source; it then stores the root in its own anc entry, so
+// later walks that reach it jump straight to the root.  Only a vertex's own
+// entry is written: path halving would have every walk store into the
+// entries of the shared upper part of the tree (the hubs of a power-law
+// graph), and those writes contend.  The invalidated vertices of one warp
+// set their bits with one atomicOr (32 consecutive vertices share a bitmap
+// word).
 __global__ void k_inv_jump(RoundArgs a)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -356,20 +387,14 @@ __global__ void k_inv_jump(RoundArgs a)
     if (v < a.g.V && v != a.source && __ldcg(&a.D[v]) != kInfNode) {
         uint32_t x = v, hops = 0;
         bool ok = true;
-        // plain (L1-cacheable) loads: a stale anc value is an older ancestor,
-        // and roots never change, so every walk still ends at v's root
-        // while the source's line, where most walks end, stays in L1
+        // plain (L1-cacheable) loads: a stale anc value is an older ancestor
+        // and roots never change, so the walk still ends at v's root, while
+        // the upper part of the tree, where most walks pass, stays in L1
         for (;;) {
             const uint32_t px = a.anc[x];
             if (px == x)
                 break;
-            const uint32_t ppx = a.anc[px];
-            if (ppx == px) {
-                x = px;
-                break;
-            }
-            a.anc[x] = ppx; // path halving: ppx is an ancestor of x
-            x = ppx;
+            x = px;
             if (++hops > a.max_rounds) { // parent pointers not a forest: corrupted state
                 ok = false;
                 break;
@@ -377,6 +402,8 @@ __global__ void k_inv_jump(RoundArgs a)
         }
         if (!ok)
             set_status(a.g.st, kErrTimeout);
+        else
+            a.anc[v] = x;
         bad = ok && x != a.source;
     }
     if (bad)
@@ -384,7 +411,7 @@ __global__ void k_inv_jump(RoundArgs a)
     const uint32_t mask = __ballot_sync(kFull, bad);
     if (lane_id() == 0 && mask) {
         atomicOr(&a.inv[v >> 5], mask);
-        atomicAdd(a.ctr + kInvTotal, (uint32_t)__popc(mask));
+        a.ctr[kInvTotal] = 1;
         count_add(a.g.st, kCtrInvalidated, __popc(mask));
     }
 }
@@ -403,14 +430,15 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
 {
     __shared__ ScanSmem sm;
     const GView &g = a.g;
-    if (ld_volatile(a.ctr + kInvTotal) == 0)
+    if (__ldg(a.ctr + kInvTotal) == 0) // set by the kernels before this one
         return;
     const uint32_t lane = lane_id();
-    unsigned long long slabs = 0, edges = 0, owners = 0, targets = 0;
+    // per-lane tallies, summed over the warp once at the end
+    uint32_t slabs = 0, edges = 0, owners = 0, targets = 0;
     const bool ok = scan_slab_chunks(
         g, sm,
         [&](uint32_t own) {
-            owners += __popc(__ballot_sync(kFull, own != kNil));
+            owners += own != kNil;
             return own != kNil ? node_dist(__ldcg(&a.D[own])) : kInf32;
         },
         [&](const uint4 *buf, const uint8_t *comp, uint32_t n, uint32_t own_l, uint32_t dx_l) {
@@ -424,7 +452,7 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
             const uint32_t own = __shfl_sync(kFull, own_l, it);
             const uint32_t dx = __shfl_sync(kFull, dx_l, it);
             const bool active = has && dx != kInf32;
-            slabs += __popc(__ballot_sync(kFull, active));
+            slabs += active;
             if (!__any_sync(kFull, active))
                 return;
             const uint4 *mine = buf + (active ? lane : 0) * 8;
@@ -442,10 +470,10 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
                 const uint32_t qq = (q + lane) & 7u;
                 const uint4 v = mine[qq];
                 const bool l0 = active && v.x < kTombKey, l1 = active && qq != 7u && v.z < kTombKey;
-                edges += __popc(__ballot_sync(kFull, l0)) + __popc(__ballot_sync(kFull, l1));
+                edges += l0 + l1;
                 const bool t0 = l0 && ((word[2 * q] >> (v.x & 31)) & 1u);
                 const bool t1 = l1 && ((word[2 * q + 1] >> (v.z & 31)) & 1u);
-                targets += __popc(__ballot_sync(kFull, t0)) + __popc(__ballot_sync(kFull, t1));
+                targets += t0 + t1;
                 if (t0) {
                     const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : v.y);
                     if (nd < kInf32)
@@ -460,38 +488,91 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
         });
     if (!ok)
         set_status(g.st, kErrTimeout);
-    count_add(g.st, kCtrScanOwners, owners);
-    count_add(g.st, kCtrScanSlabs, slabs);
-    count_add(g.st, kCtrScanEdges, edges);
-    count_add(g.st, kCtrScanTargets, targets);
+    count_add(g.st, kCtrScanOwners, __reduce_add_sync(kFull, owners));
+    count_add(g.st, kCtrScanSlabs, __reduce_add_sync(kFull, slabs));
+    count_add(g.st, kCtrScanEdges, __reduce_add_sync(kFull, edges));
+    count_add(g.st, kCtrScanTargets, __reduce_add_sync(kFull, targets));
 }
 
 // Enqueues the lists of every vertex invalidated by this call that the pass
 // above gave a finite distance (one warp per 32-vertex word of the bitmap),
 // stamped with the prologue's round so that the incremental prologue does
-// not enqueue it again.
-__global__ void k_enqueue_invalid(RoundArgs a)
+// not enqueue it again.  The frontier slots of vertices with few lists are
+// reserved with one atomicAdd per block (a warp-level reservation would put
+// one atomic per 32 vertices on the single frontier counter); a vertex with
+// many lists is written by its whole warp.
+__global__ void __launch_bounds__(256) k_enqueue_invalid(RoundArgs a)
 {
+    constexpr uint32_t kSmall = 8;
+    __shared__ uint32_t s_total, s_base;
     const uint32_t lane = lane_id();
     const uint64_t word = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    if (word >= ((uint64_t)a.g.V + 31) / 32 || ld_volatile(a.ctr + kInvTotal) == 0)
-        return;
-    const uint32_t bits = __ldcg(&a.inv[word]);
-    if (bits == 0)
-        return;
-    const uint32_t y = (uint32_t)word * 32 + lane;
-    bool pred = (bits >> lane) & 1u;
+    if (threadIdx.x == 0)
+        s_total = 0;
+    __syncthreads();
+    bool pred = false;
     uint2 vi = make_uint2(0, 0);
-    if (pred) {
-        pred = __ldcg(&a.D[y]) != kInfNode;
+    const uint32_t y = (uint32_t)word * 32 + lane;
+    if (word < ((uint64_t)a.g.V + 31) / 32 && __ldg(a.ctr + kInvTotal) != 0) {
+        const uint32_t bits = __ldcg(&a.inv[word]);
+        pred = (bits >> lane) & 1u;
         if (pred) {
-            vi = a.g.vinfo[y];
-            a.stamp[y] = ld_volatile(a.ctr + kRid) + 1;
+            pred = __ldcg(&a.D[y]) != kInfNode;
+            if (pred) {
+                vi = a.g.vinfo[y];
+                a.stamp[y] = __ldg(a.ctr + kRid) + 1;
+            }
         }
     }
     count_add(a.g.st, kCtrScanImproved, __popc(__ballot_sync(kFull, pred)));
-    enqueue_lists_vi(y, pred, vi, a.front[0], a.ctr + kCnt0, a.cap, (int *)(a.ctr + kOverflow));
+    // small vertices: warp scan of bucket counts, then a block reservation
+    const bool small = pred && vi.y <= kSmall;
+    const uint32_t c = small ? vi.y : 0;
+    uint32_t incl = c;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o)
+            incl += t;
+    }
+    const uint32_t wtotal = __shfl_sync(kFull, incl, 31);
+    uint32_t woff = 0;
+    if (lane == 0 && wtotal)
+        woff = atomicAdd(&s_total, wtotal);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_total)
+        s_base = atomicAdd(a.ctr + kCnt0, s_total);
+    __syncthreads();
+    int *overflow = (int *)(a.ctr + kOverflow);
+    if (wtotal) {
+        const uint32_t at = s_base + __shfl_sync(kFull, woff, 0) + incl - c;
+        for (uint32_t k = 0; k < c; ++k) {
+            if (at + k < a.cap)
+                a.front[0][at + k] = make_uint2(vi.x + k, y);
+            else
+                *overflow = 1;
+        }
+    }
+    // large vertices: one at a time, written by the whole warp
+    uint32_t big = __ballot_sync(kFull, pred && !small);
+    while (big) {
+        const uint32_t l = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t first = __shfl_sync(kFull, vi.x, l), nb = __shfl_sync(kFull, vi.y, l);
+        const uint32_t yl = __shfl_sync(kFull, y, l);
+        uint32_t base = 0;
+        if (lane == 0)
+            base = atomicAdd(a.ctr + kCnt0, nb);
+        base = __shfl_sync(kFull, base, 0);
+        for (uint32_t k = lane; k < nb; k += 32) {
+            if (base + k < a.cap)
+                a.front[0][base + k] = make_uint2(first + k, yl);
+            else
+                *overflow = 1;
+        }
+    }
 }
+
 
 // Incremental seeds: relax the entries inserted since the last commit.
 // Every list in the updated-list log is walked from its UpdateIterator start
@@ -503,12 +584,12 @@ __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
 {
     const GView &g = a.g;
     const uint32_t sub = lane_id() & 7u, gi = lane_id() >> 3;
-    const uint32_t n = min(ld_volatile(&g.st->ulog_count), g.H);
+    const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
-    if (warp0 * 4 >= n)
-        return;
-    const uint32_t round = ld_volatile(a.ctr + kRid) + 1;
+    __shared__ BlockFrontier bq;
+    bq_init(bq);
+    const uint32_t round = __ldg(a.ctr + kRid) + 1;
     int *overflow = (int *)(a.ctr + kOverflow);
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
     uint64_t i = warp0 * 4 + gi;
@@ -529,13 +610,14 @@ __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
         lists += __popc(__ballot_sync(kFull, go && sub == 0));
         const uint32_t x = src;
         slabs += walk_lists_g8_from(g, start, true, x0, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            relax_edge(a, x, dx, y, w, live, round, a.front[0], a.ctr + kCnt0, overflow, edges, improved);
+            relax_edge(a, x, dx, y, w, live, round, bq, a.front[0], a.ctr + kCnt0, overflow, edges, improved);
         });
         L = nL;
         nL = nnL;
         src = nsrc;
         mk = nmk;
     }
+    bq_flush(bq, a.front[0], a.ctr + kCnt0, a.cap, overflow);
     count_add(g.st, kCtrSeedLists, lists);
     count_add(g.st, kCtrSeedSlabs, slabs);
     count_add(g.st, kCtrSeedEdges, edges);
@@ -716,9 +798,12 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
                 k_inv_jump<<<grid_for(V, 256), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
-            MK_TRY(timed(g, "sssp_relax_into_invalid", s, 2, [&]() {
+            MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
                 static const uint32_t grid = resident_grid(k_relax_into_invalid_slabs, kScanWarps * 32);
                 k_relax_into_invalid_slabs<<<grid, kScanWarps * 32, 0, s>>>(a);
+                return cudaSuccess;
+            }));
+            MK_TRY(timed(g, "sssp_enqueue_invalid", s, 1, [&]() {
                 k_enqueue_invalid<<<grid_for(((uint64_t)V + 31) / 32 * 32, 256), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));

@@ -95,18 +95,21 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
                                                 uint64_t n, uint32_t vbits, uint8_t *__restrict__ flags,
                                                 uint32_t max_hops)
 {
+    __shared__ uint32_t s2[2];
     const uint32_t lane = lane_id();
     const unsigned long long warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t pos = warp * 32 + lane;
-    if (warp * 32 >= n || read_status(g.st) != 0)
-        return;
-    const LaneEdge e = load_sorted(g, skey, sidx, n, vbits, pos);
+    // no early exit: the whole block meets in mark_updated_block
+    const bool run = warp * 32 < n && status_hint(g.st) == 0;
+    LaneEdge e{};
+    if (run)
+        e = load_sorted(g, skey, sidx, n, vbits, pos);
     const uint32_t w = (e.first && w_in) ? w_in[e.idx] : 1u;
     uint8_t done = 0;
     unsigned long long loads = 0, linked = 0;
     uint32_t mark_list = 0; // the list this lane leads, if it received an insert
     bool mark = false;
-    uint32_t todo = __ballot_sync(kFull, e.first);
+    uint32_t todo = run ? __ballot_sync(kFull, e.first) : 0u;
     while (todo) {
         const uint32_t leader = __ffs(todo) - 1;
         const uint32_t L = __shfl_sync(kFull, e.list, leader);
@@ -231,8 +234,8 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
             }
         }
     }
-    mark_updated_warp(g, mark_list, mark);
-    if (e.inb && flags)
+    mark_updated_block(g, mark_list, mark, s2);
+    if (run && e.inb && flags)
         flags[e.idx] = done;
     count_add(g.st, kCtrInsertSlabs, loads);
     count_add(g.st, kCtrInsertNewSlabs, linked);
@@ -241,21 +244,24 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
 // One warp per 32 sorted edges: find each destination in its list's chain,
 // overwrite the pair with TOMBSTONE, stop as soon as every destination of
 // the group is found or the chain ends; removed edges go to the change log
-// with a warp-aggregated enqueue.
+// with a block-aggregated enqueue.
 __global__ void __launch_bounds__(256) k_delete(GView g, const uint64_t *__restrict__ skey,
                                                 const uint32_t *__restrict__ sidx, uint64_t n, uint32_t vbits,
                                                 uint8_t *__restrict__ flags, unsigned long long *dlog,
                                                 uint32_t dlog_cap, uint32_t max_hops)
 {
+    __shared__ uint32_t s2[2];
     const uint32_t lane = lane_id();
     const unsigned long long warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t pos = warp * 32 + lane;
-    if (warp * 32 >= n || read_status(g.st) != 0)
-        return;
-    const LaneEdge e = load_sorted(g, skey, sidx, n, vbits, pos);
+    // no early exit: the whole block meets in block_enqueue
+    const bool run = warp * 32 < n && status_hint(g.st) == 0;
+    LaneEdge e{};
+    if (run)
+        e = load_sorted(g, skey, sidx, n, vbits, pos);
     bool removed = false;
     unsigned long long loads = 0;
-    uint32_t todo = __ballot_sync(kFull, e.first);
+    uint32_t todo = run ? __ballot_sync(kFull, e.first) : 0u;
     while (todo) {
         const uint32_t leader = __ffs(todo) - 1;
         const uint32_t L = __shfl_sync(kFull, e.list, leader);
@@ -282,9 +288,9 @@ __global__ void __launch_bounds__(256) k_delete(GView g, const uint64_t *__restr
         }
     }
     const unsigned long long rec = ((unsigned long long)e.src << 32) | e.dst;
-    if (!warp_enqueue(dlog, &g.st->dlog_count, dlog_cap, rec, removed) && lane == 0)
+    if (!block_enqueue(dlog, &g.st->dlog_count, dlog_cap, rec, removed, s2))
         set_status(g.st, kErrTimeout);
-    if (e.inb && flags)
+    if (run && e.inb && flags)
         flags[e.idx] = removed ? 1 : 0;
     count_add(g.st, kCtrDeleteSlabs, loads);
 }

@@ -29,24 +29,37 @@ __device__ __forceinline__ uint32_t walk_list(const GView &g, uint32_t slab, uin
     return hop;
 }
 
-// Appends the slab lists of vertex y (for every lane with pred) to the list
-// frontier `out` as <list, y> entries (the source travels with the list, so
-// a consumer needs no list_src lookup): lanes with few buckets write their
-// own entries after one warp-aggregated atomicAdd; a vertex with many
-// buckets is written by the whole warp.  Must be called by the full warp.
-// Sets *overflow on a lane whose entries would not fit in `cap`.
-// enqueue_lists with y's vinfo entry already loaded by the caller (valid
-// where pred holds), so that load can overlap the caller's own atomics.
-__device__ __forceinline__ void enqueue_lists_vi(uint32_t y, bool pred, uint2 vi, uint2 *out, uint32_t *count,
-                                                 uint32_t cap, int *overflow)
+// A block's staging area for frontier entries.  Warps reserve slots with
+// shared-memory atomics; the block copies the staged entries to the global
+// frontier with one global atomicAdd (bq_flush), instead of one atomic per
+// enqueuing warp on the single global frontier counter, where thousands of
+// warps a round would serialise.
+constexpr uint32_t kBlockBuf = 1024;
+struct BlockFrontier {
+    uint2 buf[kBlockBuf];
+    uint32_t count; // slots reserved; those at or past kBlockBuf went to the global frontier
+    uint32_t base;
+};
+
+// Appends the slab lists of vertex y (for every lane with pred; vi is y's
+// vinfo entry, loaded by the caller) to the list frontier as <list, y>
+// entries (the source travels with the list, so a consumer needs no list_src
+// lookup).  Lanes with few buckets write their entries through the block's
+// staging area: the warp's entries take slots [off, off + total) of the
+// block buffer and those that do not fit go to the global frontier directly.
+// A vertex with many buckets is written to the global frontier by the whole
+// warp.  Must be called by the full warp; sets *overflow for an entry that
+// would not fit in `cap`.
+__device__ __forceinline__ void enqueue_lists_block(BlockFrontier &bq, uint32_t y, bool pred, uint2 vi, uint2 *out,
+                                                    uint32_t *count, uint32_t cap, int *overflow)
 {
     constexpr uint32_t kSmall = 8;
     const uint32_t lane = lane_id();
     if (!__any_sync(kFull, pred))
         return;
     const bool small = pred && vi.y <= kSmall;
-    // small vertices: exclusive scan of bucket counts across the warp
-    uint32_t c = small ? vi.y : 0, incl = c;
+    const uint32_t c = small ? vi.y : 0;
+    uint32_t incl = c;
 #pragma unroll
     for (uint32_t o = 1; o < 32; o <<= 1) {
         const uint32_t t = __shfl_up_sync(kFull, incl, o);
@@ -55,19 +68,26 @@ __device__ __forceinline__ void enqueue_lists_vi(uint32_t y, bool pred, uint2 vi
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total) {
-        uint32_t base = 0;
+        uint32_t off = 0;
         if (lane == 0)
-            base = atomicAdd(count, total);
-        base = __shfl_sync(kFull, base, 0);
-        const uint32_t at = base + incl - c;
+            off = atomicAdd(&bq.count, total);
+        off = __shfl_sync(kFull, off, 0);
+        const uint32_t room = off < kBlockBuf ? min(kBlockBuf - off, total) : 0u;
+        uint32_t gbase = 0;
+        if (room < total && lane == 0)
+            gbase = atomicAdd(count, total - room);
+        gbase = __shfl_sync(kFull, gbase, 0);
         for (uint32_t k = 0; k < c; ++k) {
-            if (at + k < cap)
-                out[at + k] = make_uint2(vi.x + k, y);
+            const uint32_t t = incl - c + k; // the warp's t-th entry
+            const uint2 ent = make_uint2(vi.x + k, y);
+            if (t < room)
+                bq.buf[off + t] = ent;
+            else if (gbase + (t - room) < cap)
+                out[gbase + (t - room)] = ent;
             else
                 *overflow = 1;
         }
     }
-    // large vertices: one at a time, written by the whole warp
     uint32_t big = __ballot_sync(kFull, pred && !small);
     while (big) {
         const uint32_t l = __ffs(big) - 1;
@@ -88,14 +108,35 @@ __device__ __forceinline__ void enqueue_lists_vi(uint32_t y, bool pred, uint2 vi
     }
 }
 
-__device__ __forceinline__ void enqueue_lists(const GView &g, uint32_t y, bool pred, uint2 *out, uint32_t *count,
-                                              uint32_t cap, int *overflow)
+// Copies the block's staged entries to the global frontier and empties the
+// staging area.  Called by every thread of the block (it synchronises the
+// block).
+__device__ __forceinline__ void bq_flush(BlockFrontier &bq, uint2 *out, uint32_t *count, uint32_t cap, int *overflow)
 {
-    uint2 vi = make_uint2(0, 0);
-    if (pred)
-        vi = g.vinfo[y];
-    enqueue_lists_vi(y, pred, vi, out, count, cap, overflow);
+    __syncthreads();
+    const uint32_t n = min(bq.count, kBlockBuf);
+    if (threadIdx.x == 0)
+        bq.base = n ? atomicAdd(count, n) : 0u;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+        if (bq.base + t < cap)
+            out[bq.base + t] = bq.buf[t];
+        else
+            *overflow = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        bq.count = 0;
+    __syncthreads();
 }
+
+__device__ __forceinline__ void bq_init(BlockFrontier &bq)
+{
+    if (threadIdx.x == 0)
+        bq.count = 0;
+    __syncthreads();
+}
+
 
 } // namespace mk
 
@@ -161,6 +202,60 @@ __device__ __forceinline__ uint4 group_load(const GView &g, uint32_t s)
     if (s != kNil)
         x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, s) + (lane_id() & 7u) * 4));
     return x;
+}
+
+// Tiled walk with 4-lane groups (eight lists per warp): lane s4 of a group
+// holds words 8*s4 .. 8*s4+7 of the slab as two 16-byte vectors, i.e. pairs
+// 4*s4 .. 4*s4+3 (lane 3: pairs 12-14, then the unused lane and the next
+// lane); f(key, weight, live) is called four times per slab by every lane.
+// With have_first, (lo0, hi0) already hold the lane's part of `slab`
+// (group4_load).  Otherwise as walk_lists_g8.
+template <typename F>
+__device__ __forceinline__ uint32_t walk_lists_g4_from(const GView &g, uint32_t slab, bool have_first, uint4 lo0,
+                                                       uint4 hi0, uint32_t first_lane, uint32_t max_hops, F &&f)
+{
+    const uint32_t lane = lane_id(), s4 = lane & 3u, gbase = lane & ~3u;
+    bool active = slab != kNil;
+    uint32_t loads = 0;
+    for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+        uint4 lo = make_uint4(kEmptyKey, kFull, kFull, kFull), hi = lo;
+        if (hop == 0 && have_first) {
+            lo = lo0;
+            hi = hi0;
+        } else if (active) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + s4 * 8);
+            lo = __ldcg(p);
+            hi = __ldcg(p + 1);
+        }
+        loads += __popc(__ballot_sync(kFull, active && s4 == 0));
+        const uint32_t w0 = 8 * s4;
+        f(lo.x, lo.y, active && lo.x < kTombKey && w0 >= first_lane);
+        f(lo.z, lo.w, active && lo.z < kTombKey && w0 + 2 >= first_lane);
+        f(hi.x, hi.y, active && hi.x < kTombKey && w0 + 4 >= first_lane);
+        f(hi.z, hi.w, active && s4 != 3u && hi.z < kTombKey && w0 + 6 >= first_lane);
+        const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
+        if (active) {
+            if (nxt == kNil || hop + 1 >= max_hops)
+                active = false;
+            else
+                slab = nxt;
+        }
+        first_lane = 0;
+    }
+    return loads;
+}
+
+// The lane's 32-byte part of slab s for a 4-lane group (words 8*s4 ..
+// 8*s4+7); empty parts for s == kNil.
+__device__ __forceinline__ void group4_load(const GView &g, uint32_t s, uint4 &lo, uint4 &hi)
+{
+    lo = make_uint4(kEmptyKey, kFull, kFull, kFull);
+    hi = lo;
+    if (s != kNil) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(slab_ptr(g, s) + (lane_id() & 3u) * 8);
+        lo = __ldcg(p);
+        hi = __ldcg(p + 1);
+    }
 }
 
 // The k-th set bit of q handed to 8-lane group `gi` in pass `pass` (four

@@ -204,7 +204,7 @@ __global__ void k_uf_init(uint32_t *p, uint32_t V)
 __global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, uint32_t max_hops, int *failed)
 {
     const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
-    const uint32_t n = min(*(volatile const uint32_t *)&g.st->ulog_count, g.H);
+    const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
     unsigned long long slabs = 0, edges = 0;
