@@ -180,22 +180,18 @@ __device__ __forceinline__ bool block_enqueue(T *arr, uint32_t *count, uint32_t 
     return true;
 }
 
-// Block-collective: every thread with `want` flags its list L as updated
-// since the last commit; the first flagging of a list in an epoch also
-// appends it to the updated-list log (block_enqueue), so later passes over
-// the updated lists (UpdateIterator consumers, UpdateSlabPointers) read the
-// log instead of testing every list's flag.  A flag is set with a 32-bit
-// atomicOr on the word holding its byte.
-__device__ __forceinline__ void mark_updated_block(const GView &g, uint32_t L, bool want, uint32_t *s2)
+// Flags list L as updated since the last commit (a 32-bit atomicOr on the
+// word holding its byte); true if this call set the flag, i.e. L's first
+// update in the epoch, which puts L in the updated-list log: later passes
+// over the updated lists (UpdateIterator consumers, UpdateSlabPointers) read
+// the log instead of testing every list's flag.
+__device__ __forceinline__ bool flag_updated(const GView &g, uint32_t L)
 {
-    if (want && *(volatile const uint8_t *)&g.lupd[L])
-        want = false;
-    if (want) {
-        uint32_t *word = reinterpret_cast<uint32_t *>(g.lupd + (L & ~3u));
-        const uint32_t bit = 1u << ((L & 3u) * 8);
-        want = !(atomicOr(word, bit) & bit);
-    }
-    block_enqueue(g.ulog, &g.st->ulog_count, g.H, L, want, s2); // a list is logged once per epoch: fits
+    if (*(volatile const uint8_t *)&g.lupd[L])
+        return false;
+    uint32_t *word = reinterpret_cast<uint32_t *>(g.lupd + (L & ~3u));
+    const uint32_t bit = 1u << ((L & 3u) * 8);
+    return !(atomicOr(word, bit) & bit);
 }
 
 // Adds a per-warp count to a work counter (lane 0 only; v must be

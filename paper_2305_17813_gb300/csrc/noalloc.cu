@@ -23,10 +23,11 @@ using namespace mk;
 __global__ void k_build_keys(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
                              const uint32_t *__restrict__ w, uint64_t n, uint32_t V, uint32_t vbits,
                              uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, DevState *st);
-__global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restrict__ skey,
+__global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint64_t *__restrict__ skey,
                                                 const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ w_in,
                                                 uint64_t n, uint32_t vbits, uint8_t *__restrict__ flags,
-                                                uint32_t max_hops);
+                                                uint32_t max_hops, uint32_t *__restrict__ cand);
+__global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n);
 
 namespace {
 
@@ -117,8 +118,10 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
     }));
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
-    return timed(g, "insert", s, 1, [&]() {
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, kout, iout, d_w, n, g->vbits, d_inserted, max_hops);
+    return timed(g, "insert", s, 2, [&]() {
+        // the sort's input positions (iin) are free now: they hold the log nominations
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, kout, iout, d_w, n, g->vbits, d_inserted, max_hops, iin);
+        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, iin, n);
         return cudaSuccess;
     });
 }

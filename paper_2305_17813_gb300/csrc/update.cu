@@ -90,26 +90,25 @@ __device__ __forceinline__ bool match_slab(uint32_t v, uint32_t members, bool mi
 }
 
 // One warp per 32 sorted edges; see the file comment.
-__global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restrict__ skey,
+__global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint64_t *__restrict__ skey,
                                                 const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ w_in,
                                                 uint64_t n, uint32_t vbits, uint8_t *__restrict__ flags,
-                                                uint32_t max_hops)
+                                                uint32_t max_hops, uint32_t *__restrict__ cand)
 {
-    __shared__ uint32_t s2[2];
     const uint32_t lane = lane_id();
     const unsigned long long warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t pos = warp * 32 + lane;
-    // no early exit: the whole block meets in mark_updated_block
-    const bool run = warp * 32 < n && status_hint(g.st) == 0;
-    LaneEdge e{};
-    if (run)
-        e = load_sorted(g, skey, sidx, n, vbits, pos);
+    if (warp * 32 >= n)
+        return;
+    if (pos < n)
+        cand[pos] = kNil;
+    if (status_hint(g.st) != 0)
+        return;
+    const LaneEdge e = load_sorted(g, skey, sidx, n, vbits, pos);
     const uint32_t w = (e.first && w_in) ? w_in[e.idx] : 1u;
     uint8_t done = 0;
     unsigned long long loads = 0, linked = 0;
-    uint32_t mark_list = 0; // the list this lane leads, if it received an insert
-    bool mark = false;
-    uint32_t todo = run ? __ballot_sync(kFull, e.first) : 0u;
+    uint32_t todo = __ballot_sync(kFull, e.first);
     while (todo) {
         const uint32_t leader = __ffs(todo) - 1;
         const uint32_t L = __shfl_sync(kFull, e.list, leader);
@@ -139,10 +138,10 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
                 set_status(g.st, kErrTimeout);
             break;
         }
-        if (lane == leader) {
-            mark = true;
-            mark_list = L;
-        }
+        // the first insert into L in this epoch nominates L for the
+        // updated-list log (k_log_updated compacts the nominations)
+        if (lane == leader && flag_updated(g, L))
+            cand[pos] = L;
         // append at the tail
         uint32_t tail = slab;
         for (uint64_t guard = 0;; ++guard) {
@@ -234,18 +233,27 @@ __global__ void __launch_bounds__(256) k_insert(GView g, const uint64_t *__restr
             }
         }
     }
-    mark_updated_block(g, mark_list, mark, s2);
-    if (run && e.inb && flags)
+    if (e.inb && flags)
         flags[e.idx] = done;
     count_add(g.st, kCtrInsertSlabs, loads);
     count_add(g.st, kCtrInsertNewSlabs, linked);
+}
+
+// Appends the lists nominated by k_insert (cand[i] != kNil) to the
+// updated-list log, with one global atomicAdd per block.
+__global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n)
+{
+    __shared__ uint32_t s2[2];
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint32_t L = i < n ? cand[i] : kNil;
+    block_enqueue(g.ulog, &g.st->ulog_count, g.H, L, L != kNil, s2); // a list is logged once per epoch: fits
 }
 
 // One warp per 32 sorted edges: find each destination in its list's chain,
 // overwrite the pair with TOMBSTONE, stop as soon as every destination of
 // the group is found or the chain ends; removed edges go to the change log
 // with a block-aggregated enqueue.
-__global__ void __launch_bounds__(256) k_delete(GView g, const uint64_t *__restrict__ skey,
+__global__ void __launch_bounds__(256, 8) k_delete(GView g, const uint64_t *__restrict__ skey,
                                                 const uint32_t *__restrict__ sidx, uint64_t n, uint32_t vbits,
                                                 uint8_t *__restrict__ flags, unsigned long long *dlog,
                                                 uint32_t dlog_cap, uint32_t max_hops)
@@ -333,8 +341,11 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     MK_TRY(stage(g, d_src, d_dst, d_w, n, s));
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
-    return timed(g, "insert", s, 1, [&]() {
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_kout, g->d_iout, d_w, n, g->vbits, d_inserted, max_hops);
+    return timed(g, "insert", s, 2, [&]() {
+        // the sort's input positions (d_iin) are free now: they hold the log nominations
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_kout, g->d_iout, d_w, n, g->vbits, d_inserted, max_hops,
+                                                  g->d_iin);
+        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_iin, n);
         return cudaSuccess;
     });
 }
