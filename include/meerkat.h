@@ -122,10 +122,12 @@ mk_status mk_graph_destroy(mk_graph *g);
  * Evaluation", insertion: an edge is stored at the end of its slab list only
  * if it is not already present): an edge already in the graph keeps its
  * weight.  Within the batch the first occurrence of a repeated (src, dst)
- * is the one stored.  The batch is sorted and grouped by source (a radix sort
- * on (src, dst)); one warp handles the edges of one slab list, walks the
- * whole chain once with 128-byte slab loads, claims free pairs with 64-bit
- * atomicCAS and links pool slabs taken from the bitmap allocator.
+ * is the one stored (a hash set of the batch's pairs keeps each pair's
+ * first position).  Each tile of 256 edges is sorted and grouped by slab
+ * list (source and bucket) in shared memory; one warp handles the edges of
+ * one slab list, walks the whole chain once with 128-byte slab loads, claims
+ * free pairs with 64-bit atomicCAS and links pool slabs taken from the
+ * bitmap allocator.
  * d_inserted (n bytes, nullable): 1 where edge i was stored by this call.
  * If the pool runs out, the status becomes MK_ERR_POOL_EXHAUSTED and the
  * batch is applied partially: exactly the edges flagged 1 were stored.
@@ -143,13 +145,13 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
  * are identical to mk_insert_batch.
  *  - n <= MK_NOALLOC_MAX_BATCH (65,536); a larger n returns
  *    MK_ERR_INVALID_ARG and enqueues nothing.
- *  - The staging scratch is one fixed 3.5 MiB device array inside the library
+ *  - The staging scratch is one fixed 2 MiB device array inside the library
  *    (every GPU that loads the library holds it until the process exits).
- *    The first call on each device looks up the array's address and checks
- *    the sort workspace size (cudaGetSymbolAddress, no allocation); make that
- *    first call before any stream capture.
- *  - Every call on a device shares the array and it keeps the last call's
- *    contents; nothing in it needs to start at zero.  Two calls whose work
+ *    The first call on each device looks up the array's address
+ *    (cudaGetSymbolAddress, no allocation); make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the array; each call clears the part
+ *    that must start empty (the hash set) on its stream.  Two calls whose work
  *    overlaps on the GPU (different streams, or different graphs at the same
  *    time) race on it: order them on one stream or with events.
  *  - Calls no cudaMalloc, cudaFree or allocating library routine. */
@@ -160,7 +162,7 @@ mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src, const uint
 /* Deletes n edges: a present edge's pair becomes TOMBSTONE (never reused;
  * paper, Sec. "Experimental Evaluation", deletion), an absent edge is a
  * no-op; the first occurrence of a repeated pair is the one that deletes.
- * Sorted and grouped like mk_insert_batch.  d_deleted (n bytes, nullable):
+ * Staged like mk_insert_batch.  d_deleted (n bytes, nullable):
  * 1 where edge i was removed by this call.  Removed edges enter the graph's
  * change log for the decremental algorithms. */
 mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
@@ -419,7 +421,7 @@ mk_status mk_profile_enable(mk_graph *g, int on);
 mk_status mk_profile_read(mk_graph *g, mk_kernel_time *out, int cap, int *n_out);
 
 /* Number of kernel launches the library has made for this graph since
- * creation (sorting and scan calls included, counted from their launch
+ * creation (scan and export-sort calls included, counted from their launch
  * plans). */
 uint64_t mk_launch_count(mk_graph *g);
 

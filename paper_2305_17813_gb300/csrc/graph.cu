@@ -44,28 +44,22 @@ mk_status ensure_scratch(mk_graph *g, uint64_t n, cudaStream_t s)
         return MK_OK;
     uint64_t cap = std::max<uint64_t>(n, 1024);
     cap = std::max<uint64_t>(cap, g->scratch_cap + g->scratch_cap / 2);
+    uint64_t table = 1;
+    while (table < 2 * cap)
+        table <<= 1;
     MK_CUDA(cudaStreamSynchronize(s));
-    device_free(g, g->d_kin, g->scratch_cap * 8);
-    device_free(g, g->d_kout, g->scratch_cap * 8);
-    device_free(g, g->d_iin, g->scratch_cap * 4);
-    device_free(g, g->d_iout, g->scratch_cap * 4);
-    device_free(g, g->d_tmp, g->tmp_bytes);
-    g->d_kin = g->d_kout = nullptr;
-    g->d_iin = g->d_iout = nullptr;
-    g->d_tmp = nullptr;
-    g->scratch_cap = 0;
-    g->tmp_bytes = 0;
-    size_t tb = 0;
-    MK_CUDA(sort_pairs_u64_u32(nullptr, tb, nullptr, nullptr, nullptr, nullptr, cap, 64, s));
-    size_t tb2 = 0;
-    MK_CUDA(exclusive_sum_u32_u64(nullptr, tb2, nullptr, nullptr, cap, s));
-    tb = std::max(tb, tb2);
-    MK_TRY(device_alloc(g, (void **)&g->d_kin, cap * 8));
-    MK_TRY(device_alloc(g, (void **)&g->d_kout, cap * 8));
-    MK_TRY(device_alloc(g, (void **)&g->d_iin, cap * 4));
-    MK_TRY(device_alloc(g, (void **)&g->d_iout, cap * 4));
-    MK_TRY(device_alloc(g, &g->d_tmp, tb));
-    g->tmp_bytes = tb;
+    device_free(g, g->d_tkey, g->table_size * 8);
+    device_free(g, g->d_tval, g->table_size * 4);
+    device_free(g, g->d_slot, g->scratch_cap * 4);
+    device_free(g, g->d_cand, g->scratch_cap * 4);
+    g->d_tkey = nullptr;
+    g->d_tval = g->d_slot = g->d_cand = nullptr;
+    g->scratch_cap = g->table_size = 0;
+    MK_TRY(device_alloc(g, (void **)&g->d_tkey, table * 8));
+    MK_TRY(device_alloc(g, (void **)&g->d_tval, table * 4));
+    MK_TRY(device_alloc(g, (void **)&g->d_slot, cap * 4));
+    MK_TRY(device_alloc(g, (void **)&g->d_cand, cap * 4));
+    g->table_size = table;
     g->scratch_cap = cap;
     return MK_OK;
 }
@@ -404,10 +398,9 @@ mk_status mk_graph_create_ex(const mk_config *cfg, void *stream, mk_graph **out)
                                                        cfg->d_bucket_per_vertex, d_bad);
     // exclusive scan of bucket counts -> head offsets (one allocation for
     // every head slab; paper, Sec. "Memory Management in Meerkat")
-    size_t tb = 0;
     void *d_tmp = nullptr;
-    if (exclusive_sum_u32_u64(nullptr, tb, d_b, d_off, V, s) != cudaSuccess ||
-        cudaMalloc(&d_tmp, tb) != cudaSuccess || exclusive_sum_u32_u64(d_tmp, tb, d_b, d_off, V, s) != cudaSuccess) {
+    if (cudaMalloc(&d_tmp, exclusive_scan_scratch_bytes(V)) != cudaSuccess ||
+        exclusive_scan_u32_u64(d_b, d_off, V, d_tmp, s, nullptr) != cudaSuccess) {
         cudaFree(d_tmp);
         cleanup_tmp();
         return fail(MK_ERR_CUDA);
@@ -507,11 +500,10 @@ mk_status mk_graph_destroy(mk_graph *g)
     cudaFree(v.ulog);
     cudaFree(v.owner);
     cudaFree(g->d_state);
-    cudaFree(g->d_kin);
-    cudaFree(g->d_kout);
-    cudaFree(g->d_iin);
-    cudaFree(g->d_iout);
-    cudaFree(g->d_tmp);
+    cudaFree(g->d_tkey);
+    cudaFree(g->d_tval);
+    cudaFree(g->d_slot);
+    cudaFree(g->d_cand);
     cudaFree(g->d_dlog);
     if (g->h_pinned)
         cudaFreeHost(g->h_pinned);
@@ -565,11 +557,10 @@ mk_status mk_graph_export(mk_graph *g, uint64_t cap, uint32_t *d_src, uint32_t *
     MK_CUDA(cudaMallocAsync((void **)&d_off, (H + 1) * 8, s));
     MK_CUDA(cudaMemsetAsync(d_cnt + H, 0, 4, s));
     k_count_live<<<grid_for(H * 32, 256), 256, 0, s>>>(g->v, d_cnt, max_hops);
-    size_t tb = 0;
-    MK_CUDA(exclusive_sum_u32_u64(nullptr, tb, d_cnt, d_off, H + 1, s));
     void *d_tmp = nullptr;
-    MK_CUDA(cudaMallocAsync(&d_tmp, tb, s));
-    MK_CUDA(exclusive_sum_u32_u64(d_tmp, tb, d_cnt, d_off, H + 1, s));
+    int scan_launches = 0;
+    MK_CUDA(cudaMallocAsync(&d_tmp, exclusive_scan_scratch_bytes(H + 1), s));
+    MK_CUDA(exclusive_scan_u32_u64(d_cnt, d_off, H + 1, d_tmp, s, &scan_launches));
     uint64_t m = 0;
     MK_CUDA(cudaMemcpyAsync(&m, d_off + H, 8, cudaMemcpyDeviceToHost, s));
     MK_CUDA(cudaStreamSynchronize(s));
@@ -588,7 +579,7 @@ mk_status mk_graph_export(mk_graph *g, uint64_t cap, uint32_t *d_src, uint32_t *
     if (m)
         MK_CUDA(sort_pairs_u64_u32(d_tmp2, tb2, k0, k1, w0, w1, m, 2 * g->vbits, s));
     k_decode_export<<<grid_for(mm, 256), 256, 0, s>>>(k1, w1, m, cap, g->vbits, d_src, d_dst, d_w, d_count);
-    g->launches += 4 + exclusive_sum_launches(H + 1) + sort_pairs_launches(m, 2 * g->vbits);
+    g->launches += 4 + scan_launches + sort_pairs_launches(m, 2 * g->vbits);
     cudaFreeAsync(d_cnt, s);
     cudaFreeAsync(d_off, s);
     cudaFreeAsync(d_tmp, s);

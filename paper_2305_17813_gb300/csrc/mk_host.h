@@ -37,16 +37,18 @@ struct TimedLaunch {
     cudaEvent_t a, b;
 };
 
-// Sorting / scanning helpers (sort.cu, CUB radix sort compiled in-tree).
+// Exclusive prefix sum of n counts into 64-bit offsets (sort.cu; the
+// library's own kernels); `scratch` holds exclusive_scan_scratch_bytes(n).
+// *launches (nullable) is increased by the kernels launched.
+uint64_t exclusive_scan_scratch_bytes(uint64_t n);
+cudaError_t exclusive_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, cudaStream_t s,
+                                   int *launches);
+// Radix sort of (key, value) pairs for the canonical order of an export
+// (CUB, compiled in-tree), and the kernel launches it makes.
 cudaError_t sort_pairs_u64_u32(void *tmp, size_t &tmp_bytes, const uint64_t *kin, uint64_t *kout,
                                const uint32_t *vin, uint32_t *vout, uint64_t n, int end_bit,
                                cudaStream_t s);
-cudaError_t exclusive_sum_u32_u64(void *tmp, size_t &tmp_bytes, const uint32_t *in, uint64_t *out,
-                                  uint64_t n, cudaStream_t s);
-// Kernel launches made by one call of the helpers above (CUB's plan for
-// these sizes), for the launch counter.
 int sort_pairs_launches(uint64_t n, int end_bit);
-int exclusive_sum_launches(uint64_t n);
 
 } // namespace mk
 
@@ -65,12 +67,13 @@ struct mk_graph {
     uint32_t vbits = 1;          // bits of a vertex id in a sort key
     mk::DevState *d_state = nullptr;
     uint64_t bytes = 0;          // device bytes held
-    // staging scratch, grown on demand
+    // staging scratch, grown on demand: the batch's hash set of (src, dst)
+    // pairs (table_size entries, a power of two >= 2 * scratch_cap), each
+    // edge's entry, and the updated-list nominations of an insert
     uint64_t scratch_cap = 0;
-    uint64_t *d_kin = nullptr, *d_kout = nullptr;
-    uint32_t *d_iin = nullptr, *d_iout = nullptr;
-    void *d_tmp = nullptr;
-    size_t tmp_bytes = 0;
+    uint64_t table_size = 0;
+    unsigned long long *d_tkey = nullptr;
+    uint32_t *d_tval = nullptr, *d_slot = nullptr, *d_cand = nullptr;
     // change log of the current epoch: deleted (src << 32 | dst)
     unsigned long long *d_dlog = nullptr;
     uint64_t dlog_cap = 0, dlog_bound = 0;

@@ -1,8 +1,9 @@
 // mk_insert_batch_noalloc: the batched insert of update.cu with its staging
-// scratch (sort keys, positions and the radix-sort workspace) taken from one
-// fixed device array declared in this file instead of buffers grown with
-// cudaMalloc.  The graph itself must already exist; this call allocates
-// nothing, on the device or on the host.
+// scratch (the batch's hash set of (src, dst) pairs, each edge's entry and
+// the updated-list nominations) taken from one fixed device array declared
+// in this file instead of buffers grown with cudaMalloc.  The graph itself
+// must already exist; this call allocates nothing, on the device or on the
+// host.
 //
 // Why: mk_insert_batch grows its staging buffers on demand, and growing them
 // calls cudaStreamSynchronize, cudaFree and cudaMalloc, which stall the
@@ -20,22 +21,24 @@
 using namespace mk;
 
 // Kernels of update.cu, launched here unchanged.
-__global__ void k_build_keys(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
-                             const uint32_t *__restrict__ w, uint64_t n, uint32_t V, uint32_t vbits,
-                             uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, DevState *st);
-__global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint64_t *__restrict__ skey,
-                                                const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ w_in,
-                                                uint64_t n, uint32_t vbits, uint8_t *__restrict__ flags,
-                                                uint32_t max_hops, uint32_t *__restrict__ cand);
+__global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
+                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, unsigned long long *tkey,
+                        uint32_t *tval, uint32_t mask, uint32_t *__restrict__ slot, DevState *st);
+__global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint32_t *__restrict__ src,
+                                                   const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w_in,
+                                                   uint64_t n, const uint32_t *__restrict__ tval,
+                                                   const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
+                                                   uint32_t max_hops, uint32_t *__restrict__ cand);
 __global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n);
 
 namespace {
 
 constexpr uint64_t kNoAllocMaxBatch = 1ull << 16;
-constexpr size_t kKeyBytes = kNoAllocMaxBatch * 8;
-constexpr size_t kIdxBytes = kNoAllocMaxBatch * 4;
-constexpr size_t kSortWorkspace = 2u << 20;
-constexpr size_t kScratchBytes = 2 * kKeyBytes + 2 * kIdxBytes + kSortWorkspace; // 3.5 MiB
+constexpr uint64_t kTable = 2 * kNoAllocMaxBatch;            // hash-set entries (a power of two)
+constexpr size_t kTkeyBytes = kTable * 8;
+constexpr size_t kTvalBytes = kTable * 4;
+constexpr size_t kEdgeBytes = kNoAllocMaxBatch * 4;
+constexpr size_t kScratchBytes = kTkeyBytes + kTvalBytes + 2 * kEdgeBytes; // 2 MiB
 
 } // namespace
 
@@ -54,9 +57,7 @@ unsigned char *g_scratch_addr[kMaxDevices] = {};
 bool g_setup_done[kMaxDevices] = {};
 
 // Per-device set-up, done by the first call on each device (with that device
-// current): the array's device address and a check that the radix sort's
-// workspace for the largest batch fits the reserved part.  Neither step
-// allocates.
+// current): the array's device address.  It allocates nothing.
 mk_status setup_device(unsigned char **base)
 {
     int dev = 0;
@@ -71,10 +72,6 @@ mk_status setup_device(unsigned char **base)
             cudaGetLastError();
             return MK_ERR_CUDA;
         }
-        size_t need = 0;
-        e = sort_pairs_u64_u32(nullptr, need, nullptr, nullptr, nullptr, nullptr, kNoAllocMaxBatch, 64, nullptr);
-        if (e != cudaSuccess || need > kSortWorkspace)
-            return MK_ERR_INTERNAL;
         g_scratch_addr[dev] = (unsigned char *)p;
         g_setup_done[dev] = true;
     }
@@ -97,31 +94,26 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
     g->change_seq++;
     if (n == 0)
         return MK_OK;
-    uint64_t *kin = (uint64_t *)base;
-    uint64_t *kout = (uint64_t *)(base + kKeyBytes);
-    uint32_t *iin = (uint32_t *)(base + 2 * kKeyBytes);
-    uint32_t *iout = (uint32_t *)(base + 2 * kKeyBytes + kIdxBytes);
-    void *work = base + 2 * kKeyBytes + 2 * kIdxBytes;
-    // nothing in the scratch has to start at zero: keys and positions are
-    // written in full before they are read, and the sort initialises its own
-    // workspace; only the caller's flags are cleared
+    unsigned long long *tkey = (unsigned long long *)base;
+    uint32_t *tval = (uint32_t *)(base + kTkeyBytes);
+    uint32_t *slot = (uint32_t *)(base + kTkeyBytes + kTvalBytes);
+    uint32_t *cand = (uint32_t *)(base + kTkeyBytes + kTvalBytes + kEdgeBytes);
+    // the hash set must start empty (all-ones keys and positions); slots and
+    // nominations are written in full before they are read; the caller's
+    // flags are cleared
+    MK_CUDA(cudaMemsetAsync(tkey, 0xFF, kTkeyBytes + kTvalBytes, s));
     if (d_inserted)
         MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
-    const int bits = 2 * (int)g->vbits;
-    MK_TRY(timed(g, "stage_keys", s, 1, [&]() {
-        k_build_keys<<<grid_for(n, 256), 256, 0, s>>>(d_src, d_dst, d_w, n, g->v.V, g->vbits, kin, iin, g->d_state);
+    MK_TRY(timed(g, "stage_dedup", s, 1, [&]() {
+        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(d_src, d_dst, d_w, n, g->v.V, tkey, tval, (uint32_t)(kTable - 1),
+                                                 slot, g->d_state);
         return cudaSuccess;
-    }));
-    MK_TRY(timed(g, "stage_sort", s, sort_pairs_launches(n, bits), [&]() {
-        size_t tb = kSortWorkspace;
-        return sort_pairs_u64_u32(work, tb, kin, kout, iin, iout, n, bits, s);
     }));
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 2, [&]() {
-        // the sort's input positions (iin) are free now: they hold the log nominations
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, kout, iout, d_w, n, g->vbits, d_inserted, max_hops, iin);
-        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, iin, n);
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, tval, slot, d_inserted, max_hops, cand);
+        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, cand, n);
         return cudaSuccess;
     });
 }

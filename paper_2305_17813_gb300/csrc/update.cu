@@ -1,63 +1,139 @@
 // Batched edge insert and delete.
 //
-// Staging: each batch is keyed by (src << b | dst) and radix sorted, so the
-// edges of one source are contiguous and repeated (src, dst) pairs are
-// adjacent with the first occurrence first (the sort is stable).  One warp
-// then owns 32 consecutive sorted edges; it groups its lanes by slab list
-// (src and bucket), walks each list's chain once with coalesced 128-byte
-// slab loads and matches all of the group's destinations against every
-// slab (paper, Sec. "Experimental Evaluation", insertion and deletion; the
-// warp-cooperative work strategy of Sec. "Motivation").  A list whose edges
-// straddle two warps is appended to by both; free pairs are claimed with
-// 64-bit atomicCAS and new slabs are linked with a CAS on the next lane.
+// Staging: in-batch duplicates are found with a hash set of the batch's
+// (src, dst) pairs that keeps, per pair, the smallest batch position
+// (k_dedup); only that first occurrence is applied.  The insert and delete
+// kernels then take the batch in tiles of 256 edges: each tile is sorted by
+// slab list (source and bucket) in shared memory, so the edges of one list
+// sit side by side, and one warp owns 32 consecutive sorted edges: it groups
+// its lanes by list, walks each list's chain once with coalesced 128-byte
+// slab loads and matches all of the group's destinations against every slab
+// (paper, Sec. "Experimental Evaluation", insertion and deletion; the
+// warp-cooperative work strategy of Sec. "Motivation").  A list with edges
+// in several warps is appended to by all of them; free pairs are claimed
+// with 64-bit atomicCAS and new slabs are linked with a CAS on the next lane.
 #include "mk_host.h"
 
 #include <algorithm>
 
 using namespace mk;
 
-// Validates the batch and writes sort keys and original positions.
-__global__ void k_build_keys(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
-                             const uint32_t *__restrict__ w, uint64_t n, uint32_t V, uint32_t vbits,
-                             uint64_t *__restrict__ keys, uint32_t *__restrict__ idx, DevState *st)
+constexpr unsigned long long kNoPair = ~0ull; // empty hash-set entry
+
+// 64-bit finaliser of splitmix64 (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014), as the hash of a (src, dst) pair.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x)
+{
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x;
+}
+
+// Validates edge i and enters its (src, dst) pair in the batch's hash set
+// (open addressing with linear probing, at most half full): the entry keeps
+// the smallest batch position of the pair, and slot[i] names the entry.
+// Invalid edges get slot kNil and set the invalid-argument status.
+__global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
+                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, unsigned long long *tkey,
+                        uint32_t *tval, uint32_t mask, uint32_t *__restrict__ slot, DevState *st)
 {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     bool bad = false;
     if (i < n) {
         const uint32_t s = src[i], d = dst[i];
         bad = s >= V || d >= V || (w && w[i] == 0);
-        keys[i] = ((uint64_t)s << vbits) | d;
-        idx[i] = (uint32_t)i;
+        uint32_t at = kNil;
+        if (!bad) {
+            const unsigned long long key = ((unsigned long long)s << 32) | d;
+            uint32_t h = (uint32_t)mix64(key) & mask;
+            for (uint32_t probe = 0; probe <= mask; ++probe) {
+                unsigned long long k = __ldcg(&tkey[h]);
+                if (k == kNoPair) {
+                    k = atomicCAS(&tkey[h], kNoPair, key);
+                    if (k == kNoPair)
+                        k = key;
+                }
+                if (k == key) {
+                    atomicMin(&tval[h], (uint32_t)i);
+                    at = h;
+                    break;
+                }
+                h = (h + 1) & mask;
+            }
+        }
+        slot[i] = at;
     }
     if (__ballot_sync(kFull, bad) && lane_id() == 0)
         set_status(st, kErrInvalid);
 }
 
-// Sorted-batch prologue shared by insert and delete: decodes this lane's
-// edge, flags the first occurrence of each (src, dst) and finds its list.
+// One lane's edge after staging: its batch position, whether it is the
+// first occurrence of its pair (only those are applied), and its list.
 struct LaneEdge {
-    bool inb, first;
+    bool first;
     uint32_t idx, src, dst, list;
 };
 
-__device__ __forceinline__ LaneEdge load_sorted(const GView &g, const uint64_t *skey, const uint32_t *sidx,
-                                                uint64_t n, uint32_t vbits, uint64_t pos)
+// Sorts the 256 keys held one per thread of the block, ascending (bitonic
+// network; thread t ends with the t-th smallest).  Compare-exchanges whose
+// partner is in the same warp use shuffles; the six steps with partners 32
+// or more threads away go through `xchg` (256 words of shared memory) with
+// a block barrier around them.
+__device__ __forceinline__ unsigned long long bitonic_sort_256(unsigned long long x, unsigned long long *xchg)
 {
-    LaneEdge e;
-    e.inb = pos < n;
-    const uint64_t key = e.inb ? skey[pos] : ~0ull;
-    uint64_t prev = __shfl_up_sync(kFull, key, 1);
-    if (lane_id() == 0)
-        prev = (e.inb && pos > 0) ? skey[pos - 1] : ~0ull;
-    e.first = e.inb && (pos == 0 || prev != key);
-    e.idx = e.inb ? sidx[pos] : 0;
-    e.src = (uint32_t)(key >> vbits);
-    e.dst = (uint32_t)(key & ((1ull << vbits) - 1));
-    e.list = 0;
-    if (e.first) {
-        const uint2 vi = g.vinfo[e.src];
-        e.list = vi.x + bucket_of(e.dst, vi.y);
+    const uint32_t t = threadIdx.x;
+    for (uint32_t k = 2; k <= 256; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            unsigned long long y;
+            if (j >= 32) {
+                xchg[t] = x;
+                __syncthreads();
+                y = xchg[t ^ j];
+                __syncthreads();
+            } else {
+                y = __shfl_xor_sync(kFull, x, j);
+            }
+            const bool lower = (t & j) == 0, up = (t & k) == 0;
+            x = (lower == up) ? min(x, y) : max(x, y);
+        }
     }
+    return x;
+}
+
+// Staging of the block's tile of 256 edges (called by the whole block, 256
+// threads): each thread tests its edge for first occurrence, finds its list
+// and forms key <list, position in tile> (or all-ones for an edge that is
+// not applied); the tile is sorted by that key (`keys`: 256 words of shared
+// memory for the sort) and thread t returns the t-th edge of the sorted
+// tile.  Edges that are not applied get flag 0 here.
+__device__ __forceinline__ LaneEdge stage_tile(const GView &g, const uint32_t *__restrict__ src,
+                                               const uint32_t *__restrict__ dst, uint64_t n,
+                                               const uint32_t *__restrict__ tval, const uint32_t *__restrict__ slot,
+                                               uint8_t *__restrict__ flags, unsigned long long *keys)
+{
+    const uint64_t tile0 = blockIdx.x * 256ull;
+    const uint64_t i = tile0 + threadIdx.x;
+    unsigned long long key = ~0ull;
+    if (i < n) {
+        const uint32_t sl = slot[i];
+        if (sl != kNil && __ldcg(&tval[sl]) == (uint32_t)i) {
+            const uint32_t s = src[i], d = dst[i];
+            const uint2 vi = g.vinfo[s];
+            key = ((unsigned long long)(vi.x + bucket_of(d, vi.y)) << 32) | threadIdx.x;
+        } else if (flags) {
+            flags[i] = 0;
+        }
+    }
+    const unsigned long long k = bitonic_sort_256(key, keys);
+    LaneEdge e;
+    e.first = k != ~0ull;
+    e.list = (uint32_t)(k >> 32);
+    e.idx = (uint32_t)(tile0 + (uint32_t)(k & 0xFFu));
+    e.src = e.first ? src[e.idx] : 0;
+    e.dst = e.first ? dst[e.idx] : 0;
     return e;
 }
 
@@ -89,22 +165,23 @@ __device__ __forceinline__ bool match_slab(uint32_t v, uint32_t members, bool mi
     return found;
 }
 
-// One warp per 32 sorted edges; see the file comment.
-__global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint64_t *__restrict__ skey,
-                                                const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ w_in,
-                                                uint64_t n, uint32_t vbits, uint8_t *__restrict__ flags,
-                                                uint32_t max_hops, uint32_t *__restrict__ cand)
+// One block per tile of 256 edges, one warp per 32 sorted edges; see the
+// file comment.
+__global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint32_t *__restrict__ src,
+                                                   const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w_in,
+                                                   uint64_t n, const uint32_t *__restrict__ tval,
+                                                   const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
+                                                   uint32_t max_hops, uint32_t *__restrict__ cand)
 {
+    __shared__ unsigned long long keys[256];
     const uint32_t lane = lane_id();
-    const unsigned long long warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t pos = warp * 32 + lane;
-    if (warp * 32 >= n)
-        return;
-    if (pos < n)
-        cand[pos] = kNil;
+    const uint64_t i = blockIdx.x * 256ull + threadIdx.x;
+    const unsigned long long warp = i >> 5; // salt of this warp's pool probes
+    if (i < n)
+        cand[i] = kNil;
+    const LaneEdge e = stage_tile(g, src, dst, n, tval, slot, flags, keys);
     if (status_hint(g.st) != 0)
         return;
-    const LaneEdge e = load_sorted(g, skey, sidx, n, vbits, pos);
     const uint32_t w = (e.first && w_in) ? w_in[e.idx] : 1u;
     uint8_t done = 0;
     unsigned long long loads = 0, linked = 0;
@@ -141,7 +218,7 @@ __global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint64_t *__re
         // the first insert into L in this epoch nominates L for the
         // updated-list log (k_log_updated compacts the nominations)
         if (lane == leader && flag_updated(g, L))
-            cand[pos] = L;
+            cand[e.idx] = L;
         // append at the tail
         uint32_t tail = slab;
         for (uint64_t guard = 0;; ++guard) {
@@ -233,7 +310,7 @@ __global__ void __launch_bounds__(256, 8) k_insert(GView g, const uint64_t *__re
             }
         }
     }
-    if (e.inb && flags)
+    if (e.first && flags)
         flags[e.idx] = done;
     count_add(g.st, kCtrInsertSlabs, loads);
     count_add(g.st, kCtrInsertNewSlabs, linked);
@@ -249,27 +326,27 @@ __global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__
     block_enqueue(g.ulog, &g.st->ulog_count, g.H, L, L != kNil, s2); // a list is logged once per epoch: fits
 }
 
-// One warp per 32 sorted edges: find each destination in its list's chain,
+// One block per tile of 256 edges, one warp per 32 sorted edges: find each
+// destination in its list's chain,
 // overwrite the pair with TOMBSTONE, stop as soon as every destination of
 // the group is found or the chain ends; removed edges go to the change log
 // with a block-aggregated enqueue.
-__global__ void __launch_bounds__(256, 8) k_delete(GView g, const uint64_t *__restrict__ skey,
-                                                const uint32_t *__restrict__ sidx, uint64_t n, uint32_t vbits,
-                                                uint8_t *__restrict__ flags, unsigned long long *dlog,
-                                                uint32_t dlog_cap, uint32_t max_hops)
+__global__ void __launch_bounds__(256, 8) k_delete(GView g, const uint32_t *__restrict__ src,
+                                                   const uint32_t *__restrict__ dst, uint64_t n,
+                                                   const uint32_t *__restrict__ tval, const uint32_t *__restrict__ slot,
+                                                   uint8_t *__restrict__ flags, unsigned long long *dlog,
+                                                   uint32_t dlog_cap, uint32_t max_hops)
 {
+    __shared__ unsigned long long keys[256];
     __shared__ uint32_t s2[2];
     const uint32_t lane = lane_id();
-    const unsigned long long warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t pos = warp * 32 + lane;
+    LaneEdge e = stage_tile(g, src, dst, n, tval, slot, flags, keys);
     // no early exit: the whole block meets in block_enqueue
-    const bool run = warp * 32 < n && status_hint(g.st) == 0;
-    LaneEdge e{};
-    if (run)
-        e = load_sorted(g, skey, sidx, n, vbits, pos);
+    if (status_hint(g.st) != 0)
+        e.first = false;
     bool removed = false;
     unsigned long long loads = 0;
-    uint32_t todo = run ? __ballot_sync(kFull, e.first) : 0u;
+    uint32_t todo = __ballot_sync(kFull, e.first);
     while (todo) {
         const uint32_t leader = __ffs(todo) - 1;
         const uint32_t L = __shfl_sync(kFull, e.list, leader);
@@ -298,7 +375,7 @@ __global__ void __launch_bounds__(256, 8) k_delete(GView g, const uint64_t *__re
     const unsigned long long rec = ((unsigned long long)e.src << 32) | e.dst;
     if (!block_enqueue(dlog, &g.st->dlog_count, dlog_cap, rec, removed, s2))
         set_status(g.st, kErrTimeout);
-    if (run && e.inb && flags)
+    if (e.first && flags)
         flags[e.idx] = removed ? 1 : 0;
     count_add(g.st, kCtrDeleteSlabs, loads);
 }
@@ -311,15 +388,13 @@ mk_status stage(mk_graph *g, const uint32_t *src, const uint32_t *dst, const uin
                 cudaStream_t s)
 {
     MK_TRY(ensure_scratch(g, n, s));
-    const int bits = 2 * (int)g->vbits;
-    MK_TRY(timed(g, "stage_keys", s, 1, [&]() {
-        k_build_keys<<<grid_for(n, 256), 256, 0, s>>>(src, dst, w, n, g->v.V, g->vbits, g->d_kin, g->d_iin,
-                                                      g->d_state);
+    // the hash set must start empty: all-ones keys and positions
+    MK_CUDA(cudaMemsetAsync(g->d_tkey, 0xFF, g->table_size * 8, s));
+    MK_CUDA(cudaMemsetAsync(g->d_tval, 0xFF, g->table_size * 4, s));
+    return timed(g, "stage_dedup", s, 1, [&]() {
+        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(src, dst, w, n, g->v.V, g->d_tkey, g->d_tval,
+                                                 (uint32_t)(g->table_size - 1), g->d_slot, g->d_state);
         return cudaSuccess;
-    }));
-    return timed(g, "stage_sort", s, sort_pairs_launches(n, bits), [&]() {
-        size_t tb = g->tmp_bytes;
-        return sort_pairs_u64_u32(g->d_tmp, tb, g->d_kin, g->d_kout, g->d_iin, g->d_iout, n, bits, s);
     });
 }
 
@@ -342,10 +417,9 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 2, [&]() {
-        // the sort's input positions (d_iin) are free now: they hold the log nominations
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_kout, g->d_iout, d_w, n, g->vbits, d_inserted, max_hops,
-                                                  g->d_iin);
-        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_iin, n);
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, g->d_tval, g->d_slot, d_inserted,
+                                                  max_hops, g->d_cand);
+        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_cand, n);
         return cudaSuccess;
     });
 }
@@ -381,7 +455,7 @@ mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     MK_TRY(stage(g, d_src, d_dst, nullptr, n, s));
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "delete", s, 1, [&]() {
-        k_delete<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_kout, g->d_iout, n, g->vbits, d_deleted, g->d_dlog,
+        k_delete<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, n, g->d_tval, g->d_slot, d_deleted, g->d_dlog,
                                                   (uint32_t)g->dlog_cap, max_hops);
         return cudaSuccess;
     });
