@@ -209,6 +209,47 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
     return None
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# kernel families, from the ncu launch list of this benchmark summarised in
+# profiles/launches_powerlaw_rmat20_b1M.md (full workload, one pass), and
+# the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
+# reported only while those sources are unchanged; otherwise traffic is null.
+NCU_TRAFFIC_SOURCES_SHA = "cf201142342282d888035e9eea43e7e0eb6ca6956fba60d11a59a38957bd4ba3"
+NCU_TRAFFIC = {
+    "sssp_rounds": 46489120,
+    "sssp_relax_into_invalid": 356063872,
+    "sssp_enqueue_invalid": 11216256,
+    "sssp_relax_updated": 145658240,
+    "sssp_invalidate_jump": 10471904,
+    "wcc_hook_all": 351031040,
+    "wcc_hook_updated": 136834432,
+    "insert": 118793024,
+    "delete": 186433152,
+    "query": 131153664,
+    "stage_dedup": 125355456,
+    "update_slab_pointers": 60652992,
+}
+
+
+def kernel_sources_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_17813_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(family):
+    """DRAM bytes per launch of `family` from the committed ncu capture, or
+    None when there is none or the kernel sources changed since."""
+    if family not in NCU_TRAFFIC or NCU_TRAFFIC_SOURCES_SHA is None:
+        return None
+    return NCU_TRAFFIC[family] if kernel_sources_sha() == NCU_TRAFFIC_SOURCES_SHA else None
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -359,7 +400,7 @@ def run_ours(args, world, rank, local):
         avg_ms = fam_time[dom] / fam_launch[dom]
         achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": ncu_traffic(dom),
                 "algorithmic_bytes_per_launch": int(per_launch_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "launches": fam_launch[dom]}
     # every family's share and achieved bandwidth, for the record

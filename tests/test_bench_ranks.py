@@ -68,3 +68,14 @@ def test_algorithmic_bytes_model():
     assert bench.algorithmic_bytes("sssp_rounds", ctr, 1, 1) == 3 * 16 + 128 * 4 + 16 * 50 + 7 * 20
     assert bench.algorithmic_bytes("wcc_hook_all", ctr, 1, 1) == 128 * 9 + 16 * 100
     assert bench.algorithmic_bytes("unknown", ctr, 1, 1) is None
+
+
+def test_traffic_reported_only_for_unchanged_kernel_sources(monkeypatch):
+    import bench
+
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", {"sssp_rounds": 123})
+    monkeypatch.setattr(bench, "NCU_TRAFFIC_SOURCES_SHA", bench.kernel_sources_sha())
+    assert bench.ncu_traffic("sssp_rounds") == 123
+    assert bench.ncu_traffic("query") is None
+    monkeypatch.setattr(bench, "NCU_TRAFFIC_SOURCES_SHA", "0" * 64)
+    assert bench.ncu_traffic("sssp_rounds") is None
