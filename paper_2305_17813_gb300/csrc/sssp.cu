@@ -52,7 +52,10 @@ enum {
 // A frontier of at most kSoloLists lists is processed by block 0 alone, with
 // block-level barriers between rounds, for at most kSoloRounds rounds in a
 // row (so the other blocks' bounded wait at the grid barrier never expires).
-constexpr uint32_t kSoloLists = 1024;
+// Block 0 has 64 four-lane groups: a frontier of up to two lists per group
+// costs block 0 at most two load chains a round, less than a grid barrier
+// plus one chain; a larger one is faster on the whole grid.
+constexpr uint32_t kSoloLists = 128;
 constexpr uint32_t kSoloRounds = 4096;
 
 __device__ __forceinline__ uint32_t node_dist(unsigned long long d) { return (uint32_t)(d >> 32); }
@@ -577,27 +580,28 @@ __global__ void __launch_bounds__(256) k_enqueue_invalid(RoundArgs a)
 // Incremental seeds: relax the entries inserted since the last commit.
 // Every list in the updated-list log is walked from its UpdateIterator start
 // (the marker slab, skipping its lanes before the marker lane, or all of it
-// when it is full).  Every 8-lane group of every warp takes one list at a
-// time (group index + k * groups in the grid); the next list's log entry,
-// source and marker are loaded a step ahead.
+// when it is full).  Every 4-lane group of every warp takes one list at a
+// time (group index + k * groups in the grid; eight lists per warp in
+// flight); the next list's log entry, source and marker are loaded a step
+// ahead.
 __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
 {
     const GView &g = a.g;
-    const uint32_t sub = lane_id() & 7u, gi = lane_id() >> 3;
+    const uint32_t s4 = lane_id() & 3u, g4 = lane_id() >> 2;
     const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 8; // 4-lane groups in the grid
     __shared__ BlockFrontier bq;
     bq_init(bq);
     const uint32_t round = __ldg(a.ctr + kRid) + 1;
     int *overflow = (int *)(a.ctr + kOverflow);
     unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
-    uint64_t i = warp0 * 4 + gi;
+    uint64_t i = warp0 * 8 + g4;
     uint32_t L = i < n ? g.ulog[i] : kNil;
     uint32_t nL = i + gs < n ? g.ulog[i + gs] : kNil;
     uint32_t src = L != kNil ? g.list_src[L] : 0;
     unsigned long long mk = L != kNil ? g.lmark[L] : 0;
-    for (uint64_t base = warp0 * 4; base < n; base += gs, i += gs) {
+    for (uint64_t base = warp0 * 8; base < n; base += gs, i += gs) {
         const uint32_t nnL = i + 2 * gs < n ? g.ulog[i + 2 * gs] : kNil;
         const uint32_t nsrc = nL != kNil ? g.list_src[nL] : 0;
         const unsigned long long nmk = nL != kNil ? g.lmark[nL] : 0;
@@ -606,10 +610,11 @@ __global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
         const uint32_t first_lane = mlane == kInvalidLane ? 32u : mlane;
         const bool go = L != kNil && dx != kInf32;
         const uint32_t start = go ? (uint32_t)(mk >> 32) : kNil;
-        const uint4 x0 = group_load(g, start);
-        lists += __popc(__ballot_sync(kFull, go && sub == 0));
+        uint4 lo, hi;
+        group4_load(g, start, lo, hi);
+        lists += __popc(__ballot_sync(kFull, go && s4 == 0));
         const uint32_t x = src;
-        slabs += walk_lists_g8_from(g, start, true, x0, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
+        slabs += walk_lists_g4_from(g, start, true, lo, hi, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
             relax_edge(a, x, dx, y, w, live, round, bq, a.front[0], a.ctr + kCnt0, overflow, edges, improved);
         });
         L = nL;
@@ -811,8 +816,8 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
         // incremental prologue: edges inserted since the last commit
         if (g->ulog_bound) {
             MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
-                // one 8-lane group per logged list
-                const uint64_t threads = g->ulog_bound * 8;
+                // one 4-lane group per logged list
+                const uint64_t threads = g->ulog_bound * 4;
                 k_relax_updated<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 10), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
