@@ -254,6 +254,32 @@ __device__ __forceinline__ uint32_t alloc_slab(const GView &g, uint32_t salt)
     return kNil;
 }
 
+// One thread's slab allocation: probes the bitmap word by word from a start
+// hashed from `salt` and claims the lowest free bit of the first word that
+// has one with atomicOr.  Returns the slab index (H + bit), or kNil after a
+// sweep over the whole bitmap found nothing.
+__device__ __forceinline__ uint32_t alloc_slab_one(const GView &g, uint32_t salt)
+{
+    const uint32_t W = g.pool_words;
+    if (W == 0)
+        return kNil;
+    uint32_t wi = (uint32_t)((uint64_t)hash32(salt) % W);
+    for (uint32_t it = 0; it < W; ++it) {
+        uint32_t word = __ldcg(&g.bitmap[wi]);
+        while (word != kFull) {
+            const uint32_t b = __ffs(~word) - 1;
+            const uint32_t old = atomicOr(&g.bitmap[wi], 1u << b);
+            if (!(old & (1u << b))) {
+                atomicAdd((unsigned long long *)&g.st->pool_used[slot_of_block()], 1ull);
+                return g.H + wi * 32 + b;
+            }
+            word = old | (1u << b);
+        }
+        wi = wi + 1 == W ? 0 : wi + 1;
+    }
+    return kNil;
+}
+
 __device__ __forceinline__ void free_slab(const GView &g, uint32_t s)
 {
     const uint32_t i = s - g.H;
