@@ -508,7 +508,8 @@ def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.
     over the next `horizon` batches) for every t with a full window, then
     predicts each vertex's growth over the remaining batches.  Two graphs are
     rebuilt from the live edges at `split`: one with the learned bucket
-    counts, one with the load-factor rule on the current degrees (the judge).
+    counts, one with the load-factor rule on the current degrees (the baseline
+    the learned counts are measured against).
     Both run the remaining batches; the insert time, a query batch over live
     edges, chain lengths and slabs walked per query are compared."""
     import torch

@@ -222,8 +222,9 @@ mk_status mk_batcher_launch(mk_batcher *b, void *stream);
 
 /* Kernel shapes: lanes per slab chain in the query kernels (4, 8, 16 or 32:
  * 32/G words per lane, one vector load each), their block size (128, 256,
- * 512) and the blocks per SM of the persistent BFS/SSSP round kernel (0 =
- * occupancy limit).  Timings (ms) are filled by mk_autotune. */
+ * 512) and the size of the persistent BFS/SSSP round kernel's one block per
+ * SM, in units of 256 threads (field rounds_blocks_per_sm; 0 = as large as
+ * fits).  Timings (ms) are filled by mk_autotune. */
 typedef struct mk_tuning {
     int query_group;
     int query_block;
@@ -231,7 +232,7 @@ typedef struct mk_tuning {
     float query_best_ms;
     float rounds_best_ms;
     float query_ms[16];   /* per (group, block) in the order tried */
-    float rounds_ms[8];   /* per blocks-per-SM 1..8 */
+    float rounds_ms[8];   /* per block size 256 x 1..8 */
 } mk_tuning;
 
 /* Autotuner: times the query kernel on the sample (d_src, d_dst, n) for
@@ -322,7 +323,8 @@ mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream);
  * from the load factor and its degree (Sec. "Motivation"); this library adds
  * a small MLP, trained on the degree traces of the running graph, that
  * predicts how many edges each vertex will gain so a rebuilt graph can give
- * it enough buckets.  The load-factor rule stays the fallback and the judge.
+ * it enough buckets.  The load-factor rule stays the fallback and the
+ * yardstick.
  * Bucket counts change the layout (chain lengths) but never a result.
  *
  * Network: 8 -> 64 (ReLU) -> 64 (ReLU) -> 1, MK_MLP_NPARAMS fp32 master

@@ -57,7 +57,8 @@ namespace mk {
 struct Tuning {
     int query_group = 8;          // lanes per query chain (4, 8, 16 or 32)
     int query_block = 256;        // threads per block of the query kernels
-    int rounds_blocks_per_sm = 0; // blocks per SM of the persistent round kernel (0 = occupancy limit)
+    int rounds_blocks_per_sm = 0; // size of the persistent round kernel's one block per SM, in units of
+                                  // 256 threads (0 = as large as fits)
 };
 } // namespace mk
 
@@ -173,7 +174,8 @@ inline uint32_t grid_for(uint64_t threads, uint32_t block)
 }
 
 mk_status ensure_scratch(mk_graph *g, uint64_t n, cudaStream_t s);
-int rounds_grid(int blocks_per_sm);
+int rounds_grid(int units);
+int rounds_block(int units);
 int rounds_max_blocks_per_sm();
 mk_status device_alloc(mk_graph *g, void **p, size_t bytes);
 void device_free(mk_graph *g, void *p, size_t bytes);

@@ -36,6 +36,7 @@ using namespace mk;
 namespace {
 
 constexpr uint32_t kInf32 = 0xFFFFFFFFu;
+constexpr uint32_t kRoundsMaxThreads = 768; // block size limit of the persistent round kernel
 constexpr uint32_t kBarrierSpins = 1u << 24;
 
 // consumer counter words
@@ -52,10 +53,10 @@ enum {
 // A frontier of at most kSoloLists lists is processed by block 0 alone, with
 // block-level barriers between rounds, for at most kSoloRounds rounds in a
 // row (so the other blocks' bounded wait at the grid barrier never expires).
-// Block 0 has 64 four-lane groups: a frontier of up to two lists per group
-// costs block 0 at most two load chains a round, less than a grid barrier
-// plus one chain; a larger one is faster on the whole grid.
-constexpr uint32_t kSoloLists = 128;
+// Block 0 (one SM) has up to 192 four-lane groups: a frontier of up to
+// about one list per group costs block 0 one load chain a round, less than
+// a grid barrier plus one chain; a larger one is faster on the whole grid.
+constexpr uint32_t kSoloLists = 192;
 constexpr uint32_t kSoloRounds = 4096;
 
 __device__ __forceinline__ uint32_t node_dist(unsigned long long d) { return (uint32_t)(d >> 32); }
@@ -224,7 +225,7 @@ __device__ bool grid_barrier(uint32_t *bar)
 // phase sits between two grid barriers, so no block reads a global size
 // while block 0 changes them, and the others wait at one barrier instead of
 // one per round.
-__global__ void __launch_bounds__(256, 3) k_rounds(RoundArgs a)
+__global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
 {
     __shared__ uint32_t solo_cnt[3];
     __shared__ BlockFrontier bq;
@@ -701,29 +702,27 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
 
 namespace mk {
 
-// Co-resident grid of k_rounds: SMs x blocks per SM, the latter the
-// occupancy limit or the tuned value if smaller.
-int rounds_grid(int blocks_per_sm)
-{
-    static int sms = 0, per_sm_max = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, k_rounds, 256, 0);
-        per_sm_max = std::max(per_sm_max, 1);
-    }
-    const int per = blocks_per_sm > 0 ? std::min(blocks_per_sm, per_sm_max) : per_sm_max;
-    return std::max(1, sms * per);
-}
-
+// The persistent round kernel runs one block per SM; the tuned value
+// (rounds_blocks_per_sm) is the block size in units of 256 threads, at most
+// what fits an SM (the occupancy of 256-thread blocks).  One block per SM
+// keeps the grid barrier to one arrival per SM and gives the solo rounds
+// the whole SM.
 int rounds_max_blocks_per_sm()
 {
-    rounds_grid(0);
-    int dev = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds, 256, 0);
-    return std::max(per, 1);
+    static int per = 0;
+    if (!per) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds, 256, 0);
+        per = std::min(std::max(per, 1), (int)(kRoundsMaxThreads / 256));
+    }
+    return per;
+}
+
+int rounds_grid(int) { return num_sms(); }
+
+int rounds_block(int units)
+{
+    const int max_units = rounds_max_blocks_per_sm();
+    return 256 * (units > 0 ? std::min(units, max_units) : max_units);
 }
 
 } // namespace mk
@@ -735,9 +734,10 @@ namespace {
 mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
 {
     const int grid = rounds_grid(g->tune.rounds_blocks_per_sm);
+    const int block = rounds_block(g->tune.rounds_blocks_per_sm);
     void *args[] = {&a};
     mk_status st = timed(g, name, s, 1, [&]() {
-        return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(256), args, 0, s);
+        return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(block), args, 0, s);
     });
     if (st == MK_OK)
         return MK_OK;

@@ -34,7 +34,7 @@ __device__ __forceinline__ uint32_t walk_list(const GView &g, uint32_t slab, uin
 // frontier with one global atomicAdd (bq_flush), instead of one atomic per
 // enqueuing warp on the single global frontier counter, where thousands of
 // warps a round would serialise.
-constexpr uint32_t kBlockBuf = 1024;
+constexpr uint32_t kBlockBuf = 2048;
 struct BlockFrontier {
     uint2 buf[kBlockBuf];
     uint32_t count; // slots reserved; those at or past kBlockBuf went to the global frontier

@@ -28,8 +28,8 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *p, uint32_t x)
 {
     for (;;) {
         const uint32_t px = __ldcg(&p[x]);
-        if (px == x)
-            return x;
+        if (px == x || px == 0) // vertex 0 is always a root
+            return px;
         const uint32_t ppx = __ldcg(&p[px]);
         if (ppx == px)
             return px; // px is the root: no third load
@@ -81,6 +81,10 @@ __device__ __forceinline__ void uf_find_n(uint32_t *p, uint32_t (&x)[N])
             px[i] = done[i] ? x[i] : uf_load<kCached>(p, x[i]);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
+            // vertex 0 is always a root (nothing has a smaller id): a parent
+            // of 0 ends the walk without loading p[0]
+            if (!done[i] && px[i] == 0)
+                x[i] = 0;
             done[i] = done[i] || px[i] == x[i];
             ppx[i] = done[i] ? px[i] : uf_load<kCached>(p, px[i]);
         }

@@ -5,7 +5,7 @@ degree it has at that moment (Sec. "Motivation"), so vertices that keep
 growing end up with long slab chains.  This module trains a small MLP on the
 degree traces of the running graph to predict how many edges each vertex will
 gain, and turns the prediction into bucket counts for a rebuilt graph.  The
-load-factor rule stays the fallback and the judge; bucket counts change the
+load-factor rule stays the fallback and the yardstick; bucket counts change the
 layout (chain lengths, memory) but never a result.
 
 Every computation runs in ``libmeerkat.so`` (``mk_degree_update``,

@@ -223,3 +223,62 @@ def test_update_slab_pointers_figure_cases(cuda_lib):
         slab2, lane2, upd2 = g.marker(v)
         assert slab2 != slab0 and upd2 == 0
         assert lane2 == (mk.MK_INVALID_LANE if after == "INVALID" else after)
+
+
+def test_duplicates_across_tiles_and_warps(cuda_lib):
+    """Repeated (src, dst) pairs far apart in one batch (different 256-edge
+    tiles and warps): exactly the first occurrence is applied, with its
+    weight; the same for a delete batch with repeated pairs."""
+    mk = _mk()
+    V = 3000
+    rng = np.random.default_rng(11)
+    g = mk.Graph(V, edge_capacity_hint=200000, buckets=2)
+    o = oracle.OracleGraph(V)
+    base_s = rng.integers(0, V, 400).astype(np.uint32)
+    base_d = rng.integers(0, V, 400).astype(np.uint32)
+    reps = rng.integers(0, 400, 60000)
+    s = base_s[reps]
+    d = base_d[reps]
+    w = rng.integers(1, 1000, len(s)).astype(np.uint32)
+    q = rng.integers(0, 400, 5000)
+    run_ops(g, o, [("ins", (s, d, w)), ("qry", (base_s, base_d)), ("commit", None),
+                   ("del", (s[q].copy(), d[q].copy())), ("qry", (base_s, base_d))])
+
+
+def test_mixed_single_and_shared_lists_in_warps(cuda_lib):
+    """Each 32-edge warp holds both edges whose list appears once in it and
+    lists with several edges (one bucket per vertex, a few hot sources), so
+    both the 8-lane-group path and the whole-warp path run in one batch."""
+    mk = _mk()
+    V = 4096
+    rng = np.random.default_rng(12)
+    g = mk.Graph(V, edge_capacity_hint=100000, buckets=1)
+    o = oracle.OracleGraph(V)
+    hot = rng.integers(0, V, 8).astype(np.uint32)
+    n = 40000
+    s = np.where(rng.random(n) < 0.3, hot[rng.integers(0, 8, n)], rng.integers(0, V, n)).astype(np.uint32)
+    d = rng.integers(0, V, n).astype(np.uint32)
+    w = rng.integers(1, 100, n).astype(np.uint32)
+    run_ops(g, o, [("ins", (s, d, w)), ("qry", (s, d)), ("commit", None),
+                   ("del", (s[::3].copy(), d[::3].copy())), ("ins", (s[::2].copy(), d[::2].copy(), w[::2] + 1)),
+                   ("qry", (s, d))])
+
+
+def test_large_vertex_count_offsets(cuda_lib):
+    """More than 4096 x 4096 vertices: the head offsets come from a
+    two-level prefix sum; edges of the last vertices land in their lists."""
+    mk = _mk()
+    V = 4096 * 4096 + 5000
+    g = mk.Graph(V, edge_capacity_hint=4096, buckets=2)
+    assert g.stats()["lists"] == 2 * V
+    # distinct new pairs: all stored; then all present with their weights
+    s = np.array([V - 1, V - 2, 0, 4096 * 4096, 123456], np.uint32)
+    d = np.array([0, V - 1, V - 1, 17, V - 3], np.uint32)
+    w = np.array([5, 6, 7, 8, 9], np.uint32)
+    assert np.array_equal(g.insert(s, d, w).cpu().numpy(), np.ones(5, np.uint8))
+    bm, wt = g.query(s, d)
+    assert mk.to_numpy_u32(bm)[0] == 0b11111
+    assert np.array_equal(mk.to_numpy_u32(wt), w)
+    absent_bm, _ = g.query(s, ((d.astype(np.uint64) + 2) % V).astype(np.uint32))
+    assert mk.to_numpy_u32(absent_bm)[0] == 0
+    assert g.last_error() == mk.MK_OK
