@@ -425,9 +425,10 @@ __global__ void k_inv_jump(RoundArgs a)
 // which stays fixed during the pass, so every such edge is relaxed even after
 // another in-neighbour has already given its target a finite distance; does
 // nothing if nothing was invalidated.  A streaming scan over the whole slab
-// array (scan_slab_chunks: the slabs in use, 32-slab chunks staged in shared
-// memory by bulk copies, the owners' tree nodes gathered a chunk ahead); the
-// slabs whose source has a finite distance are relaxed, one per lane.  Only
+// array (scan_slab_chunks: 32-slab chunks, of which only the slabs whose
+// source has a finite distance are staged in shared memory by bulk copies;
+// the owners' tree nodes are gathered two chunks ahead); each kept slab is
+// relaxed by one lane.  Only
 // distances change here (64-bit atomic minima whose results are not needed);
 // the improved targets are enqueued by k_enqueue_invalid.
 __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(RoundArgs a)
@@ -445,17 +446,17 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
             owners += own != kNil;
             return own != kNil ? node_dist(__ldcg(&a.D[own])) : kInf32;
         },
+        [](uint32_t dx) { return dx != kInf32; }, // slabs of unreached or invalidated sources are not read
         [&](const uint4 *buf, const uint8_t *comp, uint32_t n, uint32_t own_l, uint32_t dx_l) {
             // lane j takes the chunk's j-th slab in use whole: first the
             // bitmap words of all its 15 destinations (loads in flight
             // together), then the relaxations.  The slab's 16-byte parts are
             // read in a lane-rotated order, so the eight lanes of each
             // shared-memory phase hit distinct banks.
-            const bool has = lane < n;
-            const uint32_t it = has ? comp[lane] : 0u;
+            const bool active = lane < n; // every kept slab's source has a finite distance
+            const uint32_t it = active ? comp[lane] : 0u;
             const uint32_t own = __shfl_sync(kFull, own_l, it);
             const uint32_t dx = __shfl_sync(kFull, dx_l, it);
-            const bool active = has && dx != kInf32;
             slabs += active;
             if (!__any_sync(kFull, active))
                 return;

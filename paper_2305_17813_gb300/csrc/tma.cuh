@@ -84,12 +84,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
 // relax-into-invalid).  Each warp walks chunks of 32 consecutive slabs
 // (chunk k of warp w starts at slab (w + k * warps) * 32).  For every chunk
 // the warp reads the 32 owners (per-slab source, kNil for an unused pool
-// slab) and copies only the slabs in use, compacted, into one of two 4 KB
-// shared-memory buffers: each such lane issues one 128-byte bulk copy, all
-// completing on the buffer's mbarrier.  The copies of chunk k+1 are issued
-// before chunk k is processed, and the owners are read two chunks ahead, so
-// slab data, owners and the caller's per-owner gather (aux) are in flight
-// while the warp works.
+// slab) and copies only the slabs the caller keeps, compacted, into one of
+// two 4 KB shared-memory buffers: each such lane issues one 128-byte bulk
+// copy, all completing on the buffer's mbarrier.  The copies of chunk k+1
+// are issued before chunk k is processed, the caller's per-owner gather
+// (aux, which decides what is kept) runs two chunks ahead and the owners
+// three, so slab data, owners and gathers are in flight while the warp
+// works.
 constexpr uint32_t kScanWarps = 4;               // warps per block of a scan kernel
 constexpr uint32_t kScanChunk = 32;              // slabs per chunk
 constexpr uint32_t kScanWaitLimit = 1u << 20;    // polls of one chunk's barrier
@@ -101,14 +102,16 @@ struct ScanSmem {
 };
 
 // Scans every slab of the array.  aux_fn(owner) -> uint32_t is evaluated per
-// lane a chunk ahead (kNil owners included); chunk_fn(buf, comp, n, owner,
-// aux) processes one chunk: buf holds its n slabs in use (slab j at buf[8j ..
-// 8j+7]) and comp[j] the lane whose owner / aux belong to slab j.  Returns
-// false if a wait timed out (the copies still in flight were then given a
-// bounded time to land).  Must be called by full warps; the barriers are
-// initialised here.
-template <typename AuxFn, typename ChunkFn>
-__device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, AuxFn &&aux_fn, ChunkFn &&chunk_fn)
+// lane two chunks ahead (kNil owners included); a slab is copied and
+// processed only if its owner is not kNil and keep_fn(aux) holds.
+// chunk_fn(buf, comp, n, owner, aux) processes one chunk: buf holds its n
+// kept slabs (slab j at buf[8j .. 8j+7]) and comp[j] the lane whose owner /
+// aux belong to slab j.  Returns false if a wait timed out (the copies still
+// in flight were then given a bounded time to land).  Must be called by
+// full warps; the barriers are initialised here.
+template <typename AuxFn, typename KeepFn, typename ChunkFn>
+__device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, AuxFn &&aux_fn, KeepFn &&keep_fn,
+                                                 ChunkFn &&chunk_fn)
 {
     const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
     const uint64_t total = (uint64_t)g.H + g.P;
@@ -121,17 +124,18 @@ __device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, A
     }
     __syncwarp();
     auto owner_of = [&](uint64_t c) -> uint32_t { return c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil; };
-    // copies chunk c's slabs in use into buffer b; returns how many
-    auto issue = [&](uint64_t c, uint32_t own, uint32_t b) -> uint32_t {
+    // copies chunk c's kept slabs into buffer b; returns how many
+    auto issue = [&](uint64_t c, uint32_t own, uint32_t aux, uint32_t b) -> uint32_t {
         if (c >= total)
             return 0;
-        const uint32_t live = __ballot_sync(kFull, own != kNil);
+        const bool keep = own != kNil && keep_fn(aux);
+        const uint32_t live = __ballot_sync(kFull, keep);
         if (lane == 0) {
             fence_proxy_async_smem(); // the warp's reads of this buffer (ordered by __syncwarp) first
             mbar_arrive_expect_tx(&sm.bar[w][b], __popc(live) * 128u);
         }
         __syncwarp();
-        if (own != kNil) {
+        if (keep) {
             const uint32_t pos = __popc(live & ((1u << lane) - 1));
             sm.comp[w][b][pos] = (uint8_t)lane;
             bulk_copy_g2s(&sm.buf[w][b][pos * 8], slab_ptr(g, (uint32_t)(c + lane)), 128u, &sm.bar[w][b]);
@@ -139,17 +143,17 @@ __device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, A
         return __popc(live);
     };
     uint64_t c = warp0 * kScanChunk;
-    uint32_t own0 = owner_of(c);
-    uint32_t n0 = issue(c, own0, 0);
+    uint32_t own0 = owner_of(c), own1 = owner_of(c + stride), own2 = owner_of(c + 2 * stride);
     uint32_t aux0 = aux_fn(own0);
-    uint32_t own1 = owner_of(c + stride);
+    uint32_t n0 = issue(c, own0, aux0, 0);
+    uint32_t aux1 = aux_fn(own1);
     uint32_t k = 0;
     bool ok = true;
     for (; c < total; c += stride, ++k) {
         const uint32_t b = k & 1;
-        const uint32_t n1 = issue(c + stride, own1, b ^ 1);
-        const uint32_t aux1 = aux_fn(own1);
-        const uint32_t own2 = owner_of(c + 2 * stride);
+        const uint32_t n1 = issue(c + stride, own1, aux1, b ^ 1);
+        const uint32_t aux2 = aux_fn(own2);
+        const uint32_t own3 = owner_of(c + 3 * stride);
         ok = __all_sync(kFull, mbar_wait(&sm.bar[w][b], (k >> 1) & 1, kScanWaitLimit));
         if (!ok)
             break;
@@ -160,6 +164,8 @@ __device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, A
         n0 = n1;
         aux0 = aux1;
         own1 = own2;
+        aux1 = aux2;
+        own2 = own3;
     }
     if (!ok) {
         mbar_wait(&sm.bar[w][k & 1], (k >> 1) & 1, kScanWaitLimit);

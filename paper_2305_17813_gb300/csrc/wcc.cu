@@ -81,10 +81,6 @@ __device__ __forceinline__ void uf_find_n(uint32_t *p, uint32_t (&x)[N])
             px[i] = done[i] ? x[i] : uf_load<kCached>(p, x[i]);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            // vertex 0 is always a root (nothing has a smaller id): a parent
-            // of 0 ends the walk without loading p[0]
-            if (!done[i] && px[i] == 0)
-                x[i] = 0;
             done[i] = done[i] || px[i] == x[i];
             ppx[i] = done[i] ? px[i] : uf_load<kCached>(p, px[i]);
         }
