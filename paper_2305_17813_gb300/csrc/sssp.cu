@@ -36,7 +36,7 @@ using namespace mk;
 namespace {
 
 constexpr uint32_t kInf32 = 0xFFFFFFFFu;
-constexpr uint32_t kRoundsMaxThreads = 768; // block size limit of the persistent round kernel
+constexpr uint32_t kRoundsMaxThreads = 1024; // block size limit of the persistent round kernel
 constexpr uint32_t kBarrierSpins = 1u << 24;
 
 // consumer counter words
