@@ -24,7 +24,7 @@ using namespace mk;
 __global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
                         const uint32_t *__restrict__ w, uint64_t n, uint32_t V, unsigned long long *tkey,
                         uint32_t *tval, uint32_t mask, uint32_t *__restrict__ slot, DevState *st);
-__global__ void __launch_bounds__(256, 5) k_insert(GView g, const uint32_t *__restrict__ src,
+__global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w_in,
                                                    uint64_t n, const uint32_t *__restrict__ tval,
                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,

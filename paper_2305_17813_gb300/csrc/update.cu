@@ -300,7 +300,7 @@ __device__ __forceinline__ bool group_append(const GView &g, bool go, uint32_t t
 
 // One block per tile of 256 edges, one warp per 32 sorted edges; see the
 // file comment.
-__global__ void __launch_bounds__(256, 5) k_insert(GView g, const uint32_t *__restrict__ src,
+__global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w_in,
                                                    uint64_t n, const uint32_t *__restrict__ tval,
                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
