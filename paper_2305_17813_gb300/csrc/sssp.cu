@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(256) k_enqueue_invalid(RoundArgs a)
 // time (group index + k * groups in the grid; eight lists per warp in
 // flight); the next list's log entry, source and marker are loaded a step
 // ahead.
-__global__ void __launch_bounds__(256) k_relax_updated(RoundArgs a)
+__global__ void __launch_bounds__(256, 5) k_relax_updated(RoundArgs a)
 {
     const GView &g = a.g;
     const uint32_t s4 = lane_id() & 3u, g4 = lane_id() >> 2;
