@@ -5,30 +5,6 @@
 
 namespace mk {
 
-// Walks one slab list with the whole warp, one 128-byte slab per step, and
-// calls f(key, weight, live) on every lane for every slab: `key` is the
-// lane's word, `weight` the word of the next lane, `live` true on key lanes
-// holding a valid vertex (neither EMPTY nor TOMBSTONE).  On the first slab
-// only lanes >= first_lane count (the UpdateIterator skips the entries that
-// were already there at the last commit).  Stops after the slab whose next
-// lane is null or after max_hops slabs; returns the number of slabs read.
-template <typename F>
-__device__ __forceinline__ uint32_t walk_list(const GView &g, uint32_t slab, uint32_t first_lane, uint32_t max_hops,
-                                              F &&f)
-{
-    const uint32_t lane = lane_id();
-    uint32_t hop = 0;
-    for (; slab != kNil && hop < max_hops; ++hop) {
-        const uint32_t v = __ldcg(slab_ptr(g, slab) + lane);
-        const uint32_t wt = __shfl_down_sync(kFull, v, 1);
-        const bool live = is_key_lane(lane) && v < kTombKey && lane >= first_lane;
-        f(v, wt, live);
-        slab = __shfl_sync(kFull, v, kNextLane);
-        first_lane = 0;
-    }
-    return hop;
-}
-
 // A block's staging area for frontier entries.  Warps reserve slots with
 // shared-memory atomics; the block copies the staged entries to the global
 // frontier with one global atomicAdd (bq_flush), instead of one atomic per
@@ -142,74 +118,18 @@ __device__ __forceinline__ void bq_init(BlockFrontier &bq)
 
 namespace mk {
 
-// walk_lists_g8 whose first slab may already be loaded: with have_first,
-// x0 holds the lane's part of `slab` (group_load), so the caller can issue
-// that load early (for example one step ahead, while the previous list is
-// processed).
-template <typename F>
-__device__ __forceinline__ uint32_t walk_lists_g8_from(const GView &g, uint32_t slab, bool have_first, uint4 x0,
-                                                       uint32_t first_lane, uint32_t max_hops, F &&f)
-{
-    const uint32_t lane = lane_id(), sub = lane & 7u, gbase = lane & ~7u;
-    bool active = slab != kNil;
-    uint32_t loads = 0;
-    for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
-        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
-        if (hop == 0 && have_first)
-            x = x0;
-        else if (active)
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
-        loads += __popc(__ballot_sync(kFull, active && sub == 0));
-        const bool last = sub == 7u;
-        const bool l0 = active && x.x < kTombKey && 4 * sub >= first_lane;
-        const bool l1 = active && !last && x.z < kTombKey && 4 * sub + 2 >= first_lane;
-        f(x.x, x.y, l0);
-        f(x.z, x.w, l1);
-        const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
-        if (active) {
-            if (nxt == kNil || hop + 1 >= max_hops)
-                active = false;
-            else
-                slab = nxt;
-        }
-        first_lane = 0;
-    }
-    return loads;
-}
-
-// Tiled walk: each 8-lane group of the warp walks its own slab list (so a
-// warp has four 128-byte slab loads in flight instead of one); lane `sub` of
-// a group loads words 4*sub .. 4*sub+3 of the slab as one 16-byte vector,
-// i.e. pairs 2*sub and 2*sub+1 (lane 7: pair 14, the unused lane 30 and the
-// next-slab lane).  `slab` and `first_lane` are per group (kNil = the group
-// has no list).  Per slab, f(key, weight, live) is called twice by every
-// lane of the warp (convergent), once for each pair the lane holds; `live`
-// is false for free / deleted keys, for key words below first_lane on the
-// first slab, and for groups without a list.  Returns the number of slabs
-// loaded by the warp.
-template <typename F>
-__device__ __forceinline__ uint32_t walk_lists_g8(const GView &g, uint32_t slab, uint32_t first_lane,
-                                                  uint32_t max_hops, F &&f)
-{
-    return walk_lists_g8_from(g, slab, false, make_uint4(0, 0, 0, 0), first_lane, max_hops, f);
-}
-
-// The lane's 16-byte part of slab s (words 4*sub .. 4*sub+3), for a group
-// that starts a walk at s; an empty part for s == kNil.
-__device__ __forceinline__ uint4 group_load(const GView &g, uint32_t s)
-{
-    uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
-    if (s != kNil)
-        x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, s) + (lane_id() & 7u) * 4));
-    return x;
-}
-
-// Tiled walk with 4-lane groups (eight lists per warp): lane s4 of a group
-// holds words 8*s4 .. 8*s4+7 of the slab as two 16-byte vectors, i.e. pairs
-// 4*s4 .. 4*s4+3 (lane 3: pairs 12-14, then the unused lane and the next
-// lane); f(key, weight, live) is called four times per slab by every lane.
-// With have_first, (lo0, hi0) already hold the lane's part of `slab`
-// (group4_load).  Otherwise as walk_lists_g8.
+// Tiled walk: each 4-lane group of the warp walks its own slab list (eight
+// lists per warp, so a warp has eight slab loads in flight instead of one);
+// lane s4 of a group holds words 8*s4 .. 8*s4+7 of the slab as two 16-byte
+// vectors, i.e. pairs 4*s4 .. 4*s4+3 (lane 3: pairs 12-14, then the unused
+// lane and the next lane).  `slab` and `first_lane` are per group (kNil =
+// the group has no list).  Per slab, f(key, weight, live) is called four
+// times by every lane of the warp (convergent); `live` is false for free /
+// deleted keys, for key words below first_lane on the first slab, and for
+// groups without a list.  With have_first, (lo0, hi0) already hold the
+// lane's part of `slab` (group4_load), loaded ahead by the caller.  Stops
+// after the slab whose next lane is null or after max_hops slabs; returns
+// the number of slabs loaded by the warp.
 template <typename F>
 __device__ __forceinline__ uint32_t walk_lists_g4_from(const GView &g, uint32_t slab, bool have_first, uint4 lo0,
                                                        uint4 hi0, uint32_t first_lane, uint32_t max_hops, F &&f)
