@@ -316,20 +316,37 @@ def run_ours(args, world, rank, local):
         dev_batches.append({k: u32(bt[k]) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst",
                                                      "q_src", "q_dst")})
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
-    names = ["insert", "bfs1", "sssp1", "wcc1", "commit1", "delete", "bfs2", "sssp2", "wcc2", "commit2", "query"]
+    # phases on the main stream; wcc1_wait / wcc2_wait are what is left of
+    # the WCC calls after BFS and SSSP (the join); the WCC calls' own
+    # durations come from events on the WCC stream
+    names = ["insert", "bfs1", "sssp1", "wcc1_wait", "commit1", "delete", "bfs2", "sssp2", "wcc2_wait", "commit2",
+             "query"]
 
-    def step(bt, ev, hooks=None):
+    # WCC only reads the graph, as BFS and SSSP do: it runs on a second
+    # stream, forked after each update batch and joined before the commit,
+    # so its kernels overlap the BFS/SSSP kernels (a user of the library
+    # can do the same: calls on one graph may overlap when none of them
+    # changes it).
+    ws = torch.cuda.Stream(device=device)
+    wsp = ctypes.c_void_p(ws.cuda_stream)
+
+    def step(bt, ev, hooks=None, wev=None):
         hooks = hooks or {}
+        wev = wev or [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
         mk.check(lib.mk_insert_batch(h, P(bt["ins_src"]), P(bt["ins_dst"]), P(bt["ins_w"]), B, P(fl_i), sp), "ins")
         ev[1].record(stream)
         if "after_insert" in hooks:
             hooks["after_insert"]()
+        ws.wait_event(ev[1])
+        wev[0].record(ws)
+        mk.check(lib.mk_incr_wcc(h, P(out["lab"]), wsp), "wcc")
+        wev[1].record(ws)
         mk.check(lib.mk_incr_bfs(h, source, P(out["bd"]), P(out["bp"]), sp), "bfs")
         ev[2].record(stream)
         mk.check(lib.mk_incr_sssp(h, source, P(out["sd"]), P(out["sp"]), sp), "sssp")
         ev[3].record(stream)
-        mk.check(lib.mk_incr_wcc(h, P(out["lab"]), sp), "wcc")
+        stream.wait_event(wev[1])
         ev[4].record(stream)
         mk.check(lib.mk_commit_batch(h, sp), "commit")
         ev[5].record(stream)
@@ -337,11 +354,15 @@ def run_ours(args, world, rank, local):
             hooks["before_delete"]()
         mk.check(lib.mk_delete_batch(h, P(bt["del_src"]), P(bt["del_dst"]), B, P(fl_d), sp), "del")
         ev[6].record(stream)
+        ws.wait_event(ev[6])
+        wev[2].record(ws)
+        mk.check(lib.mk_incr_wcc(h, P(out["lab"]), wsp), "wcc")
+        wev[3].record(ws)
         mk.check(lib.mk_incr_bfs(h, source, P(out["bd"]), P(out["bp"]), sp), "bfs")
         ev[7].record(stream)
         mk.check(lib.mk_incr_sssp(h, source, P(out["sd"]), P(out["sp"]), sp), "sssp")
         ev[8].record(stream)
-        mk.check(lib.mk_incr_wcc(h, P(out["lab"]), sp), "wcc")
+        stream.wait_event(wev[3])
         ev[9].record(stream)
         mk.check(lib.mk_commit_batch(h, sp), "commit")
         ev[10].record(stream)
@@ -363,6 +384,7 @@ def run_ours(args, world, rank, local):
     g.profile(True)
     launches0 = g.launch_count()
     evs = [events() for _ in range(K)]
+    wevs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     clock = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
     barrier(dist, device)
@@ -372,7 +394,7 @@ def run_ours(args, world, rank, local):
         for k in range(K):
             flush.fill_(k + 1)
             torch.cuda.nvtx.range_push("step")
-            step(dev_batches[W + k], evs[k])
+            step(dev_batches[W + k], evs[k], wev=wevs[k])
             torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     wall = time.time() - wall0
@@ -387,6 +409,8 @@ def run_ours(args, world, rank, local):
     step_ms = [evs[k][0].elapsed_time(evs[k][11]) for k in range(K)]
     phase = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
              for i, n in enumerate(names)}
+    wcc_incr = statistics.mean(wevs[k][0].elapsed_time(wevs[k][1]) for k in range(K))
+    wcc_static = statistics.mean(wevs[k][2].elapsed_time(wevs[k][3]) for k in range(K))
     local_ms = statistics.mean(step_ms)
     ms_max, = reduce_across([local_ms], "max", dist, device)
     units_total, = reduce_across([3.0 * B], "sum", dist, device)
@@ -427,7 +451,8 @@ def run_ours(args, world, rank, local):
         "query_medges_s": round(B / phase["query"] / 1e3, 1),
         "incr_sssp_ms": round(phase["sssp1"], 3), "decr_sssp_ms": round(phase["sssp2"], 3),
         "incr_bfs_ms": round(phase["bfs1"], 3), "decr_bfs_ms": round(phase["bfs2"], 3),
-        "incr_wcc_ms": round(phase["wcc1"], 3), "static_wcc_ms": round(phase["wcc2"], 3),
+        "incr_wcc_ms": round(wcc_incr, 3), "static_wcc_ms": round(wcc_static, 3),
+        "wcc_overlap": "WCC runs on a second stream beside BFS/SSSP; its ms are its own duration there",
         "phases_ms": {k: round(v, 3) for k, v in phase.items()},
         "roofline": roof, "kernels": kernels, "counters": ctr,
         "gpu_launches": int(launches), "wall_s_timed": round(wall, 3), "gen_s": round(gen_s, 1),
