@@ -273,7 +273,10 @@ def run_ours(args, world, rank, local):
     n_e2e = 0 if args.no_e2e else K
     G, source, batches, gen_s = make_workload(args, W + K + n_e2e)
     V, E = G.V, len(G.src)
-    stream = torch.cuda.current_stream()
+    # the step runs on a high-priority stream; WCC, which only reads the
+    # graph, runs beside it on a default-priority stream (see step())
+    stream = torch.cuda.Stream(device=device, priority=-1)
+    torch.cuda.set_stream(stream)
     sp = ctypes.c_void_p(stream.cuda_stream)
 
     def u32(a):
