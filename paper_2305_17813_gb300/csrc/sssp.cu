@@ -62,24 +62,6 @@ constexpr uint32_t kSoloRounds = 4096;
 __device__ __forceinline__ uint32_t node_dist(unsigned long long d) { return (uint32_t)(d >> 32); }
 __device__ __forceinline__ uint32_t node_parent(unsigned long long d) { return (uint32_t)d; }
 
-// Relaxes edge (x, y, w) given x's distance dx; returns true if D[y] dropped.
-__device__ __forceinline__ bool relax(unsigned long long *D, uint32_t x, uint32_t dx, uint32_t y, uint32_t w)
-{
-    const unsigned long long nd = (unsigned long long)dx + w;
-    if (nd >= kInf32)
-        return false;
-    const unsigned long long cand = (nd << 32) | x;
-    if (cand >= __ldcg(&D[y]))
-        return false;
-    return cand < atomicMin(&D[y], cand);
-}
-
-// Vertex-level dedup for one round: true for the first lane that stamps y.
-__device__ __forceinline__ bool first_this_round(uint32_t *stamp, uint32_t y, uint32_t round)
-{
-    return atomicExch(&stamp[y], round) != round;
-}
-
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) { return *(volatile const uint32_t *)p; }
 
 } // namespace
@@ -103,22 +85,58 @@ struct RoundArgs {
 
 namespace {
 
-// Relaxes edge (x, y, w) for every lane with `live` and enqueues the lists of
-// each vertex whose distance this lane lowered first in this round (staged in
-// the block's frontier buffer).  y's vinfo entry is loaded before the stamp
-// exchange so both are in flight together.  Must be called by the full warp.
-__device__ __forceinline__ void relax_edge(const RoundArgs &a, uint32_t x, uint32_t dx, uint32_t y, uint32_t w,
-                                           bool live, uint32_t round, BlockFrontier &bq, uint2 *Fn, uint32_t *cnt,
-                                           int *overflow, unsigned long long &edges, unsigned long long &improved)
+// Relaxes the lane's four edges (x, y[k], w[k]) with live[k] and enqueues
+// the lists of each vertex whose distance this lane lowered first in this
+// round (staged in the block's frontier buffer).  The accesses of the four
+// edges go out together, step by step: the four targets' tree nodes are
+// read, then the atomic minima of the candidates that beat them are issued,
+// then the improved targets' vinfo entries are read and their round stamps
+// exchanged, so a slab costs three memory round trips per lane instead of
+// three per edge.  Must be called by the full warp.
+__device__ __forceinline__ void relax_edges4(const RoundArgs &a, uint32_t x, uint32_t dx, const uint32_t (&y)[4],
+                                             const uint32_t (&w)[4], const bool (&live)[4], uint32_t round,
+                                             BlockFrontier &bq, uint2 *Fn, uint32_t *cnt, int *overflow,
+                                             unsigned long long &edges, unsigned long long &improved)
 {
-    edges += __popc(__ballot_sync(kFull, live));
-    bool up = live && relax(a.D, x, dx, y, a.unit ? 1u : w);
-    uint2 vi = make_uint2(0, 0);
-    if (up)
-        vi = a.g.vinfo[y];
-    up = up && first_this_round(a.stamp, y, round);
-    improved += __popc(__ballot_sync(kFull, up));
-    enqueue_lists_block(bq, y, up, vi, Fn, cnt, a.cap, overflow);
+    // candidate of edge k: <nd[k], x>
+    auto cand = [&](uint32_t d) { return ((unsigned long long)d << 32) | x; };
+    uint32_t nd[4];
+    unsigned long long cur[4];
+    bool up[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        edges += __popc(__ballot_sync(kFull, live[k]));
+        const unsigned long long d = (unsigned long long)dx + (a.unit ? 1u : w[k]);
+        up[k] = live[k] && d < kInf32;
+        nd[k] = (uint32_t)d;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        cur[k] = up[k] ? __ldcg(&a.D[y[k]]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (up[k] && cand(nd[k]) < cur[k])
+            cur[k] = atomicMin(&a.D[y[k]], cand(nd[k]));
+        else
+            up[k] = false;
+    uint2 vi[4];
+    uint32_t st[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        up[k] = up[k] && cand(nd[k]) < cur[k];
+        vi[k] = make_uint2(0, 0);
+        st[k] = round;
+        if (up[k]) {
+            vi[k] = a.g.vinfo[y[k]];
+            st[k] = atomicExch(&a.stamp[y[k]], round);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        up[k] = up[k] && st[k] != round;
+        improved += __popc(__ballot_sync(kFull, up[k]));
+        enqueue_lists_block(bq, y[k], up[k], vi[k], Fn, cnt, a.cap, overflow);
+    }
 }
 
 // One round over frontier F[0, n): every 4-lane group of every warp takes
@@ -151,9 +169,11 @@ __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2
         lists += __popc(__ballot_sync(kFull, e.x != kNil && s4 == 0));
         const uint32_t L = dx != kInf32 ? e.x : kNil;
         const uint32_t x = e.y, d = dx;
-        slabs += walk_lists_g4_from(g, L, true, lo, hi, 0, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            relax_edge(a, x, d, y, w, live, round, bq, Fn, cnt, overflow, edges, improved);
-        });
+        slabs += walk_lists_g4_from(g, L, true, lo, hi, 0, a.max_hops,
+                                    [&](const uint32_t(&y)[4], const uint32_t(&w)[4], const bool(&live)[4]) {
+                                        relax_edges4(a, x, d, y, w, live, round, bq, Fn, cnt, overflow, edges,
+                                                     improved);
+                                    });
         e = ne;
         ne = nne;
         dx = ndx;
@@ -616,9 +636,11 @@ __global__ void __launch_bounds__(256, 5) k_relax_updated(RoundArgs a)
         group4_load(g, start, lo, hi);
         lists += __popc(__ballot_sync(kFull, go && s4 == 0));
         const uint32_t x = src;
-        slabs += walk_lists_g4_from(g, start, true, lo, hi, first_lane, a.max_hops, [&](uint32_t y, uint32_t w, bool live) {
-            relax_edge(a, x, dx, y, w, live, round, bq, a.front[0], a.ctr + kCnt0, overflow, edges, improved);
-        });
+        slabs += walk_lists_g4_from(g, start, true, lo, hi, first_lane, a.max_hops,
+                                    [&](const uint32_t(&y)[4], const uint32_t(&w)[4], const bool(&live)[4]) {
+                                        relax_edges4(a, x, dx, y, w, live, round, bq, a.front[0], a.ctr + kCnt0,
+                                                     overflow, edges, improved);
+                                    });
         L = nL;
         nL = nnL;
         src = nsrc;

@@ -123,8 +123,10 @@ namespace mk {
 // lane s4 of a group holds words 8*s4 .. 8*s4+7 of the slab as two 16-byte
 // vectors, i.e. pairs 4*s4 .. 4*s4+3 (lane 3: pairs 12-14, then the unused
 // lane and the next lane).  `slab` and `first_lane` are per group (kNil =
-// the group has no list).  Per slab, f(key, weight, live) is called four
-// times by every lane of the warp (convergent); `live` is false for free /
+// the group has no list).  Per slab, f(key, weight, live) is called once by
+// every lane of the warp (convergent) with the lane's four pairs as arrays
+// (key[k], weight[k], live[k], k = 0..3), so that the callee can put the
+// memory accesses of all four in flight together; `live` is false for free /
 // deleted keys, for key words below first_lane on the first slab, and for
 // groups without a list.  With have_first, (lo0, hi0) already hold the
 // lane's part of `slab` (group4_load), loaded ahead by the caller.  Stops
@@ -149,10 +151,12 @@ __device__ __forceinline__ uint32_t walk_lists_g4_from(const GView &g, uint32_t 
         }
         loads += __popc(__ballot_sync(kFull, active && s4 == 0));
         const uint32_t w0 = 8 * s4;
-        f(lo.x, lo.y, active && lo.x < kTombKey && w0 >= first_lane);
-        f(lo.z, lo.w, active && lo.z < kTombKey && w0 + 2 >= first_lane);
-        f(hi.x, hi.y, active && hi.x < kTombKey && w0 + 4 >= first_lane);
-        f(hi.z, hi.w, active && s4 != 3u && hi.z < kTombKey && w0 + 6 >= first_lane);
+        const uint32_t key[4] = {lo.x, lo.z, hi.x, hi.z}, wt[4] = {lo.y, lo.w, hi.y, hi.w};
+        const bool live[4] = {active && lo.x < kTombKey && w0 >= first_lane,
+                              active && lo.z < kTombKey && w0 + 2 >= first_lane,
+                              active && hi.x < kTombKey && w0 + 4 >= first_lane,
+                              active && s4 != 3u && hi.z < kTombKey && w0 + 6 >= first_lane};
+        f(key, wt, live);
         const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
         if (active) {
             if (nxt == kNil || hop + 1 >= max_hops)
