@@ -7,7 +7,7 @@
 // slab list (source and bucket) in shared memory, so the edges of one list
 // sit side by side, and one warp owns 32 consecutive sorted edges.  An edge
 // whose list has no other edge in the warp (nearly every edge of a random
-// batch) is handled by one 8-lane group, four at a time per warp, with
+// batch) is handled by one 4-lane group, eight at a time per warp, with
 // 16-byte slab loads; the lists with several edges in the warp are walked
 // once each by the whole warp, which matches all of the list's destinations
 // against every 128-byte slab (paper, Sec. "Experimental Evaluation",
@@ -169,33 +169,50 @@ __device__ __forceinline__ bool match_slab(uint32_t v, uint32_t members, bool mi
     return found;
 }
 
-// Lanes of the calling lane's 8-lane group in a warp-wide ballot.
-__device__ __forceinline__ uint32_t group_bits(uint32_t ballot) { return (ballot >> (lane_id() & ~7u)) & 0xFFu; }
+// Lanes of the calling lane's 4-lane group in a warp-wide ballot.
+__device__ __forceinline__ uint32_t group_bits(uint32_t ballot) { return (ballot >> (lane_id() & ~3u)) & 0xFu; }
 
-// Finds key d in list L with one 8-lane group (lane sub holds words 4*sub ..
-// 4*sub+3 of each slab: pairs 2*sub and 2*sub+1; lane 7's second slot is the
-// unused lane and the next lane).  Every group of the warp calls it in
-// lockstep (L == kNil: the group has nothing to do).  On return *slab is the
-// slab where the walk stopped -- the one holding d (*pair = its pair index)
-// or the chain's tail -- and x holds the lane's part of it.  Returns 1 if d
-// was found, 0 if not, 2 if the hop bound was hit.
-__device__ __forceinline__ uint32_t group_find(const GView &g, uint32_t L, uint32_t d, uint32_t max_hops,
-                                               uint32_t *slab, uint32_t *pair, uint4 &x, unsigned long long &loads)
+// Index (0..3) of the lane's first pair whose key is k, 4 if none.  Lane s4
+// of a 4-lane group holds words 8*s4 .. 8*s4+7 of a slab as two 16-byte
+// vectors (lo, hi): pairs 4*s4 .. 4*s4+3; lane 3's last slot is the unused
+// lane and the next lane, not a pair.
+__device__ __forceinline__ uint32_t first_pair_with(const uint4 &lo, const uint4 &hi, uint32_t k)
 {
-    const uint32_t sub = lane_id() & 7u, gbase = lane_id() & ~7u;
+    const bool last = (lane_id() & 3u) == 3u;
+    return lo.x == k ? 0u : lo.z == k ? 1u : hi.x == k ? 2u : (!last && hi.z == k) ? 3u : 4u;
+}
+
+__device__ __forceinline__ void group_load(const GView &g, uint32_t s, uint4 &lo, uint4 &hi)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(slab_ptr(g, s) + (lane_id() & 3u) * 8);
+    lo = __ldcg(p);
+    hi = __ldcg(p + 1);
+}
+
+// Finds key d in list L with one 4-lane group (layout of first_pair_with).
+// Every group of the warp calls it in lockstep (L == kNil: the group has
+// nothing to do).  On return *slab is the slab where the walk stopped -- the
+// one holding d (*pair = its pair index) or the chain's tail -- and (lo, hi)
+// hold the lane's part of it.  Returns 1 if d was found, 0 if not, 2 if the
+// hop bound was hit.
+__device__ __forceinline__ uint32_t group_find(const GView &g, uint32_t L, uint32_t d, uint32_t max_hops,
+                                               uint32_t *slab, uint32_t *pair, uint4 &lo, uint4 &hi,
+                                               unsigned long long &loads)
+{
+    const uint32_t s4 = lane_id() & 3u, gbase = lane_id() & ~3u;
     bool active = L != kNil;
     uint32_t res = 0, s = L;
-    x = make_uint4(kEmptyKey, kFull, kEmptyKey, kFull);
+    lo = make_uint4(kEmptyKey, kFull, kEmptyKey, kFull);
+    hi = lo;
     for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
         if (active)
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, s) + sub * 4));
-        loads += __popc(__ballot_sync(kFull, active && sub == 0));
-        const bool h0 = active && x.x == d, h1 = active && sub != 7u && x.z == d;
-        const uint32_t hits = group_bits(__ballot_sync(kFull, h0 || h1));
-        const uint32_t frees = group_bits(__ballot_sync(kFull, active && (x.x == kEmptyKey ||
-                                                                              (sub != 7u && x.z == kEmptyKey))));
-        const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
-        const uint32_t hp = __shfl_sync(kFull, h0 ? 2 * sub : 2 * sub + 1, gbase + (hits ? __ffs(hits) - 1 : 0));
+            group_load(g, s, lo, hi);
+        loads += __popc(__ballot_sync(kFull, active && s4 == 0));
+        const uint32_t hk = first_pair_with(lo, hi, d);
+        const uint32_t hits = group_bits(__ballot_sync(kFull, active && hk < 4u));
+        const uint32_t frees = group_bits(__ballot_sync(kFull, active && first_pair_with(lo, hi, kEmptyKey) < 4u));
+        const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
+        const uint32_t hp = __shfl_sync(kFull, 4 * s4 + hk, gbase + (hits ? __ffs(hits) - 1 : 0));
         if (active) {
             if (hits) {
                 *pair = hp;
@@ -215,32 +232,32 @@ __device__ __forceinline__ uint32_t group_find(const GView &g, uint32_t L, uint3
     return res;
 }
 
-// Appends <d, wt> to a list whose tail is `tail` (x = the lane's part of
-// it) with one 8-lane group: the group's lowest free pair is claimed with a
-// 64-bit CAS (a lost CAS re-reads the tail); a full tail with nothing after
-// it gets a pool slab holding the pair, published with a CAS on the tail's
-// next lane (the loser frees its slab and moves on to the winner's).  Every
-// group calls it in lockstep (go == false: nothing to do).  Returns true on
-// the group's lanes if the pair was stored; sets *err (kErrPool or
-// kErrTimeout) when it gives up.
-__device__ __forceinline__ bool group_append(const GView &g, bool go, uint32_t tail, uint4 x, uint32_t d, uint32_t wt,
-                                             uint32_t owner_src, uint32_t salt, uint64_t guard_max,
+// Appends <d, wt> to a list whose tail is `tail` ((lo, hi) = the lane's part
+// of it) with one 4-lane group: the tail's lowest free pair is claimed with
+// a 64-bit CAS (a lost CAS re-reads the tail), so the pairs of a slab fill
+// in order; a full tail with nothing after it gets a pool slab holding the
+// pair, published with a CAS on the tail's next lane (the loser frees its
+// slab and moves on to the winner's).  Every group calls it in lockstep
+// (go == false: nothing to do).  Returns true on the group's lanes if the
+// pair was stored; sets *err (kErrPool or kErrTimeout) when it gives up.
+__device__ __forceinline__ bool group_append(const GView &g, bool go, uint32_t tail, uint4 lo, uint4 hi, uint32_t d,
+                                             uint32_t wt, uint32_t owner_src, uint32_t salt, uint64_t guard_max,
                                              unsigned long long &loads, unsigned long long &linked, int *err)
 {
-    const uint32_t sub = lane_id() & 7u, gbase = lane_id() & ~7u;
+    const uint32_t s4 = lane_id() & 3u, gbase = lane_id() & ~3u;
     bool active = go, stored = false;
     for (uint64_t guard = 0; __any_sync(kFull, active); ++guard) {
-        const bool f0 = x.x == kEmptyKey, f1 = sub != 7u && x.z == kEmptyKey;
-        const uint32_t frees = group_bits(__ballot_sync(kFull, active && (f0 || f1)));
-        const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
+        const uint32_t fk = first_pair_with(lo, hi, kEmptyKey);
+        const uint32_t frees = group_bits(__ballot_sync(kFull, active && fk < 4u));
+        const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
         if (active && guard > guard_max) {
             *err = kErrTimeout;
             active = false;
         }
         // claim the group's lowest free pair
         bool ok = false;
-        if (active && frees && sub == (uint32_t)(__ffs(frees) - 1)) {
-            const uint32_t p = f0 ? 2 * sub : 2 * sub + 1;
+        if (active && frees && s4 == (uint32_t)(__ffs(frees) - 1)) {
+            const uint32_t p = 4 * s4 + fk;
             ok = atomicCAS(reinterpret_cast<unsigned long long *>(slab_ptr(g, tail) + 2 * p), kEmptyPair,
                            pack_pair(d, wt)) == kEmptyPair;
         }
@@ -248,26 +265,28 @@ __device__ __forceinline__ bool group_append(const GView &g, bool go, uint32_t t
         // a full tail with nothing after it: a new slab holding the pair
         const bool grow = active && !frees && nxt == kNil;
         uint32_t ns = kNil;
-        if (grow && sub == 0)
+        if (grow && s4 == 0)
             ns = alloc_slab_one(g, salt ^ (uint32_t)(guard << 24));
         ns = __shfl_sync(kFull, ns, gbase);
         uint32_t old = kNil;
         if (grow && ns != kNil) {
-            uint4 word = make_uint4(kEmptyKey, kFull, kEmptyKey, kFull);
-            if (sub == 0)
-                word = make_uint4(d, wt, kEmptyKey, kFull);
-            else if (sub == 7u)
-                word = make_uint4(kEmptyKey, kFull, kFull, kNil);
-            __stcg(reinterpret_cast<uint4 *>(slab_ptr(g, ns) + sub * 4), word);
-            if (sub == 0)
+            uint4 wlo = make_uint4(kEmptyKey, kFull, kEmptyKey, kFull), whi = wlo;
+            if (s4 == 0)
+                wlo = make_uint4(d, wt, kEmptyKey, kFull);
+            else if (s4 == 3u)
+                whi = make_uint4(kEmptyKey, kFull, kFull, kNil);
+            uint4 *q = reinterpret_cast<uint4 *>(slab_ptr(g, ns) + s4 * 8);
+            __stcg(q, wlo);
+            __stcg(q + 1, whi);
+            if (s4 == 0)
                 g.owner[ns] = owner_src;
             __threadfence();
-            if (sub == 0)
+            if (s4 == 0)
                 old = atomicCAS(slab_ptr(g, tail) + kNextLane, kNil, ns);
         }
         old = __shfl_sync(kFull, old, gbase);
         const bool won = grow && ns != kNil && old == kNil;
-        linked += __popc(__ballot_sync(kFull, won && sub == 0));
+        linked += __popc(__ballot_sync(kFull, won && s4 == 0));
         if (active) {
             if (frees) {
                 if (claimed) {
@@ -283,17 +302,17 @@ __device__ __forceinline__ bool group_append(const GView &g, bool go, uint32_t t
                 stored = true;
                 active = false;
             } else { // lost the link: free the slab, follow the winner's
-                if (sub == 0)
+                if (s4 == 0)
                     g.owner[ns] = kNil;
                 __threadfence();
-                if (sub == 0)
+                if (s4 == 0)
                     free_slab(g, ns);
                 tail = old;
             }
         }
         if (active)
-            x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, tail) + sub * 4));
-        loads += __popc(__ballot_sync(kFull, active && sub == 0));
+            group_load(g, tail, lo, hi);
+        loads += __popc(__ballot_sync(kFull, active && s4 == 0));
     }
     return stored;
 }
@@ -316,18 +335,18 @@ __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__re
     if (status_hint(g.st) != 0)
         return;
     const uint32_t w = (e.first && w_in) ? w_in[e.idx] : 1u;
-    const uint32_t gi = lane >> 3, sub = lane & 7u;
+    const uint32_t gi = lane >> 2, s4 = lane & 3u;
     uint8_t done = 0;
     unsigned long long loads = 0, linked = 0;
     // edges whose list no other lane of the warp has (nearly all of a random
-    // batch): one per 8-lane group, four per warp at a time
+    // batch): one per 4-lane group, eight per warp at a time
     const uint32_t peers = __match_any_sync(kFull, e.first ? (unsigned long long)e.list : (1ull << 32) | lane);
     const bool single = e.first && __popc(peers) == 1;
     const uint32_t sq = __ballot_sync(kFull, single);
     const uint32_t rank = __popc(sq & lanemask_lt());
     const uint64_t guard_max = n + 64 + 4ull * max_hops;
     int err = 0;
-    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(sq); ++pass) {
+    for (uint32_t pass = 0; pass * 8 < (uint32_t)__popc(sq); ++pass) {
         const uint32_t own = group_item(sq, pass, gi);
         const uint32_t o = own & 31u;
         const uint32_t Lo = __shfl_sync(kFull, e.list, o), d = __shfl_sync(kFull, e.dst, o);
@@ -335,22 +354,22 @@ __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__re
         const uint32_t io = __shfl_sync(kFull, e.idx, o);
         const uint32_t L = own < 32 ? Lo : kNil;
         uint32_t tail = kNil, pair = 0;
-        uint4 x;
-        const uint32_t f = group_find(g, L, d, max_hops, &tail, &pair, x, loads);
+        uint4 lo, hi;
+        const uint32_t f = group_find(g, L, d, max_hops, &tail, &pair, lo, hi, loads);
         if (f == 2)
             err = kErrTimeout;
-        const bool st = group_append(g, L != kNil && f == 0, tail, x, d, wo, so,
-                                     (uint32_t)(warp * 4 + gi) * 0x9E3779B9u ^ tail, guard_max, loads, linked, &err);
+        const bool st = group_append(g, L != kNil && f == 0, tail, lo, hi, d, wo, so,
+                                     (uint32_t)(warp * 8 + gi) * 0x9E3779B9u ^ tail, guard_max, loads, linked, &err);
         // the first insert into L in this epoch nominates L for the
         // updated-list log (k_log_updated compacts the nominations)
-        if (st && sub == 0 && flag_updated(g, L))
+        if (st && s4 == 0 && flag_updated(g, L))
             cand[io] = L;
-        // the edge of rank r went to group r % 4 in pass r / 4
-        const uint32_t res = __shfl_sync(kFull, st ? 1u : 0u, (rank & 3u) * 8);
-        if (single && (rank >> 2) == pass)
+        // the edge of rank r went to group r % 8 in pass r / 8
+        const uint32_t res = __shfl_sync(kFull, st ? 1u : 0u, (rank & 7u) * 4);
+        if (single && (rank >> 3) == pass)
             done = (uint8_t)res;
     }
-    if (err && sub == 0)
+    if (err && s4 == 0)
         set_status(g.st, err);
     // lists with several edges in the warp: the whole warp per list
     uint32_t todo = __ballot_sync(kFull, e.first && !single);
@@ -512,28 +531,28 @@ __global__ void __launch_bounds__(256, 8) k_delete(GView g, const uint32_t *__re
     // no early exit: the whole block meets in block_enqueue
     if (status_hint(g.st) != 0)
         e.first = false;
-    const uint32_t gi = lane >> 3, sub = lane & 7u;
+    const uint32_t gi = lane >> 2, s4 = lane & 3u;
     bool removed = false;
     unsigned long long loads = 0;
-    // edges whose list no other lane of the warp has: one per 8-lane group
+    // edges whose list no other lane of the warp has: one per 4-lane group
     const uint32_t peers = __match_any_sync(kFull, e.first ? (unsigned long long)e.list : (1ull << 32) | lane);
     const bool single = e.first && __popc(peers) == 1;
     const uint32_t sq = __ballot_sync(kFull, single);
     const uint32_t rank = __popc(sq & lanemask_lt());
-    for (uint32_t pass = 0; pass * 4 < (uint32_t)__popc(sq); ++pass) {
+    for (uint32_t pass = 0; pass * 8 < (uint32_t)__popc(sq); ++pass) {
         const uint32_t own = group_item(sq, pass, gi);
         const uint32_t o = own & 31u;
         const uint32_t Lo = __shfl_sync(kFull, e.list, o), d = __shfl_sync(kFull, e.dst, o);
         const uint32_t L = own < 32 ? Lo : kNil;
         uint32_t at = kNil, pair = 0;
-        uint4 x;
-        const uint32_t f = group_find(g, L, d, max_hops, &at, &pair, x, loads);
-        if (f == 2 && sub == 0)
+        uint4 lo, hi;
+        const uint32_t f = group_find(g, L, d, max_hops, &at, &pair, lo, hi, loads);
+        if (f == 2 && s4 == 0)
             set_status(g.st, kErrTimeout);
-        if (f == 1 && sub == 0)
+        if (f == 1 && s4 == 0)
             *reinterpret_cast<unsigned long long *>(slab_ptr(g, at) + 2 * pair) = kTombPair;
-        const uint32_t res = __shfl_sync(kFull, f == 1 ? 1u : 0u, (rank & 3u) * 8);
-        if (single && (rank >> 2) == pass)
+        const uint32_t res = __shfl_sync(kFull, f == 1 ? 1u : 0u, (rank & 7u) * 4);
+        if (single && (rank >> 3) == pass)
             removed = res != 0;
     }
     // lists with several edges in the warp: the whole warp per list

@@ -182,12 +182,12 @@ __device__ __forceinline__ void group4_load(const GView &g, uint32_t s, uint4 &l
     }
 }
 
-// The k-th set bit of q handed to 8-lane group `gi` in pass `pass` (four
+// The k-th set bit of q handed to 4-lane group `gi` in pass `pass` (eight
 // groups per pass): returns the lane index holding that group's item, or
 // 32 when the pass has fewer items than groups.
 __device__ __forceinline__ uint32_t group_item(uint32_t q, uint32_t pass, uint32_t gi)
 {
-    const uint32_t k = pass * 4 + gi;
+    const uint32_t k = pass * 8 + gi;
     if (k >= (uint32_t)__popc(q))
         return 32;
     return nth_set_bit(q, k);
