@@ -172,7 +172,8 @@ mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
  * bucket, walk its chain).  d_bitmap (ceil(n/32) words, required): bit i%32 of
  * word i/32 is 1 iff edge i is present.  d_w (n words, nullable): the stored
  * weight, or 0 when absent.  Queries are independent and unsorted; one
- * 8-lane group with 16-byte loads walks one query's chain. */
+ * group of 4 or 8 lanes (the tuned shape) with 16-byte loads walks one
+ * query's chain. */
 mk_status mk_query_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                          uint32_t *d_bitmap, uint32_t *d_w, void *stream);
 

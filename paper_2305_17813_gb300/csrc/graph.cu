@@ -157,41 +157,48 @@ __global__ void k_rule(uint32_t *deg, uint32_t V, float per_bucket)
 // "UpdateSlabPointers()"): for every updated list, walk from its marker slab
 // to the last slab; the new marker is that slab and the first free key lane
 // in it, or kInvalidLane when it is full; the updated flag is cleared.  The
-// updated lists are read from the updated-list log; every 8-lane group of
-// every warp takes one logged list at a time and walks it with 16-byte loads
-// (lane sub holds words 4*sub .. 4*sub+3).
+// updated lists are read from the updated-list log; every 4-lane group of
+// every warp takes one logged list at a time (eight per warp) and walks it
+// with two 16-byte loads per lane (lane s4 holds words 8*s4 .. 8*s4+7).
 __global__ void __launch_bounds__(256) k_update_slab_pointers(GView g, uint32_t max_hops)
 {
-    const uint32_t lane = lane_id(), sub = lane & 7u, gi = lane >> 3, gbase = lane & ~7u;
+    const uint32_t lane = lane_id(), s4 = lane & 3u, gi = lane >> 2, gbase = lane & ~3u;
     const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 8;
     unsigned long long loads = 0;
-    for (uint64_t base = warp0 * 4; base < n; base += gs) {
+    for (uint64_t base = warp0 * 8; base < n; base += gs) {
         const uint64_t i = base + gi;
         const uint32_t list = i < n ? g.ulog[i] : kNil;
         uint32_t slab = list != kNil ? (uint32_t)(g.lmark[list] >> 32) : kNil;
         bool active = slab != kNil;
-        uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
+        uint4 lo = make_uint4(kEmptyKey, kFull, kFull, kFull), hi = lo;
         for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
-            if (active)
-                x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
-            loads += __popc(__ballot_sync(kFull, active && sub == 0));
-            const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
+            if (active) {
+                const uint4 *p = reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + s4 * 8);
+                lo = __ldcg(p);
+                hi = __ldcg(p + 1);
+            }
+            loads += __popc(__ballot_sync(kFull, active && s4 == 0));
+            const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
             if (active) {
                 if (nxt == kNil || hop + 1 >= max_hops)
-                    active = false; // x keeps the last slab
+                    active = false; // (lo, hi) keep the last slab
                 else
                     slab = nxt;
             }
         }
-        // first free key lane of the last slab: key words 4*sub and 4*sub+2
-        // (word 30, lane 7's third word, is not a key lane)
-        uint32_t fl = x.x == kEmptyKey ? 4 * sub : ((sub != 7u && x.z == kEmptyKey) ? 4 * sub + 2 : 32u);
-        fl = min(fl, __shfl_xor_sync(kFull, fl, 4));
+        // first free key lane of the last slab: key words 8*s4, +2, +4, +6
+        // (word 30, lane 3's seventh word, is not a key lane)
+        const uint32_t w0 = 8 * s4;
+        uint32_t fl = lo.x == kEmptyKey   ? w0
+                      : lo.z == kEmptyKey ? w0 + 2
+                      : hi.x == kEmptyKey ? w0 + 4
+                      : (s4 != 3u && hi.z == kEmptyKey) ? w0 + 6
+                                                        : 32u;
         fl = min(fl, __shfl_xor_sync(kFull, fl, 2));
         fl = min(fl, __shfl_xor_sync(kFull, fl, 1));
-        if (sub == 0 && list != kNil) {
+        if (s4 == 0 && list != kNil) {
             g.lmark[list] = ((unsigned long long)slab << 32) | (fl < 32 ? fl : (uint32_t)kInvalidLane);
             g.lupd[list] = 0;
         }
@@ -524,8 +531,8 @@ mk_status mk_commit_batch(mk_graph *g, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t max_hops = g->v.P + 2;
     MK_TRY(timed(g, "update_slab_pointers", s, 2, [&]() {
-        // one 8-lane group per logged list
-        const uint32_t grid = std::min<uint32_t>(grid_for(std::max<uint64_t>(g->ulog_bound, 1) * 8, 256), num_sms() * 16);
+        // one 4-lane group per logged list
+        const uint32_t grid = std::min<uint32_t>(grid_for(std::max<uint64_t>(g->ulog_bound, 1) * 4, 256), num_sms() * 16);
         k_update_slab_pointers<<<grid, 256, 0, s>>>(g->v, max_hops);
         k_clear_logs<<<1, 1, 0, s>>>(g->d_state);
         return cudaSuccess;

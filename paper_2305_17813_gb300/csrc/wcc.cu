@@ -9,7 +9,8 @@
 // a whole slab at once: the source and the slab's live destinations are
 // hooked under the smallest of their roots (one parallel round of finds and
 // CASes per slab instead of one union per edge on the same source root), and
-// a warp walks four lists at a time.
+// a warp walks eight lists at a time (incremental pass) or eight slabs (static
+// pass).
 //
 // Static pass: every live edge of every list.  Incremental pass (insert-only
 // epochs): only the entries written since the last commit, read with the
@@ -173,15 +174,6 @@ __device__ __forceinline__ bool group_union(uint32_t *p, const uint32_t (&e)[N],
     return false;
 }
 
-// The two elements of one lane of an 8-lane group.
-__device__ __forceinline__ bool group_union2(uint32_t *p, uint32_t e0, bool a0, uint32_t e1, bool a1,
-                                             uint32_t limit)
-{
-    const uint32_t e[2] = {e0, e1};
-    const bool act[2] = {a0, a1};
-    return group_union<8, 2>(p, e, act, limit);
-}
-
 } // namespace
 
 __global__ void k_uf_init(uint32_t *p, uint32_t V)
@@ -195,25 +187,25 @@ __global__ void k_uf_init(uint32_t *p, uint32_t V)
 // with the destinations inserted since the last commit, read with the
 // UpdateIterator from the list's marker (the marker slab's lanes before the
 // marker lane are skipped; a full marker slab is skipped entirely).  Every
-// 8-lane group of every warp takes one list at a time (group index + k *
-// groups in the grid) and walks it with 16-byte loads (pairs 2*sub and
-// 2*sub+1 per lane); the unused slot of lane 7 (slab lane 30) carries the
-// list's source, so each slab's source and destinations are united in one
-// group_union2.  The next list's log entry, source and marker are loaded a
-// step ahead.
-__global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, uint32_t max_hops, int *failed)
+// 4-lane group of every warp takes one list at a time (group index + k *
+// groups in the grid; eight lists per warp) and walks it with two 16-byte
+// loads per lane (pairs 4*s4 .. 4*s4+3); the unused slot of lane 3 (slab
+// lane 30) carries the list's source, so each slab's source and
+// destinations are united in one group_union.  The next list's log entry,
+// source and marker are loaded a step ahead.
+__global__ void __launch_bounds__(256, 5) k_uf_hook(GView g, uint32_t *p, uint32_t max_hops, int *failed)
 {
-    const uint32_t lane = lane_id(), gi = lane >> 3, sub = lane & 7u, gbase = lane & ~7u;
+    const uint32_t lane = lane_id(), gi = lane >> 2, s4 = lane & 3u, gbase = lane & ~3u;
     const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 4;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 8;
     unsigned long long slabs = 0, edges = 0;
-    uint64_t i = warp0 * 4 + gi;
+    uint64_t i = warp0 * 8 + gi;
     uint32_t L = i < n ? g.ulog[i] : kNil;
     uint32_t nL = i + gs < n ? g.ulog[i + gs] : kNil;
     uint32_t src = L != kNil ? g.list_src[L] : 0;
     unsigned long long mk = L != kNil ? g.lmark[L] : 0;
-    for (uint64_t base = warp0 * 4; base < n; base += gs, i += gs) {
+    for (uint64_t base = warp0 * 8; base < n; base += gs, i += gs) {
         const uint32_t nnL = i + 2 * gs < n ? g.ulog[i + 2 * gs] : kNil;
         const uint32_t nsrc = nL != kNil ? g.list_src[nL] : 0;
         const unsigned long long nmk = nL != kNil ? g.lmark[nL] : 0;
@@ -222,17 +214,25 @@ __global__ void __launch_bounds__(256, 6) k_uf_hook(GView g, uint32_t *p, uint32
         uint32_t slab = L != kNil ? (uint32_t)(mk >> 32) : kNil;
         bool active = slab != kNil;
         for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
-            uint4 x = make_uint4(kEmptyKey, kFull, kFull, kFull);
-            if (active)
-                x = __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * 4));
-            slabs += __popc(__ballot_sync(kFull, active && sub == 0));
-            const bool last = sub == 7u;
-            const bool a0 = active && x.x < kTombKey && 4 * sub >= first_lane;
-            const bool a1 = last ? active : (active && x.z < kTombKey && 4 * sub + 2 >= first_lane);
-            edges += __popc(__ballot_sync(kFull, a0)) + __popc(__ballot_sync(kFull, a1 && !last));
-            if (!group_union2(p, x.x, a0, last ? src : x.z, a1, 1u << 20) && lane == 0)
+            uint4 lo = make_uint4(kEmptyKey, kFull, kFull, kFull), hi = lo;
+            if (active) {
+                const uint4 *q = reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + s4 * 8);
+                lo = __ldcg(q);
+                hi = __ldcg(q + 1);
+            }
+            slabs += __popc(__ballot_sync(kFull, active && s4 == 0));
+            const bool last = s4 == 3u;
+            const uint32_t w0 = 8 * s4;
+            const uint32_t e[4] = {lo.x, lo.z, hi.x, last ? src : hi.z};
+            const bool act[4] = {active && lo.x < kTombKey && w0 >= first_lane,
+                                 active && lo.z < kTombKey && w0 + 2 >= first_lane,
+                                 active && hi.x < kTombKey && w0 + 4 >= first_lane,
+                                 last ? active : (active && hi.z < kTombKey && w0 + 6 >= first_lane)};
+            edges += __popc(__ballot_sync(kFull, act[0])) + __popc(__ballot_sync(kFull, act[1])) +
+                     __popc(__ballot_sync(kFull, act[2])) + __popc(__ballot_sync(kFull, act[3] && !last));
+            if (!group_union<4, 4>(p, e, act, 1u << 20) && lane == 0)
                 *failed = 1;
-            const uint32_t nxt = __shfl_sync(kFull, x.w, gbase + 7);
+            const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
             if (active) {
                 if (nxt == kNil || hop + 1 >= max_hops)
                     active = false;
@@ -374,8 +374,8 @@ extern "C" mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream)
     }
     if (incremental) {
         MK_TRY(timed(g, "wcc_hook_updated", s, 1, [&]() {
-            // one 8-lane group per logged list
-            const uint64_t threads = std::max<uint64_t>(g->ulog_bound, 1) * 8;
+            // one 4-lane group per logged list
+            const uint64_t threads = std::max<uint64_t>(g->ulog_bound, 1) * 4;
             k_uf_hook<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 12), 256, 0, s>>>(g->v, c->uf, max_hops,
                                                                                                failed);
             return cudaSuccess;
