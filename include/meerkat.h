@@ -145,7 +145,7 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
  * are identical to mk_insert_batch.
  *  - n <= MK_NOALLOC_MAX_BATCH (65,536); a larger n returns
  *    MK_ERR_INVALID_ARG and enqueues nothing.
- *  - The staging scratch is one fixed 2 MiB device array inside the library
+ *  - The staging scratch is one fixed 1 MiB device array inside the library
  *    (every GPU that loads the library holds it until the process exits).
  *    The first call on each device looks up the array's address
  *    (cudaGetSymbolAddress, no allocation); make that first call before any

@@ -48,15 +48,12 @@ mk_status ensure_scratch(mk_graph *g, uint64_t n, cudaStream_t s)
     while (table < 2 * cap)
         table <<= 1;
     MK_CUDA(cudaStreamSynchronize(s));
-    device_free(g, g->d_tkey, g->table_size * 8);
-    device_free(g, g->d_tval, g->table_size * 4);
+    device_free(g, g->d_tpos, g->table_size * 4);
     device_free(g, g->d_slot, g->scratch_cap * 4);
     device_free(g, g->d_cand, g->scratch_cap * 4);
-    g->d_tkey = nullptr;
-    g->d_tval = g->d_slot = g->d_cand = nullptr;
+    g->d_tpos = g->d_slot = g->d_cand = nullptr;
     g->scratch_cap = g->table_size = 0;
-    MK_TRY(device_alloc(g, (void **)&g->d_tkey, table * 8));
-    MK_TRY(device_alloc(g, (void **)&g->d_tval, table * 4));
+    MK_TRY(device_alloc(g, (void **)&g->d_tpos, table * 4));
     MK_TRY(device_alloc(g, (void **)&g->d_slot, cap * 4));
     MK_TRY(device_alloc(g, (void **)&g->d_cand, cap * 4));
     g->table_size = table;
@@ -507,8 +504,7 @@ mk_status mk_graph_destroy(mk_graph *g)
     cudaFree(v.ulog);
     cudaFree(v.owner);
     cudaFree(g->d_state);
-    cudaFree(g->d_tkey);
-    cudaFree(g->d_tval);
+    cudaFree(g->d_tpos);
     cudaFree(g->d_slot);
     cudaFree(g->d_cand);
     cudaFree(g->d_dlog);

@@ -69,12 +69,12 @@ struct mk_graph {
     mk::DevState *d_state = nullptr;
     uint64_t bytes = 0;          // device bytes held
     // staging scratch, grown on demand: the batch's hash set of (src, dst)
-    // pairs (table_size entries, a power of two >= 2 * scratch_cap), each
-    // edge's entry, and the updated-list nominations of an insert
+    // pairs as batch positions (table_size entries, a power of two >= 2 *
+    // scratch_cap), each edge's entry, and the updated-list nominations of
+    // an insert
     uint64_t scratch_cap = 0;
     uint64_t table_size = 0;
-    unsigned long long *d_tkey = nullptr;
-    uint32_t *d_tval = nullptr, *d_slot = nullptr, *d_cand = nullptr;
+    uint32_t *d_tpos = nullptr, *d_slot = nullptr, *d_cand = nullptr;
     // change log of the current epoch: deleted (src << 32 | dst)
     unsigned long long *d_dlog = nullptr;
     uint64_t dlog_cap = 0, dlog_bound = 0;

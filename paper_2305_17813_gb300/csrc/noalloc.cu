@@ -22,11 +22,11 @@ using namespace mk;
 
 // Kernels of update.cu, launched here unchanged.
 __global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
-                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, unsigned long long *tkey,
-                        uint32_t *tval, uint32_t mask, uint32_t *__restrict__ slot, DevState *st);
+                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, uint32_t *tpos, uint32_t mask,
+                        uint32_t *__restrict__ slot, DevState *st);
 __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w_in,
-                                                   uint64_t n, const uint32_t *__restrict__ tval,
+                                                   uint64_t n, const uint32_t *__restrict__ tpos,
                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
                                                    uint32_t max_hops, uint32_t *__restrict__ cand);
 __global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n);
@@ -35,10 +35,9 @@ namespace {
 
 constexpr uint64_t kNoAllocMaxBatch = 1ull << 16;
 constexpr uint64_t kTable = 2 * kNoAllocMaxBatch;            // hash-set entries (a power of two)
-constexpr size_t kTkeyBytes = kTable * 8;
-constexpr size_t kTvalBytes = kTable * 4;
+constexpr size_t kTposBytes = kTable * 4;
 constexpr size_t kEdgeBytes = kNoAllocMaxBatch * 4;
-constexpr size_t kScratchBytes = kTkeyBytes + kTvalBytes + 2 * kEdgeBytes; // 2 MiB
+constexpr size_t kScratchBytes = kTposBytes + 2 * kEdgeBytes; // 1 MiB
 
 } // namespace
 
@@ -94,25 +93,24 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
     g->change_seq++;
     if (n == 0)
         return MK_OK;
-    unsigned long long *tkey = (unsigned long long *)base;
-    uint32_t *tval = (uint32_t *)(base + kTkeyBytes);
-    uint32_t *slot = (uint32_t *)(base + kTkeyBytes + kTvalBytes);
-    uint32_t *cand = (uint32_t *)(base + kTkeyBytes + kTvalBytes + kEdgeBytes);
-    // the hash set must start empty (all-ones keys and positions); slots and
+    uint32_t *tpos = (uint32_t *)base;
+    uint32_t *slot = (uint32_t *)(base + kTposBytes);
+    uint32_t *cand = (uint32_t *)(base + kTposBytes + kEdgeBytes);
+    // the hash set must start empty (all-ones positions); slots and
     // nominations are written in full before they are read; the caller's
     // flags are cleared
-    MK_CUDA(cudaMemsetAsync(tkey, 0xFF, kTkeyBytes + kTvalBytes, s));
+    MK_CUDA(cudaMemsetAsync(tpos, 0xFF, kTposBytes, s));
     if (d_inserted)
         MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
     MK_TRY(timed(g, "stage_dedup", s, 1, [&]() {
-        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(d_src, d_dst, d_w, n, g->v.V, tkey, tval, (uint32_t)(kTable - 1),
-                                                 slot, g->d_state);
+        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(d_src, d_dst, d_w, n, g->v.V, tpos, (uint32_t)(kTable - 1), slot,
+                                                 g->d_state);
         return cudaSuccess;
     }));
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 2, [&]() {
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, tval, slot, d_inserted, max_hops, cand);
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, tpos, slot, d_inserted, max_hops, cand);
         k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, cand, n);
         return cudaSuccess;
     });

@@ -22,8 +22,6 @@
 
 using namespace mk;
 
-constexpr unsigned long long kNoPair = ~0ull; // empty hash-set entry
-
 // 64-bit finaliser of splitmix64 (Steele, Lea and Flood, "Fast splittable
 // pseudorandom number generators", 2014), as the hash of a (src, dst) pair.
 __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
@@ -37,12 +35,16 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
 }
 
 // Validates edge i and enters its (src, dst) pair in the batch's hash set
-// (open addressing with linear probing, at most half full): the entry keeps
-// the smallest batch position of the pair, and slot[i] names the entry.
+// (open addressing with linear probing, at most half full).  An entry holds
+// a batch position of its pair rather than the pair: an edge claims an empty
+// entry with one CAS, and an edge that meets a taken entry compares its pair
+// with the batch's pair at the stored position; on a match it lowers the
+// entry to its own position if that is smaller (atomicMin), so every entry
+// ends with the smallest position of its pair.  slot[i] names the entry.
 // Invalid edges get slot kNil and set the invalid-argument status.
 __global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
-                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, unsigned long long *tkey,
-                        uint32_t *tval, uint32_t mask, uint32_t *__restrict__ slot, DevState *st)
+                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, uint32_t *tpos, uint32_t mask,
+                        uint32_t *__restrict__ slot, DevState *st)
 {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     bool bad = false;
@@ -54,14 +56,10 @@ __global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__rest
             const unsigned long long key = ((unsigned long long)s << 32) | d;
             uint32_t h = (uint32_t)mix64(key) & mask;
             for (uint32_t probe = 0; probe <= mask; ++probe) {
-                unsigned long long k = __ldcg(&tkey[h]);
-                if (k == kNoPair) {
-                    k = atomicCAS(&tkey[h], kNoPair, key);
-                    if (k == kNoPair)
-                        k = key;
-                }
-                if (k == key) {
-                    atomicMin(&tval[h], (uint32_t)i);
+                const uint32_t j = atomicCAS(&tpos[h], kNil, (uint32_t)i);
+                if (j == kNil || (src[j] == s && dst[j] == d)) {
+                    if (j != kNil && j > (uint32_t)i)
+                        atomicMin(&tpos[h], (uint32_t)i);
                     at = h;
                     break;
                 }
@@ -115,7 +113,7 @@ __device__ __forceinline__ unsigned long long bitonic_sort_256(unsigned long lon
 // tile.  Edges that are not applied get flag 0 here.
 __device__ __forceinline__ LaneEdge stage_tile(const GView &g, const uint32_t *__restrict__ src,
                                                const uint32_t *__restrict__ dst, uint64_t n,
-                                               const uint32_t *__restrict__ tval, const uint32_t *__restrict__ slot,
+                                               const uint32_t *__restrict__ tpos, const uint32_t *__restrict__ slot,
                                                uint8_t *__restrict__ flags, unsigned long long *keys)
 {
     const uint64_t tile0 = blockIdx.x * 256ull;
@@ -123,7 +121,7 @@ __device__ __forceinline__ LaneEdge stage_tile(const GView &g, const uint32_t *_
     unsigned long long key = ~0ull;
     if (i < n) {
         const uint32_t sl = slot[i];
-        if (sl != kNil && __ldcg(&tval[sl]) == (uint32_t)i) {
+        if (sl != kNil && __ldcg(&tpos[sl]) == (uint32_t)i) {
             const uint32_t s = src[i], d = dst[i];
             const uint2 vi = g.vinfo[s];
             key = ((unsigned long long)(vi.x + bucket_of(d, vi.y)) << 32) | threadIdx.x;
@@ -321,7 +319,7 @@ __device__ __forceinline__ bool group_append(const GView &g, bool go, uint32_t t
 // file comment.
 __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w_in,
-                                                   uint64_t n, const uint32_t *__restrict__ tval,
+                                                   uint64_t n, const uint32_t *__restrict__ tpos,
                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
                                                    uint32_t max_hops, uint32_t *__restrict__ cand)
 {
@@ -331,7 +329,7 @@ __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__re
     const unsigned long long warp = i >> 5; // salt of this warp's pool probes
     if (i < n)
         cand[i] = kNil;
-    const LaneEdge e = stage_tile(g, src, dst, n, tval, slot, flags, keys);
+    const LaneEdge e = stage_tile(g, src, dst, n, tpos, slot, flags, keys);
     if (status_hint(g.st) != 0)
         return;
     const uint32_t w = (e.first && w_in) ? w_in[e.idx] : 1u;
@@ -520,14 +518,14 @@ __global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__
 // with a block-aggregated enqueue.
 __global__ void __launch_bounds__(256, 8) k_delete(GView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, uint64_t n,
-                                                   const uint32_t *__restrict__ tval, const uint32_t *__restrict__ slot,
+                                                   const uint32_t *__restrict__ tpos, const uint32_t *__restrict__ slot,
                                                    uint8_t *__restrict__ flags, unsigned long long *dlog,
                                                    uint32_t dlog_cap, uint32_t max_hops)
 {
     __shared__ unsigned long long keys[256];
     __shared__ uint32_t s2[2];
     const uint32_t lane = lane_id();
-    LaneEdge e = stage_tile(g, src, dst, n, tval, slot, flags, keys);
+    LaneEdge e = stage_tile(g, src, dst, n, tpos, slot, flags, keys);
     // no early exit: the whole block meets in block_enqueue
     if (status_hint(g.st) != 0)
         e.first = false;
@@ -598,12 +596,11 @@ mk_status stage(mk_graph *g, const uint32_t *src, const uint32_t *dst, const uin
                 cudaStream_t s)
 {
     MK_TRY(ensure_scratch(g, n, s));
-    // the hash set must start empty: all-ones keys and positions
-    MK_CUDA(cudaMemsetAsync(g->d_tkey, 0xFF, g->table_size * 8, s));
-    MK_CUDA(cudaMemsetAsync(g->d_tval, 0xFF, g->table_size * 4, s));
+    // the hash set must start empty (all-ones positions)
+    MK_CUDA(cudaMemsetAsync(g->d_tpos, 0xFF, g->table_size * 4, s));
     return timed(g, "stage_dedup", s, 1, [&]() {
-        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(src, dst, w, n, g->v.V, g->d_tkey, g->d_tval,
-                                                 (uint32_t)(g->table_size - 1), g->d_slot, g->d_state);
+        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(src, dst, w, n, g->v.V, g->d_tpos, (uint32_t)(g->table_size - 1),
+                                                 g->d_slot, g->d_state);
         return cudaSuccess;
     });
 }
@@ -627,7 +624,7 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 2, [&]() {
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, g->d_tval, g->d_slot, d_inserted,
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, g->d_tpos, g->d_slot, d_inserted,
                                                   max_hops, g->d_cand);
         k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_cand, n);
         return cudaSuccess;
@@ -665,7 +662,7 @@ mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     MK_TRY(stage(g, d_src, d_dst, nullptr, n, s));
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "delete", s, 1, [&]() {
-        k_delete<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, n, g->d_tval, g->d_slot, d_deleted, g->d_dlog,
+        k_delete<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, n, g->d_tpos, g->d_slot, d_deleted, g->d_dlog,
                                                   (uint32_t)g->dlog_cap, max_hops);
         return cudaSuccess;
     });
