@@ -214,20 +214,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # profiles/launches_powerlaw_rmat20_b1M.md (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "cf201142342282d888035e9eea43e7e0eb6ca6956fba60d11a59a38957bd4ba3"
+NCU_TRAFFIC_SOURCES_SHA = "c7a95fd98b5692ea87578f46e07ca812601e95f5896f123e5b802b17c04abb73"
 NCU_TRAFFIC = {
-    "sssp_rounds": 46489120,
-    "sssp_relax_into_invalid": 356063872,
-    "sssp_enqueue_invalid": 11216256,
-    "sssp_relax_updated": 145658240,
-    "sssp_invalidate_jump": 10471904,
-    "wcc_hook_all": 351031040,
-    "wcc_hook_updated": 136834432,
-    "insert": 118793024,
-    "delete": 186433152,
-    "query": 131153664,
-    "stage_dedup": 125355456,
-    "update_slab_pointers": 60652992,
+    "sssp_rounds": 46955200,
+    "sssp_relax_into_invalid": 281393280,
+    "sssp_enqueue_invalid": 11145984,
+    "sssp_relax_updated": 149820352,
+    "sssp_invalidate_jump": 20943808,
+    "sssp_invalidate": 13741632,
+    "wcc_hook_all": 351127680,
+    "wcc_hook_updated": 139695232,
+    "insert": 241860352,
+    "delete": 199024000,
+    "query": 130466816,
+    "stage_dedup": 40151168,
+    "update_slab_pointers": 60534528,
 }
 
 
