@@ -470,9 +470,11 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
         [&](const uint4 *buf, const uint8_t *comp, uint32_t n, uint32_t own_l, uint32_t dx_l) {
             // lane j takes the chunk's j-th slab in use whole: first the
             // bitmap words of all its 15 destinations (loads in flight
-            // together), then the relaxations.  The slab's 16-byte parts are
-            // read in a lane-rotated order, so the eight lanes of each
-            // shared-memory phase hit distinct banks.
+            // together), keeping the keys in registers and the live pairs
+            // as bits of a mask; then the bit tests, reading a weight from
+            // shared memory only for a relaxed edge.  The slab's 16-byte
+            // parts are read in a lane-rotated order, so the eight lanes of
+            // each shared-memory phase hit distinct banks.
             const bool active = lane < n; // every kept slab's source has a finite distance
             const uint32_t it = active ? comp[lane] : 0u;
             const uint32_t own = __shfl_sync(kFull, own_l, it);
@@ -480,35 +482,35 @@ __global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_slabs(Ro
             slabs += active;
             if (!__any_sync(kFull, active))
                 return;
-            const uint4 *mine = buf + (active ? lane : 0) * 8;
-            uint32_t word[16];
+            const uint32_t *mine = reinterpret_cast<const uint32_t *>(buf + (active ? lane : 0) * 8);
+            uint32_t key[16], word[16];
+            uint32_t live = 0; // bit k: pair k of the rotated order is a live edge
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const uint32_t qq = (q + lane) & 7u;
-                const uint4 v = mine[qq];
+                const uint4 v = reinterpret_cast<const uint4 *>(mine)[qq];
                 const bool l0 = active && v.x < kTombKey, l1 = active && qq != 7u && v.z < kTombKey;
+                key[2 * q] = v.x;
+                key[2 * q + 1] = v.z;
+                live |= (l0 ? 1u : 0u) << (2 * q) | (l1 ? 1u : 0u) << (2 * q + 1);
                 word[2 * q] = l0 ? __ldg(&a.inv[v.x >> 5]) : 0u; // the bitmap is fixed during the pass
                 word[2 * q + 1] = l1 ? __ldg(&a.inv[v.z >> 5]) : 0u;
             }
+            uint32_t hit = 0; // bit k: pair k's destination is invalidated
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t qq = (q + lane) & 7u;
-                const uint4 v = mine[qq];
-                const bool l0 = active && v.x < kTombKey, l1 = active && qq != 7u && v.z < kTombKey;
-                edges += l0 + l1;
-                const bool t0 = l0 && ((word[2 * q] >> (v.x & 31)) & 1u);
-                const bool t1 = l1 && ((word[2 * q + 1] >> (v.z & 31)) & 1u);
-                targets += t0 + t1;
-                if (t0) {
-                    const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : v.y);
-                    if (nd < kInf32)
-                        atomicMin(&a.D[v.x], (nd << 32) | own);
-                }
-                if (t1) {
-                    const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : v.w);
-                    if (nd < kInf32)
-                        atomicMin(&a.D[v.z], (nd << 32) | own);
-                }
+            for (int k = 0; k < 16; ++k)
+                hit |= ((word[k] >> (key[k] & 31u)) & 1u) << k;
+            hit &= live;
+            edges += __popc(live);
+            targets += __popc(hit);
+            while (hit) {
+                const int k = __ffs(hit) - 1;
+                hit &= hit - 1;
+                // pair k sits in part (k/2 + lane) % 8, word 2 * (k & 1), weight next to it
+                const uint32_t at = (((uint32_t)(k >> 1) + lane) & 7u) * 4 + 2 * (k & 1);
+                const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : mine[at + 1]);
+                if (nd < kInf32)
+                    atomicMin(&a.D[mine[at]], (nd << 32) | own);
             }
         });
     if (!ok)
