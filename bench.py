@@ -191,8 +191,9 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
     if family == "delete":
         return launches * n_per_launch * (8 + 32 + 32) + 128 * ctr["delete_slabs"]
     if family == "sssp_rounds":
+        # rounds, then the tree nodes unpacked into the caller's dist/parent
         return (ctr["relax_lists"] * (4 + 4 + 8) + 128 * ctr["relax_slabs"] + 16 * ctr["relax_edges"]
-                + ctr["relax_improved"] * (8 + 4 + 8))
+                + ctr["relax_improved"] * (8 + 4 + 8) + ctr.get("unpacked", 0) * (8 + 4 + 4))
     if family == "sssp_relax_into_invalid":
         return 4 * ctr["scan_owners"] + (128 + 8) * ctr["scan_slabs"] + 16 * ctr["scan_targets"]
     if family == "sssp_enqueue_invalid":
@@ -200,8 +201,8 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
     if family == "sssp_relax_updated":
         return (ctr["seed_lists"] * (4 + 8 + 8) + 128 * ctr["seed_slabs"] + 16 * ctr["seed_edges"]
                 + ctr["seed_improved"] * (8 + 4 + 8))
-    if family == "sssp_invalidate_jump":
-        return ctr["jump_vertices"] * (8 + 4 + 8 + 4)
+    if family == "sssp_invalidate_walk":
+        return ctr["walk_vertices"] * 8 + ctr["invalidated"] * 8
     if family == "wcc_hook_all":
         return 128 * ctr["wcc_slabs"] + 16 * ctr["wcc_edges"]
     if family == "wcc_hook_updated":
@@ -220,7 +221,6 @@ NCU_TRAFFIC = {
     "sssp_relax_into_invalid": 281393280,
     "sssp_enqueue_invalid": 11145984,
     "sssp_relax_updated": 149820352,
-    "sssp_invalidate_jump": 20943808,
     "sssp_invalidate": 13741632,
     "wcc_hook_all": 351127680,
     "wcc_hook_updated": 139695232,

@@ -410,7 +410,8 @@ mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *sla
  * edges united; BFS/SSSP rounds and grid barriers of the round kernel;
  * decremental scan: slabs in use copied, slabs relaxed, live edges examined, edges
  * into invalidated vertices, invalidated vertices given a finite distance;
- * vertices visited by the invalidation pass (then reserved words up to 32).
+ * vertices visited by the invalidation pass; BFS/SSSP tree nodes written to
+ * the caller's dist/parent arrays (then reserved words up to 32).
  * The BFS/SSSP prologue words above count the inserted-edge prologue only.  Copies up to n
  * (<= 32) values to out (host); reset != 0 zeroes them.  Synchronises
  * `stream`. */

@@ -331,7 +331,6 @@ static void destroy_consumer(mk_graph *g, Consumer *c)
     device_free(g, c->front[1], H * 8);
     device_free(g, c->stamp, V * 4);
     device_free(g, c->inv, (V + 31) / 32 * 4);
-    device_free(g, c->anc, V * 4);
     device_free(g, c->uf, V * 4);
     device_free(g, c->counters, 64);
     delete c;

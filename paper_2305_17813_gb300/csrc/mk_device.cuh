@@ -63,7 +63,8 @@ enum Counter {
     kCtrScanEdges = 22,    //   live edges examined
     kCtrScanTargets = 23,  //   edges into invalidated vertices (relaxed)
     kCtrScanImproved = 24, //   invalidated vertices given a finite distance
-    kCtrJumpVertices = 25, // vertices visited by the invalidation pass
+    kCtrWalkVertices = 25, // vertices visited by the invalidation pass
+    kCtrUnpacked = 26,     // BFS/SSSP tree nodes written to the caller's dist/parent arrays
     kNumCounters = 32
 };
 

@@ -26,7 +26,6 @@ struct Consumer {
     uint2 *front[2] = {nullptr, nullptr}; // BFS/SSSP list frontiers (H entries <list, source> each)
     uint32_t *stamp = nullptr;  // BFS/SSSP: round in which a vertex was last enqueued
     uint32_t *inv = nullptr;    // BFS/SSSP: bitmap of vertices invalidated by this call's deletes
-    uint32_t *anc = nullptr;    // BFS/SSSP: tree ancestors for the invalidation (pointer jumping)
     uint32_t round = 0;         // last stamp value used
     uint32_t *uf = nullptr;     // WCC: union-find parents (V)
     uint32_t *counters = nullptr; // device: frontier sizes etc. (16 words)

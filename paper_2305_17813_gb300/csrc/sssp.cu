@@ -80,7 +80,8 @@ struct RoundArgs {
     uint32_t max_rounds;
     uint32_t source;
     int unit;
-    uint32_t *anc;        // decremental prologue: tree ancestor of each vertex (pointer jumping)
+    uint32_t *dist;       // the caller's outputs (nullable), written when the phase ends
+    uint32_t *parent;
 };
 
 namespace {
@@ -316,11 +317,29 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
         r = s_word;
         __syncthreads(); // every thread has read s_word before thread 0 rewrites it
     }
+    // The phase is over: every block left the loop at the same round, after
+    // the grid barrier that ended the last relaxation, so D is final.  The
+    // call's epilogue runs here instead of in two more launches: the tree
+    // nodes go to the caller's arrays, and the round stamp moves past every
+    // id this call used.
+    if (a.dist || a.parent) {
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < a.g.V; v += stride) {
+            const unsigned long long d = __ldcg(&a.D[v]);
+            if (a.dist)
+                a.dist[v] = node_dist(d);
+            if (a.parent)
+                a.parent[v] = node_parent(d);
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr[kRoundsDone] = r;
+        a.ctr[kRid] += r + 2;
         atomicAdd(&a.g.st->ctr[kCtrRounds][0], (unsigned long long)r);
         atomicAdd(&a.g.st->ctr[kCtrGridBarriers][0], (unsigned long long)bars);
-        if (!ok || r >= a.max_rounds)
+        if (a.dist || a.parent)
+            atomicAdd(&a.g.st->ctr[kCtrUnpacked][0], (unsigned long long)a.g.V);
+        if (!ok || r >= a.max_rounds || ld_volatile(a.ctr + kOverflow) != 0)
             set_status(a.g.st, kErrTimeout);
     }
 }
@@ -378,57 +397,39 @@ __global__ void k_invalidate(const unsigned long long *dlog, const DevState *st,
 
 // The invalidation spreads to every tree descendant of the seeds: a vertex
 // is invalid iff the path from it up the shortest-path tree reaches a seed
-// before the source.  The paper walks each vertex up to the source; here the
-// walks share their work by pointer jumping on a copy of the parent pointers
-// (the union-find "find" with path halving): anc[v] starts as v's tree
-// parent, and as v itself at the source, at the seeds and at unreached
-// vertices, which are the roots of the forest.  Tree parents have strictly
-// smaller distances (weights are >= 1), so the forest has no cycles.
-__global__ void k_inv_anc_init(RoundArgs a)
-{
-    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.g.V)
-        return;
-    const unsigned long long d = __ldcg(&a.D[v]);
-    a.anc[v] = (v == a.source || d == kInfNode) ? v : node_parent(d);
-}
-
-// Each reached vertex walks anc up to its root and is invalidated when the
-// root is not the source; it then stores the root in its own anc entry, so
-// later walks that reach it jump straight to the root.  Only a vertex's own
-// entry is written: path halving would have every walk store into the
-// entries of the shared upper part of the tree (the hubs of a power-law
-// graph), and those writes contend.  The invalidated vertices of one warp
-// set their bits with one atomicOr (32 consecutive vertices share a bitmap
-// word).
-__global__ void k_inv_jump(RoundArgs a)
+// before the source.  As in the paper, each reached vertex walks its tree
+// parents up until it meets the source (valid) or a vertex without a tree
+// node (invalid: a seed, or a vertex this pass has already invalidated);
+// invalid vertices get <INF, INVALID> at once, so later walks through them
+// stop there.  Tree parents have strictly smaller distances (weights are
+// >= 1), so every walk ends.  The loads are plain (L1-cacheable): the upper
+// part of the tree, where most walks pass, stays in L1, and a stale line can
+// only hide an invalidation made by this pass, whose walk went on up the
+// same parents to the same seed, so the outcome is the same.  The
+// invalidated vertices of one warp set their bits with one atomicOr (32
+// consecutive vertices share a bitmap word).
+__global__ void k_inv_walk(RoundArgs a)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if ((v & ~31u) >= a.g.V)
         return;
-    count_add(a.g.st, kCtrJumpVertices, __popc(__ballot_sync(kFull, v < a.g.V)));
+    count_add(a.g.st, kCtrWalkVertices, __popc(__ballot_sync(kFull, v < a.g.V)));
     bool bad = false;
-    if (v < a.g.V && v != a.source && __ldcg(&a.D[v]) != kInfNode) {
-        uint32_t x = v, hops = 0;
-        bool ok = true;
-        // plain (L1-cacheable) loads: a stale anc value is an older ancestor
-        // and roots never change, so the walk still ends at v's root, while
-        // the upper part of the tree, where most walks pass, stays in L1
-        for (;;) {
-            const uint32_t px = a.anc[x];
-            if (px == x)
+    const unsigned long long dv = v < a.g.V && v != a.source ? a.D[v] : kInfNode;
+    if (dv != kInfNode) {
+        uint32_t x = node_parent(dv), hops = 0;
+        while (x != a.source) {
+            const unsigned long long dx = a.D[x];
+            if (dx == kInfNode) {
+                bad = true;
                 break;
-            x = px;
-            if (++hops > a.max_rounds) { // parent pointers not a forest: corrupted state
-                ok = false;
+            }
+            x = node_parent(dx);
+            if (++hops > a.max_rounds) { // parent pointers not a tree: corrupted state
+                set_status(a.g.st, kErrTimeout);
                 break;
             }
         }
-        if (!ok)
-            set_status(a.g.st, kErrTimeout);
-        else
-            a.anc[v] = x;
-        bad = ok && x != a.source;
     }
     if (bad)
         a.D[v] = kInfNode;
@@ -655,11 +656,13 @@ __global__ void __launch_bounds__(256, 5) k_relax_updated(RoundArgs a)
     count_add(g.st, kCtrSeedImproved, improved);
 }
 
-// Ends a call: advances the round stamp past every id used, reports an
-// overflowed frontier.
-__global__ void k_sssp_finish(uint32_t *ctr, DevState *st)
+// Ends a call of the host-driven fallback (the round kernel does this
+// itself): advances the round stamp past every id used (`rounds` rounds),
+// reports an overflowed frontier.
+__global__ void k_sssp_finish(uint32_t *ctr, DevState *st, uint32_t rounds)
 {
-    ctr[kRid] += ctr[kRoundsDone] + 2;
+    ctr[kRoundsDone] = rounds;
+    ctr[kRid] += rounds + 2;
     if (ctr[kOverflow])
         set_status(st, kErrTimeout);
 }
@@ -702,8 +705,6 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
     if (st == MK_OK)
         st = device_alloc(g, (void **)&c->inv, (V + 31) / 32 * 4);
     if (st == MK_OK)
-        st = device_alloc(g, (void **)&c->anc, V * 4);
-    if (st == MK_OK)
         st = device_alloc(g, (void **)&c->counters, 64);
     if (st == MK_OK && (cudaMemset(c->stamp, 0, V * 4) != cudaSuccess || cudaMemset(c->counters, 0, 64) != cudaSuccess))
         st = MK_ERR_CUDA;
@@ -713,7 +714,6 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
         device_free(g, c->front[1], H * 8);
         device_free(g, c->stamp, V * 4);
         device_free(g, c->inv, (V + 31) / 32 * 4);
-        device_free(g, c->anc, V * 4);
         device_free(g, c->counters, 64);
         delete c;
         return st;
@@ -754,8 +754,9 @@ int rounds_block(int units)
 
 namespace {
 
-// Runs every round of one phase.  Input: front[0], size in ctr[kCnt0],
-// ctr[kCnt0 + 1] zero.
+// Runs every round of one phase and the call's epilogue (round stamp,
+// overflow check, a.dist / a.parent written from D).  Input: front[0], size
+// in ctr[kCnt0], ctr[kCnt0 + 1] zero.
 mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
 {
     const int grid = rounds_grid(g->tune.rounds_blocks_per_sm);
@@ -774,8 +775,14 @@ mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
         MK_CUDA(cudaMemcpyAsync(g->h_pinned, a.ctr + kCnt0 + r % 3, 4, cudaMemcpyDeviceToHost, s));
         MK_CUDA(cudaStreamSynchronize(s));
         const uint32_t n = g->h_pinned[0];
-        if (n == 0)
-            return MK_OK;
+        if (n == 0) {
+            return timed(g, "sssp_finish", s, 2, [&]() {
+                k_sssp_finish<<<1, 1, 0, s>>>(a.ctr, g->d_state, r);
+                if (a.dist || a.parent)
+                    k_unpack<<<grid_for(a.g.V, 256), 256, 0, s>>>(a.D, a.g.V, a.dist, a.parent);
+                return cudaSuccess;
+            });
+        }
         MK_TRY(timed(g, name, s, 1, [&]() {
             k_round_once<<<grid_for((uint64_t)n, 256), 256, 0, s>>>(a, r, n);
             return cudaSuccess;
@@ -798,12 +805,13 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     a.ctr = c->counters;
     a.stamp = c->stamp;
     a.inv = c->inv;
-    a.anc = c->anc;
     a.cap = H;
     a.max_hops = g->v.P + 2;
     a.max_rounds = V + 2;
     a.source = source;
     a.unit = kind == kBfs ? 1 : 0;
+    a.dist = d_dist;
+    a.parent = d_parent;
     const bool incremental = c->epoch == g->epoch;
     MK_CUDA(cudaMemsetAsync(c->counters, 0, kClearWords * 4, s));
     MK_CUDA(cudaMemsetAsync(c->counters + kBar, 0, 8, s));
@@ -823,9 +831,8 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
                                                                                                  g->d_state, a);
                 return cudaSuccess;
             }));
-            MK_TRY(timed(g, "sssp_invalidate_jump", s, 2, [&]() {
-                k_inv_anc_init<<<grid_for(V, 256), 256, 0, s>>>(a);
-                k_inv_jump<<<grid_for(V, 256), 256, 0, s>>>(a);
+            MK_TRY(timed(g, "sssp_invalidate_walk", s, 1, [&]() {
+                k_inv_walk<<<grid_for(V, 256), 256, 0, s>>>(a);
                 return cudaSuccess;
             }));
             MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
@@ -848,14 +855,8 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
             }));
         }
     }
-    // common epilogue: rounds until no distance improves
+    // common epilogue: rounds until no distance improves, then the outputs
     MK_TRY(run_phase(g, a, "sssp_rounds", s));
-    MK_TRY(timed(g, "sssp_unpack", s, 2, [&]() {
-        k_sssp_finish<<<1, 1, 0, s>>>(c->counters, g->d_state);
-        if (d_dist || d_parent)
-            k_unpack<<<grid_for(V, 256), 256, 0, s>>>(c->D, V, d_dist, d_parent);
-        return cudaSuccess;
-    }));
     c->epoch = g->epoch;
     c->seq = g->change_seq;
     return MK_OK;
