@@ -215,20 +215,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # profiles/launches_powerlaw_rmat20_b1M.md (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "c7a95fd98b5692ea87578f46e07ca812601e95f5896f123e5b802b17c04abb73"
+NCU_TRAFFIC_SOURCES_SHA = "ad5c461455cd09a5b7326dc23b68699168f433716cc9e46e2f9d540d3bbd79ed"
 NCU_TRAFFIC = {
-    "sssp_rounds": 46955200,
-    "sssp_relax_into_invalid": 281393280,
-    "sssp_enqueue_invalid": 11145984,
-    "sssp_relax_updated": 149820352,
-    "sssp_invalidate": 13741632,
-    "wcc_hook_all": 351127680,
-    "wcc_hook_updated": 139695232,
-    "insert": 241860352,
-    "delete": 199024000,
-    "query": 130466816,
-    "stage_dedup": 40151168,
-    "update_slab_pointers": 60534528,
+    "sssp_rounds": 49301312,
+    "sssp_relax_into_invalid": 281360192,
+    "sssp_enqueue_invalid": 11143744,
+    "sssp_relax_updated": 149819904,
+    "sssp_invalidate_walk": 8524416,
+    "sssp_invalidate": 13743872,
+    "wcc_hook_all": 351103232,
+    "wcc_hook_updated": 139596928,
+    "insert": 241746304,
+    "delete": 198771584,
+    "query": 130690560,
+    "stage_dedup": 40154368,
+    "update_slab_pointers": 60568384,
 }
 
 
