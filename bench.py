@@ -215,21 +215,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # profiles/launches_powerlaw_rmat20_b1M.md (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "ad5c461455cd09a5b7326dc23b68699168f433716cc9e46e2f9d540d3bbd79ed"
+NCU_TRAFFIC_SOURCES_SHA = "552bfb6de3db825a87c4ed7f3948d6e405a38636b7f7e32e7700023b59a47090"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49301312,
-    "sssp_relax_into_invalid": 281360192,
-    "sssp_enqueue_invalid": 11143744,
-    "sssp_relax_updated": 149819904,
-    "sssp_invalidate_walk": 8524416,
-    "sssp_invalidate": 13743872,
-    "wcc_hook_all": 351103232,
-    "wcc_hook_updated": 139596928,
-    "insert": 241746304,
-    "delete": 198771584,
-    "query": 130690560,
-    "stage_dedup": 40154368,
-    "update_slab_pointers": 60568384,
+    "sssp_rounds": 49446528,
+    "sssp_relax_into_invalid": 281274624,
+    "sssp_enqueue_invalid": 11139072,
+    "sssp_relax_updated": 149913216,
+    "sssp_invalidate_walk": 8524096,
+    "sssp_invalidate": 13739968,
+    "wcc_hook_all": 351008128,
+    "wcc_hook_updated": 139749504,
+    "insert": 241921792,
+    "delete": 198795904,
+    "query": 130562048,
+    "stage_dedup": 40166336,
+    "update_slab_pointers": 60561856,
 }
 
 

@@ -48,7 +48,7 @@ enum {
     kClearWords = 8,  // words [0, 8) are cleared at the start of every call
     kSoloR = 6,       // round index reached by a solo phase of block 0
     kRid = 8,         // last round stamp used (kept across calls)
-    kBar = 10         // grid barrier: arrival count, generation
+    kBar = 10         // grid barrier: arrivals of the launch so far
 };
 // A frontier of at most kSoloLists lists is processed by block 0 alone, with
 // block-level barriers between rounds, for at most kSoloRounds rounds in a
@@ -203,30 +203,28 @@ __device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t *cnts, u
     bq_flush(bq, a.front[in ^ 1], cnt, a.cap, (int *)(a.ctr + kOverflow));
 }
 
-// Bounded sense-counting grid barrier for a co-resident (cooperative) grid.
-// Returns false when a wait gave up.
-__device__ bool grid_barrier(uint32_t *bar)
+// Bounded grid barrier for a co-resident (cooperative) grid on one counter
+// that only grows: barrier k of a launch is passed once the counter reaches
+// k * gridDim.x, so a block arrives with one atomicAdd and polls; nothing is
+// reset between barriers (the counter is zeroed before each launch).
+// `passed` is the block's count of barriers so far (thread 0's copy is the
+// one used).  Returns false when the wait gave up.
+__device__ bool grid_barrier(uint32_t *bar, uint32_t &passed)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile uint32_t *gen = bar + 1;
-        const uint32_t g0 = *gen;
+        const uint32_t target = (++passed) * gridDim.x;
         __threadfence();
+        atomicAdd(bar, 1u);
         int ok = 1;
-        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
-            uint32_t spins = 0;
-            while (*gen == g0) {
-                if (++spins > kBarrierSpins) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        uint32_t spins = 0;
+        while ((int)(ld_volatile(bar) - target) < 0) {
+            if (++spins > kBarrierSpins) {
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
         ok_s = ok;
@@ -255,7 +253,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t rid = __ldg(a.ctr + kRid);
     uint32_t *gcnt = a.ctr + kCnt0;
-    uint32_t r = 0, bars = 0;
+    uint32_t r = 0, bars = 0, passed = 0;
     bool ok = true;
     __shared__ uint32_t s_word;
     while (r < a.max_rounds) {
@@ -270,7 +268,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
         if (n > kSoloLists) {
             round_step(a, gcnt, r, n, warp0, nwarps, rid, bq);
             ++bars;
-            if (!grid_barrier(a.ctr + kBar)) {
+            if (!grid_barrier(a.ctr + kBar, passed)) {
                 ok = false;
                 break;
             }
@@ -279,7 +277,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
         }
         // every block has read n: block 0 may now change the global sizes
         bars += 2;
-        if (!grid_barrier(a.ctr + kBar)) {
+        if (!grid_barrier(a.ctr + kBar, passed)) {
             ok = false;
             break;
         }
@@ -307,7 +305,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
                 a.ctr[kSoloR] = r;
             }
         }
-        if (!grid_barrier(a.ctr + kBar)) {
+        if (!grid_barrier(a.ctr + kBar, passed)) {
             ok = false;
             break;
         }
@@ -814,7 +812,7 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     a.parent = d_parent;
     const bool incremental = c->epoch == g->epoch;
     MK_CUDA(cudaMemsetAsync(c->counters, 0, kClearWords * 4, s));
-    MK_CUDA(cudaMemsetAsync(c->counters + kBar, 0, 8, s));
+    MK_CUDA(cudaMemsetAsync(c->counters + kBar, 0, 4, s));
     if (!incremental) {
         MK_TRY(timed(g, "sssp_init", s, 1, [&]() {
             k_sssp_init<<<grid_for(V, 256), 256, 0, s>>>(c->D, V, source, c->front[0], c->counters + kCnt0,
