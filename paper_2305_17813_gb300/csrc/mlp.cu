@@ -2,7 +2,7 @@
 // will gain, so that a rebuilt graph can give it enough buckets up front.
 // The paper fixes bucket counts a priori from the load factor and the
 // current degree (Sec. "Motivation"); this is a project addition on top of
-// that rule, which stays its fallback and its judge.  It may change the
+// that rule, which stays its fallback and its yardstick.  It may change the
 // memory layout (bucket counts) but never a result.
 //
 // Network: 8 inputs -> 64 ReLU -> 64 ReLU -> 1.  Master weights are fp32;
