@@ -68,6 +68,28 @@ def test_algorithmic_bytes_model():
     assert bench.algorithmic_bytes("sssp_rounds", ctr, 1, 1) == 3 * 16 + 128 * 4 + 16 * 50 + 7 * 20
     assert bench.algorithmic_bytes("wcc_hook_all", ctr, 1, 1) == 128 * 9 + 16 * 100
     assert bench.algorithmic_bytes("unknown", ctr, 1, 1) is None
+    # the round kernel also unpacks the tree nodes into dist/parent
+    assert bench.algorithmic_bytes("sssp_rounds", dict(ctr, unpacked=1000), 1, 1) == (
+        3 * 16 + 128 * 4 + 16 * 50 + 7 * 20 + 1000 * 16)
+    dec = {"scan_owners": 40, "scan_slabs": 30, "scan_targets": 20, "scan_improved": 5, "walk_vertices": 64,
+           "invalidated": 6, "seed_lists": 2, "seed_slabs": 3, "seed_edges": 11, "seed_improved": 1}
+    assert bench.algorithmic_bytes("sssp_relax_into_invalid", dec, 1, 1) == 4 * 40 + 136 * 30 + 16 * 20
+    assert bench.algorithmic_bytes("sssp_enqueue_invalid", dec, 1, 1) == 5 * 28
+    assert bench.algorithmic_bytes("sssp_invalidate_walk", dec, 1, 1) == 64 * 8 + 6 * 8
+    assert bench.algorithmic_bytes("sssp_relax_updated", dec, 1, 1) == 2 * 20 + 128 * 3 + 16 * 11 + 1 * 20
+
+
+def test_every_traffic_family_has_a_byte_model_or_is_staging():
+    import bench
+
+    ctr = {name: 1 for name in ["query_slabs", "insert_slabs", "insert_new_slabs", "delete_slabs", "relax_lists",
+                                "relax_slabs", "relax_edges", "relax_improved", "invalidated", "wcc_slabs",
+                                "wcc_edges", "seed_lists", "seed_slabs", "seed_edges", "seed_improved",
+                                "wcc_upd_slabs", "wcc_upd_edges", "scan_owners", "scan_slabs", "scan_targets",
+                                "scan_improved", "walk_vertices", "unpacked"]}
+    without_model = {f for f in bench.NCU_TRAFFIC if bench.algorithmic_bytes(f, ctr, 1, 1) is None}
+    # staging, the change-log seeds and the commit are not roofline families
+    assert without_model <= {"stage_dedup", "sssp_invalidate", "update_slab_pointers"}
 
 
 def test_traffic_reported_only_for_unchanged_kernel_sources(monkeypatch):
