@@ -10,6 +10,12 @@ pass of the whole path on one batch size B (default 2^20):
     vertex) and WCC -> commit -> delete B live edges -> BFS, SSSP (decremental)
     and WCC (static recompute) -> commit -> query B edges (half present)
 
+WCC and the query batch only read the graph, as BFS and SSSP do: they run
+on a second stream (default priority) forked after each update batch and
+joined before the next change, beside BFS/SSSP on the main stream (high
+priority); the step's phases are timed on the main stream and the second
+stream's calls by their own events.
+
 value = 3B edges (inserted + deleted + queried) / step time, in Medges/s,
 with inputs resident in device memory; `e2e` is the same through the C-ABI
 with the inputs copied from pinned host buffers and the results (flags,
