@@ -4,11 +4,18 @@
 Workload (R-MAT scale 20: V = 1,048,576, 16,777,216 draws with a/b/c/d =
 0.57/0.19/0.19/0.05, duplicates and self-loops dropped, weights U[1,100];
 buckets from the load-factor rule with load factor 0.7).  One step is one
-pass of the whole path on one batch size B (default 2^20):
+pass of the whole path on one batch of size B (default 2^20):
 
     insert B new R-MAT edges -> incremental BFS, SSSP (from the max-degree
     vertex) and WCC -> commit -> delete B live edges -> BFS, SSSP (decremental)
     and WCC (static recompute) -> commit -> query B edges (half present)
+
+The batches come from synth.PowerlawStream, which draws every delete from
+the edges live at that point and exactly half of the queries from the live
+edges; after the timed region every timed step is checked from the kernels'
+own flags and bitmaps (all deletes applied, exactly B // 2 queries present,
+the inserts the stream expects), and the run stops without a value if one
+is off.
 
 WCC and the query batch only read the graph, as BFS and SSSP do: they run
 on a second stream (default priority) forked after each update batch and
@@ -18,14 +25,18 @@ stream's calls by their own events.
 
 value = 3B edges (inserted + deleted + queried) / step time, in Medges/s,
 with inputs resident in device memory; `e2e` is the same through the C-ABI
-with the inputs copied from pinned host buffers and the results (flags,
-bitmap, SSSP distances) copied back inside the timed region.  L2 is flushed
-between steps by writing a 512 MiB buffer.
+with the inputs copied from pinned host buffers and every result (flags,
+bitmap, BFS/SSSP distances and parents, WCC labels) copied back inside the
+timed region.  L2 is flushed between steps by writing a 512 MiB buffer.
+After them come three steps with every call on one stream (`kernels_solo`:
+each kernel family's own GB/s and fraction of the measured copy bandwidth)
+and steps at the workload's other batch sizes 2^12, 2^16 and 2^22
+(`per_batch`), continuing the same stream of batches.
 
 `--impl reference` times the CPU oracle (plain single-threaded C++,
-recomputing everything from scratch) on the same workload and metric.
-Under torchrun each rank runs an independent replica (weak scaling); rank 0
-prints one JSON line.
+recomputing everything from scratch) on the same workload and metric, every
+part of every step executed (see OracleStep).  Under torchrun each rank runs
+an independent replica (weak scaling); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -36,6 +47,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -60,6 +72,9 @@ def parse_args(argv=None):
     p.add_argument("--draws", type=int, default=1 << 24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-solo", action="store_true", help="skip the steps that time every kernel alone")
+    p.add_argument("--no-per-batch", action="store_true",
+                   help="skip the steps at the workload's other batch sizes (2^12, 2^16, 2^22)")
     p.add_argument("--workload", choices=["powerlaw", "growth", "served", "road"], default="powerlaw",
                    help="powerlaw: the benchmark line; growth: the learned-sizing study on the R-MAT "
                         "scale-22 growth stream; served: plain vs continuous-batching serving on the R-MAT "
@@ -107,15 +122,15 @@ def barrier(dist, device=None):
 
 # -------------------------------------------------------------- workload
 
-def make_workload(args, n_batches):
+def make_workload(args, max_batch):
+    """The R-MAT graph, the BFS/SSSP source (largest out-degree, ties to the
+    smallest id) and the batch stream (synth.PowerlawStream)."""
     import synth
 
-    t0 = time.time()
     G = synth.powerlaw_graph(scale=args.scale, draws=args.draws)
     deg = np.bincount(G.src, minlength=G.V)
     source = int(np.argmax(deg))
-    batches = [synth.powerlaw_batch(G, k, args.batch) for k in range(n_batches)]
-    return G, source, batches, time.time() - t0
+    return G, source, synth.PowerlawStream(G, max_batch=max_batch)
 
 
 def workload_config(args, G):
@@ -128,6 +143,7 @@ def workload_config(args, G):
         "batch": args.batch,
         "buckets": "load-factor rule, load factor 0.7",
         "l2": "flushed between timed steps (512 MiB write)",
+        "batches": "deletes drawn from the edges live at the delete, queries exactly half live (checked per step)",
         "parallelism": "independent replica per GPU",
     }
 
@@ -217,8 +233,8 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# kernel families, from the ncu launch list of this benchmark summarised in
-# profiles/launches_powerlaw_rmat20_b1M.md (full workload, one pass), and
+# kernel families, from the committed ncu launch list of this benchmark
+# (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
 NCU_TRAFFIC_SOURCES_SHA = "7c40a5cb5cbb9d2ac94b78f631250ad2c8dc2c74747ed419265b0b6764bb4f3a"
@@ -268,84 +284,79 @@ def measured_peak():
 
 # ----------------------------------------------------------------- GPU arm
 
-def run_ours(args, world, rank, local):
-    import torch
+class StepRunner:
+    """One device graph of the power-law workload and the step that the
+    benchmark times (see the module docstring), with per-step output buffers
+    so that every timed step can be checked afterwards."""
 
-    import paper_2305_17813_gb300 as mk
+    def __init__(self, args, G, source, capacity_edges, device):
+        import torch
 
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    dist = dist_init(world, True)
-    lib = mk.load()
-    W, K, B = args.warmup, args.steps, args.batch
-    n_e2e = 0 if args.no_e2e else K
-    G, source, batches, gen_s = make_workload(args, W + K + n_e2e)
-    V, E = G.V, len(G.src)
-    # the step runs on a high-priority stream; WCC, which only reads the
-    # graph, runs beside it on a default-priority stream (see step())
-    stream = torch.cuda.Stream(device=device, priority=-1)
-    torch.cuda.set_stream(stream)
-    sp = ctypes.c_void_p(stream.cuda_stream)
+        import paper_2305_17813_gb300 as mk
 
-    def u32(a):
-        return mk.to_device_u32(a, device)
+        self.mk, self.torch, self.device = mk, torch, device
+        self.lib = lib = mk.load()
+        self.V, self.source = G.V, source
+        # the step runs on a high-priority stream; the calls that only read
+        # the graph (WCC, the query batch) run beside it on a second stream
+        self.stream = torch.cuda.Stream(device=device, priority=-1)
+        torch.cuda.set_stream(self.stream)
+        self.sp = ctypes.c_void_p(self.stream.cuda_stream)
+        self.side = torch.cuda.Stream(device=device)
+        self.sidep = ctypes.c_void_p(self.side.cuda_stream)
+        E = len(G.src)
+        src_d = self.u32(G.src)
+        buckets = mk.bucket_rule(G.V, src_d, 0.7)
+        self.g = mk.Graph(G.V, edge_capacity_hint=capacity_edges, buckets=buckets)
+        self.h = self.g.handle
+        chunk = 1 << 22
+        dst_d, w_d = self.u32(G.dst), self.u32(G.w)
+        for i in range(0, E, chunk):
+            mk.check(lib.mk_insert_batch(self.h, self.P(src_d[i:i + chunk]), self.P(dst_d[i:i + chunk]),
+                                         self.P(w_d[i:i + chunk]), min(chunk, E - i), None, self.sp), "load")
+        del src_d, dst_d, w_d
+        self.g.commit()
+        self.out = {k: torch.empty(G.V, dtype=torch.int32, device=device) for k in ("bd", "bp", "sd", "sp", "lab")}
+        P = self.P
+        for fn, a, b in ((lib.mk_incr_bfs, "bd", "bp"), (lib.mk_incr_sssp, "sd", "sp")):
+            mk.check(fn(self.h, source, P(self.out[a]), P(self.out[b]), self.sp), "static")
+        mk.check(lib.mk_incr_wcc(self.h, P(self.out["lab"]), self.sp), "static wcc")
+        self.g.commit()
+        torch.cuda.synchronize()
+        st = self.g.last_error()
+        if st != mk.MK_OK:
+            raise RuntimeError("device status %d after the load" % st)
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
 
-    src_d = u32(G.src)
-    buckets = mk.bucket_rule(V, src_d, 0.7)
-    g = mk.Graph(V, edge_capacity_hint=E + (W + K + n_e2e + 2) * B, buckets=buckets)
-    h = g.handle
-    chunk = 1 << 22
-    dst_d, w_d = u32(G.dst), u32(G.w)
-    for i in range(0, E, chunk):
-        mk.check(lib.mk_insert_batch(h, ctypes.c_void_p(src_d[i:i + chunk].data_ptr()),
-                                     ctypes.c_void_p(dst_d[i:i + chunk].data_ptr()),
-                                     ctypes.c_void_p(w_d[i:i + chunk].data_ptr()), min(chunk, E - i), None, sp),
-                 "load")
-    del src_d, dst_d, w_d
-    g.commit()
-    out = {k: torch.empty(V, dtype=torch.int32, device=device) for k in
-           ("bd", "bp", "sd", "sp", "lab")}
-    fl_i = torch.empty(B, dtype=torch.uint8, device=device)
-    fl_d = torch.empty(B, dtype=torch.uint8, device=device)
-    bm = torch.empty((B + 31) // 32, dtype=torch.int32, device=device)
-    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
-    for fn, a, b in ((lib.mk_incr_bfs, "bd", "bp"), (lib.mk_incr_sssp, "sd", "sp")):
-        mk.check(fn(h, source, P(out[a]), P(out[b]), sp), "static")
-    mk.check(lib.mk_incr_wcc(h, P(out["lab"]), sp), "static wcc")
-    g.commit()
-    torch.cuda.synchronize()
-    st = g.last_error()
-    if st != mk.MK_OK:
-        raise RuntimeError("device status %d after the load" % st)
+    def u32(self, a):
+        return self.mk.to_device_u32(a, self.device)
 
-    # X2 autotuner: kernel shapes for this graph (untimed setup)
-    tb = batches[0]
-    tuning = g.autotune(tb["q_src"], tb["q_dst"], source)
-    g.commit()
-    dev_batches = []
-    for bt in batches[:W + K]:
-        dev_batches.append({k: u32(bt[k]) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst",
-                                                     "q_src", "q_dst")})
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
-    # phases on the main stream; wcc1_wait / wcc2_wait / query_wait are what
-    # is left of the calls on the second stream after BFS and SSSP (the
-    # joins); their own durations come from events on that stream
-    names = ["insert", "bfs1", "sssp1", "wcc1_wait", "commit1", "delete", "bfs2", "sssp2", "wcc2_wait", "commit2",
-             "query_wait"]
+    @staticmethod
+    def P(t):
+        return ctypes.c_void_p(t.data_ptr())
 
-    # WCC only reads the graph, as BFS and SSSP do: it runs on a second
-    # stream, forked after each update batch and joined before the commit,
-    # so its kernels overlap the BFS/SSSP kernels (a user of the library
-    # can do the same: calls on one graph may overlap when none of them
-    # changes it).
-    ws = torch.cuda.Stream(device=device)
-    wsp = ctypes.c_void_p(ws.cuda_stream)
+    def to_device(self, bt):
+        return {k: self.u32(bt[k]) for k in BATCH_KEYS}
 
-    def step(bt, ev, hooks=None, wev=None):
+    def outputs(self, n, steps):
+        """Per-step flag and bitmap buffers (insert flags, delete flags,
+        query bitmap) for `steps` steps of batch size n."""
+        torch = self.torch
+        return [(torch.empty(n, dtype=torch.uint8, device=self.device),
+                 torch.empty(n, dtype=torch.uint8, device=self.device),
+                 torch.empty((n + 31) // 32, dtype=torch.int32, device=self.device)) for _ in range(steps)]
+
+    def step(self, bt, n, outs, ev, wev, hooks=None, solo=False):
+        """One step on batch bt (device tensors) of size n.  ev: 12 events
+        on the main stream, wev: 5 on the second stream.  solo=True runs
+        every call on the main stream (no overlap)."""
+        mk, lib, P, h, out, src = self.mk, self.lib, self.P, self.h, self.out, self.source
+        stream, sp = self.stream, self.sp
+        ws, wsp = (stream, sp) if solo else (self.side, self.sidep)
+        fl_i, fl_d, bm = outs
         hooks = hooks or {}
-        wev = wev or [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record(stream)
-        mk.check(lib.mk_insert_batch(h, P(bt["ins_src"]), P(bt["ins_dst"]), P(bt["ins_w"]), B, P(fl_i), sp), "ins")
+        mk.check(lib.mk_insert_batch(h, P(bt["ins_src"]), P(bt["ins_dst"]), P(bt["ins_w"]), n, P(fl_i), sp), "ins")
         ev[1].record(stream)
         if "after_insert" in hooks:
             hooks["after_insert"]()
@@ -353,9 +364,9 @@ def run_ours(args, world, rank, local):
         wev[0].record(ws)
         mk.check(lib.mk_incr_wcc(h, P(out["lab"]), wsp), "wcc")
         wev[1].record(ws)
-        mk.check(lib.mk_incr_bfs(h, source, P(out["bd"]), P(out["bp"]), sp), "bfs")
+        mk.check(lib.mk_incr_bfs(h, src, P(out["bd"]), P(out["bp"]), sp), "bfs")
         ev[2].record(stream)
-        mk.check(lib.mk_incr_sssp(h, source, P(out["sd"]), P(out["sp"]), sp), "sssp")
+        mk.check(lib.mk_incr_sssp(h, src, P(out["sd"]), P(out["sp"]), sp), "sssp")
         ev[3].record(stream)
         stream.wait_event(wev[1])
         ev[4].record(stream)
@@ -363,7 +374,7 @@ def run_ours(args, world, rank, local):
         ev[5].record(stream)
         if "before_delete" in hooks:
             hooks["before_delete"]()
-        mk.check(lib.mk_delete_batch(h, P(bt["del_src"]), P(bt["del_dst"]), B, P(fl_d), sp), "del")
+        mk.check(lib.mk_delete_batch(h, P(bt["del_src"]), P(bt["del_dst"]), n, P(fl_d), sp), "del")
         ev[6].record(stream)
         ws.wait_event(ev[6])
         wev[2].record(ws)
@@ -371,11 +382,11 @@ def run_ours(args, world, rank, local):
         wev[3].record(ws)
         # the query batch only reads the graph too: after the delete, beside
         # the decremental BFS/SSSP (a commit moves only update markers)
-        mk.check(lib.mk_query_batch(h, P(bt["q_src"]), P(bt["q_dst"]), B, P(bm), None, wsp), "query")
+        mk.check(lib.mk_query_batch(h, P(bt["q_src"]), P(bt["q_dst"]), n, P(bm), None, wsp), "query")
         wev[4].record(ws)
-        mk.check(lib.mk_incr_bfs(h, source, P(out["bd"]), P(out["bp"]), sp), "bfs")
+        mk.check(lib.mk_incr_bfs(h, src, P(out["bd"]), P(out["bp"]), sp), "bfs")
         ev[7].record(stream)
-        mk.check(lib.mk_incr_sssp(h, source, P(out["sd"]), P(out["sp"]), sp), "sssp")
+        mk.check(lib.mk_incr_sssp(h, src, P(out["sd"]), P(out["sp"]), sp), "sssp")
         ev[8].record(stream)
         stream.wait_event(wev[3])
         ev[9].record(stream)
@@ -384,159 +395,317 @@ def run_ours(args, world, rank, local):
         stream.wait_event(wev[4])
         ev[11].record(stream)
 
-    def events():
-        return [torch.cuda.Event(enable_timing=True) for _ in range(12)]
+    def events(self, n):
+        return [self.torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
-    for k in range(W):
-        flush.fill_(k)
-        torch.cuda.nvtx.range_push("step")  # lets a profiler select the steps' kernels
-        step(dev_batches[k], events())
-        torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    if g.last_error() != mk.MK_OK:
-        raise RuntimeError("device status after warm-up")
-    g.counters(reset=True)
-    g.profile(True)
-    launches0 = g.launch_count()
-    evs = [events() for _ in range(K)]
-    wevs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
-    clock = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
-                         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
-    barrier(dist, device)
-    torch.cuda.synchronize()
-    wall0 = time.time()
-    with clock:
-        for k in range(K):
-            flush.fill_(k + 1)
-            torch.cuda.nvtx.range_push("step")
-            step(dev_batches[W + k], evs[k], wev=wevs[k])
+    def run(self, batches, n, warmup, flush_tag, solo=False, clock=None, dist=None):
+        """Warm-up steps, then the timed steps, each on its own batch; returns
+        the timing record and the per-step outputs of the timed steps."""
+        torch, mk, g = self.torch, self.mk, self.g
+        dev = [self.to_device(bt) for bt in batches]
+        warm_outs = self.outputs(n, 1)[0]
+        for k in range(warmup):
+            self.flush.fill_(flush_tag + k)
+            torch.cuda.nvtx.range_push("step")  # lets a profiler select the steps' kernels
+            self.step(dev[k], n, warm_outs, self.events(12), self.events(5), solo=solo)
             torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-    wall = time.time() - wall0
-    barrier(dist, device)
-    launches = g.launch_count() - launches0
-    prof = g.profile_read()
-    g.profile(False)
-    ctr = g.counters()
-    status = g.last_error()
-    if status != mk.MK_OK:
-        raise RuntimeError("device status %d in the timed region" % status)
-    step_ms = [evs[k][0].elapsed_time(evs[k][11]) for k in range(K)]
-    phase = {n: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
-             for i, n in enumerate(names)}
-    wcc_incr = statistics.mean(wevs[k][0].elapsed_time(wevs[k][1]) for k in range(K))
-    wcc_static = statistics.mean(wevs[k][2].elapsed_time(wevs[k][3]) for k in range(K))
-    query_ms = statistics.mean(wevs[k][3].elapsed_time(wevs[k][4]) for k in range(K))
-    local_ms = statistics.mean(step_ms)
-    ms_max, = reduce_across([local_ms], "max", dist, device)
+        if g.last_error() != mk.MK_OK:
+            raise RuntimeError("device status after warm-up")
+        K = len(batches) - warmup
+        outs = self.outputs(n, K)
+        evs = [self.events(12) for _ in range(K)]
+        wevs = [self.events(5) for _ in range(K)]
+        g.counters(reset=True)
+        g.profile(True)
+        g.profile_read()
+        launches0 = g.launch_count()
+        barrier(dist, self.device)
+        torch.cuda.synchronize()
+        wall0 = time.time()
+        with (clock if clock is not None else _Null()):
+            for k in range(K):
+                self.flush.fill_(flush_tag + warmup + k)
+                torch.cuda.nvtx.range_push("step")
+                self.step(dev[warmup + k], n, outs[k], evs[k], wevs[k], solo=solo)
+                torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+        wall = time.time() - wall0
+        barrier(dist, self.device)
+        launches = g.launch_count() - launches0
+        prof = g.profile_read()
+        g.profile(False)
+        ctr = g.counters()
+        status = g.last_error()
+        if status != mk.MK_OK:
+            raise RuntimeError("device status %d in the timed region" % status)
+        names = ["insert", "bfs1", "sssp1", "wcc1_wait", "commit1", "delete", "bfs2", "sssp2", "wcc2_wait",
+                 "commit2", "query_wait"]
+        rec = {
+            "step_ms": [evs[k][0].elapsed_time(evs[k][11]) for k in range(K)],
+            "phase": {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
+                      for i, nm in enumerate(names)},
+            "wcc_incr": statistics.mean(wevs[k][0].elapsed_time(wevs[k][1]) for k in range(K)),
+            "wcc_static": statistics.mean(wevs[k][2].elapsed_time(wevs[k][3]) for k in range(K)),
+            "query_ms": statistics.mean(wevs[k][3].elapsed_time(wevs[k][4]) for k in range(K)),
+            "prof": prof, "ctr": ctr, "launches": int(launches), "wall": wall, "K": K,
+        }
+        return rec, outs, batches[warmup:]
+
+    def close(self):
+        self.g.close()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+BATCH_KEYS = ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst", "q_src", "q_dst")
+
+
+def check_steps(outs, batches, n):
+    """The workload check of every timed step, from the kernels' own
+    outputs: each insert flagged exactly the edges that the stream added to
+    its live set, each delete removed all n edges, and exactly n // 2
+    queries were present.  Raises when a step was not a step of the
+    workload (no value is printed then)."""
+    ins, dele, qry = [], [], []
+    for (fl_i, fl_d, bm), bt in zip(outs, batches):
+        ni = int(fl_i.sum().item())
+        nd = int(fl_d.sum().item())
+        words = bm.cpu().numpy().view(np.uint32)
+        nq = int(np.unpackbits(words.view(np.uint8)).sum())
+        if ni != bt["n_inserted"] or nd != n or nq != bt["n_present"]:
+            raise RuntimeError("batch %d is off the workload: %d inserted (stream: %d), %d of %d deleted, "
+                               "%d of %d queries present (stream: %d)"
+                               % (bt["k"], ni, bt["n_inserted"], nd, n, nq, n, bt["n_present"]))
+        ins.append(ni / n)
+        dele.append(nd / n)
+        qry.append(nq / n)
+    return {"steps_checked": len(outs), "batches": [int(bt["k"]) for bt in batches],
+            "insert_applied_frac": [round(min(ins), 4), round(max(ins), 4)],
+            "delete_applied_frac": [round(min(dele), 4), round(max(dele), 4)],
+            "query_present_frac": [round(min(qry), 4), round(max(qry), 4)],
+            "rule": "every delete removes a live edge and exactly half the queries are present, checked from "
+                    "the kernels' flags and bitmaps of every timed step"}
+
+
+def family_table(prof, ctr, n, peak):
+    """Per kernel family: launches, summed CUDA-event ms, share of the summed
+    time, and (where a byte model exists) achieved GB/s and its fraction of
+    the measured copy bandwidth."""
+    fam_time = {name: t for name, (m, t) in prof.items()}
+    fam_launch = {name: m for name, (m, t) in prof.items()}
+    total = sum(fam_time.values()) or 1.0
+    out = {}
+    for name in sorted(fam_time, key=fam_time.get, reverse=True):
+        bt = algorithmic_bytes(name, ctr, n, fam_launch[name])
+        out[name] = {"launches": fam_launch[name], "ms": round(fam_time[name], 3),
+                     "share": round(fam_time[name] / total, 4)}
+        if bt is not None and fam_time[name] > 0:
+            gbs = bt / (fam_time[name] / 1e3) / 1e9
+            out[name]["gbs"] = round(gbs, 1)
+            out[name]["frac"] = round(gbs / peak, 4)
+    return out
+
+
+def summarize(rec, n, peak, units_factor=3.0):
+    ph = rec["phase"]
+    ms = statistics.mean(rec["step_ms"])
+    return {
+        "value": round(units_factor * n / (ms / 1e3) / 1e6, 2), "ms_per_step": round(ms, 3),
+        "insert_medges_s": round(n / ph["insert"] / 1e3, 1),
+        "delete_medges_s": round(n / ph["delete"] / 1e3, 1),
+        "query_medges_s": round(n / rec["query_ms"] / 1e3, 1),
+        "incr_sssp_ms": round(ph["sssp1"], 3), "decr_sssp_ms": round(ph["sssp2"], 3),
+        "incr_bfs_ms": round(ph["bfs1"], 3), "decr_bfs_ms": round(ph["bfs2"], 3),
+        "incr_wcc_ms": round(rec["wcc_incr"], 3), "static_wcc_ms": round(rec["wcc_static"], 3),
+    }
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    W, K, B = args.warmup, args.steps, args.batch
+    n_e2e = 0 if args.no_e2e else K
+    n_solo = 0 if args.no_solo else 3
+    per_batch = [] if args.no_per_batch else [b for b in PER_BATCH if b != B]
+    t0 = time.time()
+    G, source, S = make_workload(args, max([B] + per_batch))
+    main_batches = [S.batch(B) for _ in range(W + K + n_e2e + n_solo)]
+    gen_s = time.time() - t0
+    V, E = G.V, len(G.src)
+    inserted_total = B * len(main_batches) + sum(pb * (PB_WARMUP + pb_steps(pb)) for pb in per_batch)
+    R = StepRunner(args, G, source, E + inserted_total, device)
+    mk, lib, g = R.mk, R.lib, R.g
+
+    # X2 autotuner: kernel shapes for this graph (untimed setup)
+    tb = main_batches[0]
+    tuning = g.autotune(tb["q_src"], tb["q_dst"], source)
+    g.commit()
+
+    peak, peak_kind = measured_peak()
+    clock = ClockSampler(os.path.join(tempfile.gettempdir(), "bench_clocks_rank%d_%d.csv" % (rank, os.getpid())))
+    rec, outs, timed = R.run(main_batches[:W + K], B, W, flush_tag=0, clock=clock, dist=dist)
+    checks = check_steps(outs, timed, B)
+    del outs
+    main = summarize(rec, B, peak)
+    ms_max, = reduce_across([statistics.mean(rec["step_ms"])], "max", dist, device)
     units_total, = reduce_across([3.0 * B], "sum", dist, device)
     value = units_total / (ms_max / 1e3) / 1e6
 
-    # roofline: kernel family with the largest share of the timed region
-    fam_time = {name: t for name, (n, t) in prof.items()}
-    fam_launch = {name: n for name, (n, t) in prof.items()}
-    dom = max(fam_time, key=fam_time.get)
-    per_launch_n = B
-    bytes_total = algorithmic_bytes(dom, ctr, per_launch_n, fam_launch[dom])
-    peak, peak_kind = measured_peak()
+    prof, ctr = rec["prof"], rec["ctr"]
+    kernels = family_table(prof, ctr, B, peak)
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
     roof = None
-    if bytes_total is not None and fam_time[dom] > 0:
-        per_launch_bytes = bytes_total / fam_launch[dom]
-        avg_ms = fam_time[dom] / fam_launch[dom]
+    bytes_total = algorithmic_bytes(dom, ctr, B, kernels[dom]["launches"])
+    if bytes_total is not None and kernels[dom]["ms"] > 0:
+        nl = kernels[dom]["launches"]
+        per_launch_bytes = bytes_total / nl
+        avg_ms = kernels[dom]["ms"] / nl
         achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": ncu_traffic(dom),
                 "algorithmic_bytes_per_launch": int(per_launch_bytes), "avg_launch_ms": round(avg_ms, 4),
-                "launches": fam_launch[dom]}
-    # every family's share and achieved bandwidth, for the record
-    kernels = {}
-    total_prof = sum(fam_time.values()) or 1.0
-    for name in sorted(fam_time, key=fam_time.get, reverse=True):
-        bt = algorithmic_bytes(name, ctr, B, fam_launch[name])
-        kernels[name] = {"launches": fam_launch[name], "ms": round(fam_time[name], 3),
-                         "share": round(fam_time[name] / total_prof, 4)}
-        if bt is not None and fam_time[name] > 0:
-            kernels[name]["gbs"] = round(bt / (fam_time[name] / 1e3) / 1e9, 1)
+                "launches": nl}
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic", "config": workload_config(args, G),
-        "insert_medges_s": round(B / phase["insert"] / 1e3, 1),
-        "delete_medges_s": round(B / phase["delete"] / 1e3, 1),
-        "query_medges_s": round(B / query_ms / 1e3, 1),
-        "incr_sssp_ms": round(phase["sssp1"], 3), "decr_sssp_ms": round(phase["sssp2"], 3),
-        "incr_bfs_ms": round(phase["bfs1"], 3), "decr_bfs_ms": round(phase["bfs2"], 3),
-        "incr_wcc_ms": round(wcc_incr, 3), "static_wcc_ms": round(wcc_static, 3),
+        **{k: v for k, v in main.items() if k not in ("value", "ms_per_step")},
         "wcc_overlap": "WCC and the query batch run on a second stream beside BFS/SSSP; their ms and rates are "
                        "their own durations there",
-        "phases_ms": {k: round(v, 3) for k, v in phase.items()},
+        "phases_ms": {k: round(v, 3) for k, v in rec["phase"].items()},
+        "workload_check": checks,
         "roofline": roof, "kernels": kernels, "counters": ctr,
-        "gpu_launches": int(launches), "wall_s_timed": round(wall, 3), "gen_s": round(gen_s, 1),
+        "gpu_launches": rec["launches"], "wall_s_timed": round(rec["wall"], 3), "gen_s": round(gen_s, 1),
         "tuning": {k: tuning[k] for k in ("query_group", "query_block", "rounds_blocks_per_sm")},
         "clocks": clock.summary(local),
     }
+    at = W + K
 
     # end to end through the C ABI with host buffers
     if n_e2e:
-        host = []
-        for bt in batches[W + K:W + K + n_e2e]:
-            host.append({k: torch.from_numpy(np.ascontiguousarray(bt[k]).view(np.int32)).pin_memory()
-                         for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst", "q_src", "q_dst")})
-        stage = {k: torch.empty(B, dtype=torch.int32, device=device) for k in host[0]}
-        h_fl_i = torch.empty(B, dtype=torch.uint8).pin_memory()
-        h_fl_d = torch.empty(B, dtype=torch.uint8).pin_memory()
-        h_bm = torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory()
-        h_sd = torch.empty(V, dtype=torch.int32).pin_memory()
-        h_spar = torch.empty(V, dtype=torch.int32).pin_memory()
-        # Every step copies its inputs in and its results out inside the timed
-        # region; the copies that later phases need overlap the earlier
-        # phases on a second stream: the delete and query inputs come in
-        # while the insert and the algorithms run, and the insert flags go
-        # out while the algorithms run.
-        copy = torch.cuda.Stream(device=device)
-        e2e_ms = []
-        for k in range(n_e2e):
-            flush.fill_(100 + k)
-            e = events()
-            torch.cuda.synchronize()
-            e[0].record(stream)
-            for key in ("ins_src", "ins_dst", "ins_w"):
+        result["e2e"] = run_e2e(R, main_batches[at:at + n_e2e], B, dist, units_total)
+        at += n_e2e
+
+    # every kernel family timed alone: the same step with every call on the
+    # main stream, so that no family shares the GPU with another
+    if n_solo:
+        srec, souts, stimed = R.run(main_batches[at:at + n_solo], B, 0, flush_tag=500, solo=True)
+        check_steps(souts, stimed, B)
+        del souts
+        sk = family_table(srec["prof"], srec["ctr"], B, peak)
+        result["kernels_solo"] = {"steps": n_solo, "ms_per_step": round(statistics.mean(srec["step_ms"]), 3),
+                                  "peak": peak, "families": sk}
+        at += n_solo
+
+    # the other batch sizes of the workload, continuing the same stream
+    if per_batch:
+        pbr = {str(B): {**main, "steps": K, "warmup": W,
+                        "o_e_share": o_e_share(kernels)}}
+        for pb in per_batch:
+            nW, nK = PB_WARMUP, pb_steps(pb)
+            bts = [S.batch(pb) for _ in range(nW + nK)]
+            prec, pouts, ptimed = R.run(bts, pb, nW, flush_tag=1000 + pb % 997)
+            pchk = check_steps(pouts, ptimed, pb)
+            del pouts
+            pk = family_table(prec["prof"], prec["ctr"], pb, peak)
+            pbr[str(pb)] = {**summarize(prec, pb, peak), "steps": nK, "warmup": nW,
+                            "batches": pchk["batches"], "o_e_share": o_e_share(pk),
+                            "top_kernels": {k: pk[k] for k in list(pk)[:5]}}
+        result["per_batch"] = pbr
+    R.close()
+    return result, dist, G, source, main_batches
+
+
+PER_BATCH = (1 << 12, 1 << 16, 1 << 20, 1 << 22)
+PB_WARMUP = 3
+
+
+def pb_steps(pb):
+    return 3 if pb >= 1 << 22 else 5
+
+
+def o_e_share(kernels):
+    """Share of the summed kernel time taken by the passes over every edge
+    (the decremental relax-into-invalid scan and the static WCC pass), which
+    do not shrink with the batch."""
+    return round(sum(kernels[k]["share"] for k in ("sssp_relax_into_invalid", "wcc_hook_all", "wcc_init")
+                     if k in kernels), 4)
+
+
+def run_e2e(R, batches, B, dist, units_total):
+    """Steps through the C ABI with the inputs in pinned host memory: every
+    step copies its inputs in and its results out inside the timed region
+    (insert and delete flags, the query bitmap, BFS and SSSP distances and
+    parents, WCC labels); the copies that later phases need overlap the
+    earlier phases on a copy stream."""
+    torch, mk = R.torch, R.mk
+    device, stream, V = R.device, R.stream, R.V
+    host = [{k: torch.from_numpy(np.ascontiguousarray(bt[k]).view(np.int32)).pin_memory() for k in BATCH_KEYS}
+            for bt in batches]
+    stage = {k: torch.empty(B, dtype=torch.int32, device=device) for k in BATCH_KEYS}
+    outs = R.outputs(B, 1)[0]
+    fl_i, fl_d, bm = outs
+    h_fl_i = torch.empty(B, dtype=torch.uint8).pin_memory()
+    h_fl_d = torch.empty(B, dtype=torch.uint8).pin_memory()
+    h_bm = torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory()
+    h_res = {k: torch.empty(V, dtype=torch.int32).pin_memory() for k in R.out}
+    copy = torch.cuda.Stream(device=device)
+    e2e_ms = []
+    for k in range(len(batches)):
+        R.flush.fill_(100 + k)
+        e = R.events(14)
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for key in ("ins_src", "ins_dst", "ins_w"):
+            stage[key].copy_(host[k][key], non_blocking=True)
+        copy.wait_event(e[0])
+        ready = torch.cuda.Event()
+        with torch.cuda.stream(copy):
+            for key in ("del_src", "del_dst", "q_src", "q_dst"):
                 stage[key].copy_(host[k][key], non_blocking=True)
-            copy.wait_event(e[0])
-            ready = torch.cuda.Event()
+            ready.record(copy)
+        inserted = torch.cuda.Event()
+
+        def after_insert():
+            inserted.record(stream)
+            copy.wait_event(inserted)
             with torch.cuda.stream(copy):
-                for key in ("del_src", "del_dst", "q_src", "q_dst"):
-                    stage[key].copy_(host[k][key], non_blocking=True)
-                ready.record(copy)
-            inserted = torch.cuda.Event()
+                h_fl_i.copy_(fl_i, non_blocking=True)
 
-            def after_insert():
-                inserted.record(stream)
-                copy.wait_event(inserted)
-                with torch.cuda.stream(copy):
-                    h_fl_i.copy_(fl_i, non_blocking=True)
-
-            step(stage, e[1:] + [torch.cuda.Event(enable_timing=True)],
-                 {"after_insert": after_insert, "before_delete": lambda: stream.wait_event(ready)})
-            h_fl_d.copy_(fl_d, non_blocking=True)
-            h_bm.copy_(bm, non_blocking=True)
-            h_sd.copy_(out["sd"], non_blocking=True)
-            h_spar.copy_(out["sp"], non_blocking=True)
-            stream.wait_stream(copy)
-            e[11].record(stream)
-            torch.cuda.synchronize()
-            e2e_ms.append(e[0].elapsed_time(e[11]))
-        if g.last_error() != mk.MK_OK:
-            raise RuntimeError("device status in the e2e pass")
-        e2e_local = statistics.mean(e2e_ms)
-        e2e_max, = reduce_across([e2e_local], "max", dist, device)
-        result["e2e"] = {"value": round(units_total / (e2e_max / 1e3) / 1e6, 2), "unit": UNIT,
-                         "h2d_bytes_per_step": int(B * 4 * 7), "d2h_bytes_per_step": int(2 * B + 4 * ((B + 31) // 32)
-                                                                                         + 8 * V),
-                         "ms_per_step": round(e2e_max, 3)}
-    g.close()
-    return result, dist, G, source, batches
+        R.step(stage, B, outs, e[1:13], R.events(5),
+               {"after_insert": after_insert, "before_delete": lambda: stream.wait_event(ready)})
+        h_fl_d.copy_(fl_d, non_blocking=True)
+        h_bm.copy_(bm, non_blocking=True)
+        for key, t in R.out.items():
+            h_res[key].copy_(t, non_blocking=True)
+        stream.wait_stream(copy)
+        e[13].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e[0].elapsed_time(e[13]))
+        bt = batches[k]
+        nq = int(np.unpackbits(h_bm.numpy().view(np.uint8)).sum())
+        if (int(h_fl_i.sum()) != bt["n_inserted"] or int(h_fl_d.sum()) != B or nq != bt["n_present"]):
+            raise RuntimeError("e2e batch %d is off the workload" % bt["k"])
+    if R.g.last_error() != mk.MK_OK:
+        raise RuntimeError("device status in the e2e pass")
+    e2e_max, = reduce_across([statistics.mean(e2e_ms)], "max", dist, device)
+    return {"value": round(units_total / (e2e_max / 1e3) / 1e6, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int(B * 4 * len(BATCH_KEYS)),
+            "d2h_bytes_per_step": int(2 * B + 4 * ((B + 31) // 32) + 4 * V * len(R.out)),
+            "ms_per_step": round(e2e_max, 3), "batches": [int(bt["k"]) for bt in batches],
+            "copies": "in: the step's 7 input arrays from pinned host memory; out: insert and delete flags, query "
+                      "bitmap, BFS and SSSP distances and parents, WCC labels"}
 
 
 # ------------------------------------------------------- learned sizing
@@ -830,69 +999,149 @@ def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=
 
 # ------------------------------------------------------------- CPU oracle
 
-ORACLE_SAMPLE = ("insert, delete and query of the step's B edges each, plus one from-scratch recompute of BFS, "
-                 "Dijkstra SSSP and union-find WCC after the insert batch; the step time counts that recompute "
-                 "twice, because the full step recomputes after each of its two update batches; single thread")
+ORACLE_SAMPLE = ("the whole step on the oracle (plain single-threaded C++): insert, delete and query of the step's "
+                 "B edges and a from-scratch BFS, Dijkstra SSSP and union-find WCC after each of the two update "
+                 "batches; two replicas of the oracle graph (one after the insert batch, one after the delete "
+                 "batch) let the six recomputes and the query batch run at once on seven host threads")
 
 
-def oracle_step(o, bt, source):
-    """Seconds of one step of the workload on the oracle (bounded sample:
-    the recompute after the delete batch is taken to cost the same as the
-    one after the insert batch)."""
-    t0 = time.perf_counter()
-    o.insert(bt["ins_src"], bt["ins_dst"], bt["ins_w"])
-    t1 = time.perf_counter()
-    o.bfs(source)
-    o.sssp(source)
-    o.wcc()
-    t2 = time.perf_counter()
-    o.delete(bt["del_src"], bt["del_dst"])
-    o.query(bt["q_src"], bt["q_dst"])
-    t3 = time.perf_counter()
-    return (t1 - t0) + 2 * (t2 - t1) + (t3 - t2)
+class OracleStep:
+    """The benchmark step on the CPU oracle, every part of it executed.
+
+    Two replicas of the oracle's edge set are kept: replica `a` is brought
+    to the state after the step's insert batch and replica `b` to the state
+    after its delete batch, so the six from-scratch recomputes of a step
+    (BFS, SSSP and WCC after each update batch) and the query batch, which
+    only read a replica, run at once on seven host threads (each oracle call
+    is one foreign call, during which ctypes releases the interpreter lock).
+    Replica `a` then applies the delete batch to catch up."""
+
+    THREADS = 7
+
+    def __init__(self, G):
+        import concurrent.futures as cf
+
+        import oracle
+
+        self.pool = cf.ThreadPoolExecutor(max_workers=self.THREADS)
+        self.a, self.b = oracle.OracleGraph(G.V), oracle.OracleGraph(G.V)
+        for f in [self.pool.submit(x.insert, G.src, G.dst, G.w) for x in (self.a, self.b)]:
+            f.result()
+
+    def advance(self, bt):
+        """Apply a batch's updates without timing (warm-up batches)."""
+        def upd(x):
+            x.insert(bt["ins_src"], bt["ins_dst"], bt["ins_w"])
+            x.delete(bt["del_src"], bt["del_dst"])
+        for f in [self.pool.submit(upd, x) for x in (self.a, self.b)]:
+            f.result()
+
+    def _timed(self, fn, *a):
+        t0 = time.perf_counter()
+        fn(*a)
+        return time.perf_counter() - t0
+
+    def step(self, bt, source):
+        """Seconds of one step and of its parts."""
+        a, b, pool, T = self.a, self.b, self.pool, self._timed
+        t0 = time.perf_counter()
+        fa = pool.submit(T, a.insert, bt["ins_src"], bt["ins_dst"], bt["ins_w"])
+        fb = pool.submit(lambda: (b.insert(bt["ins_src"], bt["ins_dst"], bt["ins_w"]),
+                                  T(b.delete, bt["del_src"], bt["del_dst"]))[1])
+        ins_s, del_s = fa.result(), fb.result()
+        t1 = time.perf_counter()
+        jobs = {"bfs1": (a.bfs, source), "sssp1": (a.sssp, source), "wcc1": (a.wcc,),
+                "bfs2": (b.bfs, source), "sssp2": (b.sssp, source), "wcc2": (b.wcc,),
+                "query": (b.query, bt["q_src"], bt["q_dst"])}
+        futs = {k: pool.submit(T, *v) for k, v in jobs.items()}
+        parts = {k: f.result() for k, f in futs.items()}
+        t2 = time.perf_counter()
+        a.delete(bt["del_src"], bt["del_dst"])
+        t3 = time.perf_counter()
+        parts.update({"insert": ins_s, "delete": del_s, "updates_wall": t1 - t0, "recompute_wall": t2 - t1,
+                      "catch_up": t3 - t2})
+        return t3 - t0, parts
+
+    def close(self):
+        self.pool.shutdown()
 
 
-def run_oracle_steps(G, batches, source, steps, B):
-    import oracle
+def oracle_summary(secs, parts, B):
+    s = statistics.mean(secs)
+    mean = lambda k: statistics.mean(p[k] for p in parts)  # noqa: E731
+    return {"value": round(3 * B / s / 1e6, 4), "ms_per_step": round(s * 1e3, 1),
+            "insert_medges_s": round(B / mean("insert") / 1e6, 3),
+            "delete_medges_s": round(B / mean("delete") / 1e6, 3),
+            "query_medges_s": round(B / mean("query") / 1e6, 3),
+            "incr_sssp_ms": round(mean("sssp1") * 1e3, 1), "decr_sssp_ms": round(mean("sssp2") * 1e3, 1),
+            "incr_bfs_ms": round(mean("bfs1") * 1e3, 1), "static_wcc_ms": round(mean("wcc2") * 1e3, 1)}
 
-    o = oracle.OracleGraph(G.V)
-    o.insert(G.src, G.dst, G.w)
-    secs = [oracle_step(o, batches[k], source) for k in range(steps)]
-    return secs
+
+def cpu_baseline(G, batches, source, B, W, steps=2):
+    """The oracle on `steps` steps of the workload (batches W, W + 1, ...
+    after W untimed batches), as in the reference arm."""
+    o = OracleStep(G)
+    for k in range(W):
+        o.advance(batches[k])
+    res = [o.step(batches[W + k], source) for k in range(steps)]
+    o.close()
+    summ = oracle_summary([r[0] for r in res], [r[1] for r in res], B)
+    cores = min(OracleStep.THREADS, os.cpu_count() or 1)
+    return {"value": summ["value"], "unit": UNIT, "cores": cores, "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": ORACLE_SAMPLE + "; B = %d; %d steps (batches %d-%d); %.1f s per step"
+                      % (B, steps, W, W + steps - 1, summ["ms_per_step"] / 1e3),
+            "phases": summ}
 
 
-def cpu_baseline(G, batches, source, B):
-    secs = run_oracle_steps(G, batches, source, 1, B)
-    s = secs[0]
-    return {"value": round(3 * B / s / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": ORACLE_SAMPLE + "; B = %d; %.1f s per step" % (B, s)}
+def cpu_all_cores(G, batches, B, W, steps=3):
+    """Batched insert, delete and query on all host cores (oracle/sharded:
+    the edge set partitioned by source, one thread per shard) over the same
+    batches W, W + 1, ... after W untimed batches."""
+    from oracle.sharded import ShardedGraph
+
+    p = ShardedGraph(G.V)
+    p.insert(G.src, G.dst, G.w)
+    for k in range(W):
+        p.insert(batches[k]["ins_src"], batches[k]["ins_dst"], batches[k]["ins_w"])
+        p.delete(batches[k]["del_src"], batches[k]["del_dst"])
+    t = {"insert": 0.0, "delete": 0.0, "query": 0.0}
+    for k in range(W, W + steps):
+        bt = batches[k]
+        for name, fn, a in (("insert", p.insert, (bt["ins_src"], bt["ins_dst"], bt["ins_w"])),
+                            ("delete", p.delete, (bt["del_src"], bt["del_dst"])),
+                            ("query", p.query, (bt["q_src"], bt["q_dst"]))):
+            t0 = time.perf_counter()
+            fn(*a)
+            t[name] += time.perf_counter() - t0
+    return {"kind": "edge set sharded by source, one thread per shard (oracle/sharded.cpp)",
+            "cores": p.threads, "steps": steps, "batch": B,
+            **{"%s_medges_s" % k: round(steps * B / v / 1e6, 2) for k, v in t.items()}}
 
 
 def run_reference(args, world, rank, local):
     if rank != 0:
         return None
     W, K, B = args.warmup, args.steps, args.batch
-    G, source, batches, _ = make_workload(args, W + K)
-    import oracle
-
-    o = oracle.OracleGraph(G.V)
-    o.insert(G.src, G.dst, G.w)
+    G, source, S = make_workload(args, B)
+    batches = [S.batch(B) for _ in range(W + K)]
+    o = OracleStep(G)
     for k in range(W):
         # warm-up steps only advance the graph: the oracle recomputes from
         # scratch and has no state a warm-up could prime
-        bt = batches[k]
-        o.insert(bt["ins_src"], bt["ins_dst"], bt["ins_w"])
-        o.delete(bt["del_src"], bt["del_dst"])
-    secs = [oracle_step(o, batches[W + k], source) for k in range(K)]
-    ms = statistics.mean(secs) * 1e3
-    value = 3 * B / (ms / 1e3) / 1e6
+        o.advance(batches[k])
+    res = [o.step(batches[W + k], source) for k in range(K)]
+    o.close()
+    summ = oracle_summary([r[0] for r in res], [r[1] for r in res], B)
+    value = summ["value"]
+    cores = min(OracleStep.THREADS, os.cpu_count() or 1)
     return {
-        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": W, "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic", "config": workload_config(args, G),
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": ORACLE_SAMPLE + "; B = %d" % B},
-        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": summ["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": workload_config(args, G),
+        **{k: v for k, v in summ.items() if k not in ("value", "ms_per_step")},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "host_cores": os.cpu_count(),
+                         "kind": "oracle", "sample": ORACLE_SAMPLE + "; B = %d; batches %d-%d" % (B, W, W + K - 1)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
@@ -1007,7 +1256,8 @@ def main(argv=None):
     result, dist, G, source, batches = run_ours(args, world, rank, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            result["cpu_baseline"] = cpu_baseline(G, batches, source, args.batch)
+            result["cpu_baseline"] = cpu_baseline(G, batches, source, args.batch, args.warmup)
+            result["cpu_all_cores_ops"] = cpu_all_cores(G, batches, args.batch, args.warmup)
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()

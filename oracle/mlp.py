@@ -107,3 +107,16 @@ def growth_targets(deg_then, deg_later, horizon):
     """log1p(max(0, later - then) / horizon) per vertex."""
     gain = np.asarray(deg_later, np.float64) - np.asarray(deg_then, np.float64)
     return np.log1p(np.maximum(gain, 0.0) / horizon)
+
+
+def adam_step(P, M, V, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, "Adam: a method for stochastic
+    optimization", ICLR 2015, Algorithm 1) at step t >= 1: biased first and
+    second moment estimates, their bias corrections, and the parameter
+    step.  Returns (P, M, V)."""
+    P, M, V, g = (np.asarray(x, np.float64) for x in (P, M, V, g))
+    M = b1 * M + (1.0 - b1) * g
+    V = b2 * V + (1.0 - b2) * g * g
+    m_hat = M / (1.0 - b1 ** t)
+    v_hat = V / (1.0 - b2 ** t)
+    return P - lr * m_hat / (np.sqrt(v_hat) + eps), M, V

@@ -30,6 +30,7 @@ _lib = None
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +66,15 @@ def _load():
             lib.syn_exponential_gaps.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64, _f64p]
             lib.syn_log_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                             _u64p]
+            lib.syn_set_create.restype = ctypes.c_void_p
+            lib.syn_set_create.argtypes = [ctypes.c_uint64]
+            lib.syn_set_destroy.argtypes = [ctypes.c_void_p]
+            lib.syn_set_count.restype = ctypes.c_uint64
+            lib.syn_set_count.argtypes = [ctypes.c_void_p]
+            for name in ("syn_set_add", "syn_set_remove"):
+                getattr(lib, name).restype = ctypes.c_uint64
+                getattr(lib, name).argtypes = [ctypes.c_void_p, _u32p, _u32p, ctypes.c_uint64, _u8p]
+            lib.syn_set_contains.argtypes = [ctypes.c_void_p, _u32p, _u32p, ctypes.c_uint64, _u8p]
             _lib = lib
     return _lib
 
@@ -162,7 +172,7 @@ def log_uniform(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
 # ------------------------------------------------------------------ recipes
 # Sub-stream tags: each recipe draws from substream(seed, TAG) so that the
 # graph, its weights and each batch use non-overlapping streams.
-TAG_PAIRS, TAG_W, TAG_PERM, TAG_QRY, TAG_QPERM, TAG_LONG, TAG_LOCAL = 1, 2, 3, 4, 5, 6, 7
+TAG_PAIRS, TAG_W, TAG_PERM, TAG_QRY, TAG_QPERM, TAG_LONG, TAG_LOCAL, TAG_QPRES = 1, 2, 3, 4, 5, 6, 7, 8
 
 
 class Batch(dict):
@@ -209,38 +219,153 @@ def powerlaw_graph(scale: int = 20, draws: int = 1 << 24, seed: int = 0, wlo: in
     return Batch(V=V, src=s, dst=d, w=w, scale=scale)
 
 
-def powerlaw_batch(g: Batch, k: int, B: int, wlo: int = 1, whi: int = 100) -> Batch:
-    """Batch k (seed 100 + k) on a graph from `powerlaw_graph`: B new R-MAT
-    inserts (self-loops dropped), B deletes drawn without replacement from the
-    initial edges (a fixed permutation consumed from the front, so they are
-    live as long as no earlier delete batch took them) and B queries, half from
-    the initial edges taken from the back of the permutation and half uniform,
-    shuffled."""
-    V, E = g.V, len(g.src)
-    seed = 100 + k
-    s, d = rmat_pairs(g.scale, B + B // 8 + 64, substream(seed, TAG_PAIRS))
-    keep = s != d
-    s, d = s[keep][:B], d[keep][:B]
-    w = weights(len(s), substream(seed, TAG_W), wlo, whi)
-    perm = _initial_perm(g)
-    lo = (k * B) % max(1, E)
-    di = np.take(perm, np.arange(lo, lo + B) % E)
-    half = B // 2
-    qi = np.take(perm, (E - 1 - ((k * half + np.arange(half)) % E)))
-    us, ud = uniform_pairs(V, B - half, substream(seed, TAG_QRY))
-    qs = np.concatenate([g.src[qi], us])
-    qd = np.concatenate([g.dst[qi], ud])
-    qp = permutation(B, substream(seed, TAG_QPERM))
-    return Batch(ins_src=s, ins_dst=d, ins_w=w, del_src=g.src[di], del_dst=g.dst[di],
-                 q_src=qs[qp], q_dst=qd[qp])
-
-
 def _initial_perm(g: Batch) -> np.ndarray:
     p = g.get("_perm")
     if p is None:
         p = permutation(len(g.src), substream(0, TAG_PERM))
         g["_perm"] = p
     return p
+
+
+class EdgeSet:
+    """Set of live (src, dst) pairs kept by a batch stream (``syn_set_*`` in
+    ``synth.c``).  It only decides which pairs a recipe draws."""
+
+    def __init__(self, capacity: int):
+        lib = _load()
+        self._lib = lib
+        self._h = lib.syn_set_create(int(capacity))
+        if not self._h:
+            raise MemoryError("EdgeSet: out of host memory")
+        self.capacity = int(capacity)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.syn_set_destroy(h)
+            self._h = None
+
+    def __len__(self):
+        return int(self._lib.syn_set_count(self._h))
+
+    def add(self, src, dst) -> np.ndarray:
+        s, d = np.ascontiguousarray(src, np.uint32), np.ascontiguousarray(dst, np.uint32)
+        f = np.zeros(len(s), np.uint8)
+        if len(s) and self._lib.syn_set_add(self._h, _p32(s), _p32(d), len(s), f.ctypes.data_as(_u8p)) == 2**64 - 1:
+            raise OverflowError("EdgeSet: more than %d live pairs" % self.capacity)
+        return f.astype(bool)
+
+    def remove(self, src, dst) -> np.ndarray:
+        s, d = np.ascontiguousarray(src, np.uint32), np.ascontiguousarray(dst, np.uint32)
+        f = np.zeros(len(s), np.uint8)
+        if len(s):
+            self._lib.syn_set_remove(self._h, _p32(s), _p32(d), len(s), f.ctypes.data_as(_u8p))
+        return f.astype(bool)
+
+    def contains(self, src, dst) -> np.ndarray:
+        s, d = np.ascontiguousarray(src, np.uint32), np.ascontiguousarray(dst, np.uint32)
+        f = np.zeros(len(s), np.uint8)
+        if len(s):
+            self._lib.syn_set_contains(self._h, _p32(s), _p32(d), len(s), f.ctypes.data_as(_u8p))
+        return f.astype(bool)
+
+
+class PowerlawStream:
+    """Batch stream of the power-law workload on a graph from
+    `powerlaw_graph`.  Batch k (seed 100 + k, any size B) is drawn against
+    the edges live when it runs, in the order the step applies it:
+
+    * inserts: B R-MAT draws of the graph's scale, self-loops dropped
+      (a draw of an edge that is already live is a no-op of the store);
+    * deletes: B distinct edges live after those inserts, the oldest first:
+      the initial edges in a fixed random order (seed 0), then the edges
+      that earlier batches actually added, in batch order;
+    * queries: exactly B // 2 edges live after the deletes (uniform over
+      them, with replacement) and B - B // 2 uniform pairs that are not
+      live (a live draw is rejected and drawn again), shuffled.
+
+    So every delete removes an edge and exactly half the queries are
+    present, at every batch size and for any number of batches.  The stream
+    keeps the live pairs in an `EdgeSet` and the deletion order in a ring;
+    batches must be drawn in order, k = 0, 1, 2, ...
+    """
+
+    def __init__(self, g: Batch, max_batch: int = 1 << 22, wlo: int = 1, whi: int = 100):
+        self.g, self.wlo, self.whi = g, wlo, whi
+        E = len(g.src)
+        self.max_batch = int(max_batch)
+        self.live = EdgeSet(E + self.max_batch)
+        if int(self.live.add(g.src, g.dst).sum()) != E:
+            raise ValueError("PowerlawStream: the graph has repeated pairs")
+        cap = 1 << max(10, int(E + self.max_batch).bit_length())
+        self._rs = np.empty(cap, np.uint32)
+        self._rd = np.empty(cap, np.uint32)
+        perm = _initial_perm(g)
+        self._rs[:E] = g.src[perm]
+        self._rd[:E] = g.dst[perm]
+        self.head, self.n_live, self.k = 0, E, 0
+
+    def _ring(self, first: int, count: int) -> np.ndarray:
+        return (first + np.arange(count, dtype=np.int64)) & (len(self._rs) - 1)
+
+    def _append(self, s: np.ndarray, d: np.ndarray):
+        if self.n_live + len(s) > len(self._rs):
+            raise OverflowError("PowerlawStream: ring full")
+        at = self._ring(self.head + self.n_live, len(s))
+        self._rs[at] = s
+        self._rd[at] = d
+        self.n_live += len(s)
+
+    def batch(self, B: int) -> Batch:
+        if B > self.max_batch:
+            raise ValueError("PowerlawStream: batch %d above max_batch %d" % (B, self.max_batch))
+        g, V = self.g, self.g.V
+        k = self.k
+        seed = 100 + k
+        s, d = rmat_pairs(g.scale, B + B // 8 + 64, substream(seed, TAG_PAIRS))
+        keep = s != d
+        s, d = s[keep][:B], d[keep][:B]
+        assert len(s) == B
+        w = weights(B, substream(seed, TAG_W), self.wlo, self.whi)
+        new = self.live.add(s, d)
+        self._append(s[new], d[new])
+        if self.n_live < B:
+            raise ValueError("PowerlawStream: fewer than %d live edges" % B)
+        at = self._ring(self.head, B)
+        ds, dd = self._rs[at].copy(), self._rd[at].copy()
+        if not self.live.remove(ds, dd).all():
+            raise AssertionError("PowerlawStream: a delete is not live")
+        self.head = (self.head + B) & (len(self._rs) - 1)
+        self.n_live -= B
+        half = B // 2
+        pick = weights(half, substream(seed, TAG_QPRES), 0, self.n_live - 1).astype(np.int64)
+        at = (self.head + pick) & (len(self._rs) - 1)
+        ps, pd = self._rs[at], self._rd[at]
+        us, ud = _absent_pairs(self.live, V, B - half, substream(seed, TAG_QRY))
+        qp = permutation(B, substream(seed, TAG_QPERM))
+        qs = np.concatenate([ps, us])[qp]
+        qd = np.concatenate([pd, ud])[qp]
+        self.k += 1
+        return Batch(ins_src=s, ins_dst=d, ins_w=w, del_src=ds, del_dst=dd, q_src=qs, q_dst=qd,
+                     k=k, n_inserted=int(new.sum()), n_present=half)
+
+
+def _absent_pairs(live: EdgeSet, V: int, n: int, seed: int):
+    """n uniform pairs over [0, V) that are not in `live` (rejection: a
+    live draw is replaced by the next draw of the same stream)."""
+    out_s, out_d, got, rnd = [], [], 0, 0
+    while got < n:
+        m = max(64, 2 * (n - got))
+        s, d = uniform_pairs(V, m, substream(seed, rnd))
+        ok = ~live.contains(s, d)
+        s, d = s[ok][:n - got], d[ok][:n - got]
+        out_s.append(s)
+        out_d.append(d)
+        got += len(s)
+        rnd += 1
+    if not out_s:
+        return np.empty(0, np.uint32), np.empty(0, np.uint32)
+    return np.concatenate(out_s), np.concatenate(out_d)
 
 
 def road_graph(rows: int = 4096, cols: int = 4096, long_frac: float = 0.001, seed: int = 0,

@@ -263,3 +263,136 @@ void syn_log_uniform(uint64_t n, uint64_t lo, uint64_t hi, uint64_t seed, uint64
         out[i] = v;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Live-edge set of a batch stream.  A recipe that must draw deletes and
+ * "present" queries from the edges that are live when a batch runs keeps
+ * the set of live (src, dst) pairs here: open addressing with linear
+ * probing over 64-bit keys src << 32 | dst and deletion by backward shift
+ * (Knuth Vol. 3, 6.4, Algorithm R), so no tombstones accumulate.  It only
+ * decides which pairs a generator draws; nothing reads it to compute an
+ * expected result. */
+typedef struct {
+    uint64_t *key;
+    uint64_t mask;
+    uint64_t count;
+} syn_set;
+
+#define SET_EMPTY UINT64_MAX
+
+static inline uint64_t set_home(const syn_set *s, uint64_t k)
+{
+    return sm_mix(k) & s->mask;
+}
+
+/* A set with room for `capacity` keys (the table holds at least twice that
+ * many slots).  Returns NULL if memory ran out. */
+void *syn_set_create(uint64_t capacity)
+{
+    syn_set *s = (syn_set *)malloc(sizeof(syn_set));
+    if (!s)
+        return NULL;
+    uint64_t slots = 1024;
+    while (slots < 2 * capacity)
+        slots <<= 1;
+    s->key = (uint64_t *)malloc(slots * sizeof(uint64_t));
+    if (!s->key) {
+        free(s);
+        return NULL;
+    }
+    memset(s->key, 0xFF, slots * sizeof(uint64_t));
+    s->mask = slots - 1;
+    s->count = 0;
+    return s;
+}
+
+void syn_set_destroy(void *h)
+{
+    syn_set *s = (syn_set *)h;
+    if (s) {
+        free(s->key);
+        free(s);
+    }
+}
+
+uint64_t syn_set_count(void *h)
+{
+    return ((syn_set *)h)->count;
+}
+
+/* Adds the pairs in order; added[i] (nullable) = 1 iff pair i was absent
+ * (so of repeated pairs only the first is 1).  Returns the number added, or
+ * UINT64_MAX if the table would pass half full (nothing after that pair is
+ * added). */
+uint64_t syn_set_add(void *h, const uint32_t *src, const uint32_t *dst, uint64_t n, uint8_t *added)
+{
+    syn_set *s = (syn_set *)h;
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t k = ((uint64_t)src[i] << 32) | dst[i];
+        uint64_t at_ = set_home(s, k);
+        while (s->key[at_] != SET_EMPTY && s->key[at_] != k)
+            at_ = (at_ + 1) & s->mask;
+        int fresh = s->key[at_] == SET_EMPTY;
+        if (fresh) {
+            if (2 * (s->count + 1) > s->mask + 1)
+                return UINT64_MAX;
+            s->key[at_] = k;
+            s->count++;
+            m++;
+        }
+        if (added)
+            added[i] = (uint8_t)fresh;
+    }
+    return m;
+}
+
+/* Removes the pairs in order; removed[i] (nullable) = 1 iff pair i was
+ * present.  Returns the number removed. */
+uint64_t syn_set_remove(void *h, const uint32_t *src, const uint32_t *dst, uint64_t n, uint8_t *removed)
+{
+    syn_set *s = (syn_set *)h;
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t k = ((uint64_t)src[i] << 32) | dst[i];
+        uint64_t at_ = set_home(s, k);
+        while (s->key[at_] != SET_EMPTY && s->key[at_] != k)
+            at_ = (at_ + 1) & s->mask;
+        int hit = s->key[at_] == k;
+        if (hit) {
+            /* backward shift: move later keys of the run into the hole
+             * unless their home lies cyclically in (hole, their slot] */
+            uint64_t hole = at_, j = at_;
+            for (;;) {
+                j = (j + 1) & s->mask;
+                if (s->key[j] == SET_EMPTY)
+                    break;
+                uint64_t home = set_home(s, s->key[j]);
+                int stays = (hole <= j) ? (hole < home && home <= j) : (hole < home || home <= j);
+                if (!stays) {
+                    s->key[hole] = s->key[j];
+                    hole = j;
+                }
+            }
+            s->key[hole] = SET_EMPTY;
+            s->count--;
+            m++;
+        }
+        if (removed)
+            removed[i] = (uint8_t)hit;
+    }
+    return m;
+}
+
+/* present[i] = 1 iff pair i is in the set. */
+void syn_set_contains(void *h, const uint32_t *src, const uint32_t *dst, uint64_t n, uint8_t *present)
+{
+    syn_set *s = (syn_set *)h;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t k = ((uint64_t)src[i] << 32) | dst[i];
+        uint64_t at_ = set_home(s, k);
+        while (s->key[at_] != SET_EMPTY && s->key[at_] != k)
+            at_ = (at_ + 1) & s->mask;
+        present[i] = (uint8_t)(s->key[at_] == k);
+    }
+}

@@ -140,7 +140,7 @@ def test_power_law_with_bucket_rule(cuda_lib):
     src = int(np.argmax(o.out_degree()))
     check_algos(g, o, [src])
     g.commit()
-    B = synth.powerlaw_batch(G, 0, 1 << 14)
+    B = synth.PowerlawStream(G, max_batch=1 << 14).batch(1 << 14)
     g.insert(B.ins_src, B.ins_dst, B.ins_w)
     o.insert(B.ins_src, B.ins_dst, B.ins_w)
     check_algos(g, o, [src])

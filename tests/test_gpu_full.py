@@ -2,9 +2,9 @@
 
 Power-law (R-MAT scale 20, 16M edges, load-factor buckets): every batch size
 of the workload (2^12, 2^16, 2^20, 2^22) is inserted, deleted and queried with
-per-edge flags and bitmaps compared to the oracle, the final edge set is
-compared in full, and BFS, SSSP and WCC from the max-degree vertex are
-compared in full after the last insert and the last delete batch.
+per-edge flags and bitmaps compared to the oracle, BFS, SSSP and WCC from the
+max-degree vertex are compared in full after every insert and every delete
+batch, and the final edge set is compared in full.
 
 Road-like (4,096 x 4,096 grid + 0.1% long-range edges, 67M edges): 64 mixed
 batches of 2^16 with incremental SSSP from the corner after each batch; each
@@ -55,9 +55,32 @@ def check_tree_properties(es, ed, ew, dist, par, src):
     assert np.array_equal(par[v].astype(np.int64), best[v]), "parent is not the min-id tight predecessor"
 
 
+def _oracle_algos(o, src):
+    """BFS, SSSP and WCC of the oracle, the three run at once (each is one
+    foreign call that releases the interpreter lock)."""
+    import concurrent.futures as cf
+
+    with cf.ThreadPoolExecutor(3) as ex:
+        f = [ex.submit(o.sssp, src), ex.submit(o.bfs, src), ex.submit(o.wcc)]
+        return f[0].result(), f[1].result(), f[2].result()
+
+
+def _compare_algos(g, o, src, what):
+    osp, obf, owc = _oracle_algos(o, src)
+    for name, (d, p), (od, op) in (("SSSP", g.sssp(src), osp), ("BFS", g.bfs(src), obf)):
+        assert np.array_equal(u32(d), od), "%s distances, %s" % (name, what)
+        assert np.array_equal(u32(p), op), "%s parents, %s" % (name, what)
+    assert np.array_equal(u32(g.wcc()), owc), "WCC labels, %s" % what
+
+
 def test_powerlaw_full_size_all_batch_sizes(cuda_lib):
+    """Every batch size of the workload in turn on one stream of batches
+    (deletes from live edges, queries half live): flags, bitmaps and
+    weights after every update, BFS/SSSP/WCC after every insert and every
+    delete batch, and the final edge set, all against the oracle."""
     mk = _mk()
     G = synth.powerlaw_graph()
+    S = synth.PowerlawStream(G)
     src = int(np.argmax(np.bincount(G.src, minlength=G.V)))
     buckets = mk.bucket_rule(G.V, G.src, 0.7)
     g = mk.Graph(G.V, edge_capacity_hint=len(G.src) + (1 << 24), buckets=buckets)
@@ -71,34 +94,24 @@ def test_powerlaw_full_size_all_batch_sizes(cuda_lib):
     g.bfs(src)
     g.wcc()
     g.commit()
-    for k, B in enumerate([1 << 12, 1 << 16, 1 << 20, 1 << 22]):
-        b = synth.powerlaw_batch(G, k, B)
+    for B in [1 << 12, 1 << 16, 1 << 20, 1 << 22]:
+        b = S.batch(B)
         f = g.insert(b.ins_src, b.ins_dst, b.ins_w).cpu().numpy()
-        assert np.array_equal(f, o.insert(b.ins_src, b.ins_dst, b.ins_w)), "insert flags, batch %d" % B
-        last = k == 3
-        if last:
-            for (d, p), (od, op) in ((g.sssp(src), o.sssp(src)), (g.bfs(src), o.bfs(src))):
-                assert np.array_equal(u32(d), od) and np.array_equal(u32(p), op)
-            assert np.array_equal(u32(g.wcc()), o.wcc())
-        else:
-            g.sssp(src)
-            g.bfs(src)
-            g.wcc()
+        of = o.insert(b.ins_src, b.ins_dst, b.ins_w)
+        assert np.array_equal(f, of), "insert flags, batch %d" % B
+        assert int(of.sum()) == b.n_inserted
+        _compare_algos(g, o, src, "after the insert batch of %d" % B)
         g.commit()
         f = g.delete(b.del_src, b.del_dst).cpu().numpy()
-        assert np.array_equal(f, o.delete(b.del_src, b.del_dst)), "delete flags, batch %d" % B
-        if last:
-            for (d, p), (od, op) in ((g.sssp(src), o.sssp(src)), (g.bfs(src), o.bfs(src))):
-                assert np.array_equal(u32(d), od) and np.array_equal(u32(p), op)
-            assert np.array_equal(u32(g.wcc()), o.wcc())
-        else:
-            g.sssp(src)
-            g.bfs(src)
-            g.wcc()
+        of = o.delete(b.del_src, b.del_dst)
+        assert np.array_equal(f, of), "delete flags, batch %d" % B
+        assert of.all(), "the stream's deletes are live"
+        _compare_algos(g, o, src, "after the delete batch of %d" % B)
         g.commit()
         bm, w = g.query(b.q_src, b.q_dst)
         obm, ow = o.query(b.q_src, b.q_dst)
         assert np.array_equal(u32(bm), obm) and np.array_equal(u32(w), ow), "query, batch %d" % B
+        assert int(oracle.bitmap_to_bool(obm, B).sum()) == B // 2
         assert g.last_error() == mk.MK_OK
     es, ed, ew = g.export()
     os_, od_, ow_ = o.export()

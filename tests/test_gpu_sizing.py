@@ -64,6 +64,71 @@ def test_features_and_targets_match_oracle(cuda_lib):
     assert np.allclose(T, omlp.growth_targets(hist[4], hist[0], 4.0), rtol=2e-6, atol=2e-6)
 
 
+def test_adam_steps_match_oracle(cuda_lib):
+    """Two Adam steps of the device (mk_mlp_adam_step: gradient kernel, then
+    the update kernel with bias corrections for steps 1 and 2) against the
+    float64 Adam of the oracle applied to the oracle's gradients.  The
+    device works in fp32, so where a gradient is tiny against the largest
+    one its sign can differ; there the step is only bounded by lr."""
+    torch, mk, sizing = _mods()
+    rng = np.random.default_rng(4)
+    P = rng.normal(0, 0.2, omlp.NPARAMS).astype(np.float32)
+    m = sizing.SizingModel(seed=5)
+    m.set_params(P)  # also clears the moments
+    lr = 1e-2
+    Pr, Mr, Vr = P.astype(np.float64), np.zeros(omlp.NPARAMS), np.zeros(omlp.NPARAMS)
+    sse = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for t in (1, 2):
+        X = rng.normal(0, 1, (3000, 8)).astype(np.float32)
+        T = rng.normal(0, 1, 3000).astype(np.float32)
+        # the oracle's gradient at the device's current masters
+        g_ref, _ = omlp.gradient(m.params(), X, T)
+        Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+        mk.check(m.lib.mk_mlp_adam_step(m._h, sizing._p(Xd), sizing._p(Td), 3000, lr, sizing._p(sse), sizing._s()),
+                 "mk_mlp_adam_step")
+        torch.cuda.synchronize()
+        Pd = m.params().astype(np.float64)
+        before = Pr.copy()
+        Pr, Mr, Vr = omlp.adam_step(Pr, Mr, Vr, g_ref, t, lr)
+        big = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+        assert big.sum() > omlp.NPARAMS // 4
+        step_d, step_r = Pd - before, Pr - before
+        assert np.allclose(step_d[big], step_r[big], rtol=2e-3, atol=1e-3 * lr), np.abs(step_d - step_r)[big].max()
+        # Kingma and Ba, Sec. 2.1: with 1 - b1 > sqrt(1 - b2) a step is at
+        # most lr (1 - b1) / sqrt(1 - b2) = 3.16 lr in size
+        assert np.all(np.abs(step_d) <= 3.2 * lr)
+        Pr = Pd.copy()  # continue both from the device's masters
+
+
+def test_sizing_buckets_match_oracle(cuda_lib):
+    """mk_sizing_buckets: the network's prediction y against the oracle's
+    forward pass, and the bucket counts against the oracle's bucket rule
+    applied to the device's own y (a ceiling decided in fp32 on the device
+    may differ only where the float64 quotient is within rounding of an
+    integer)."""
+    torch, mk, sizing = _mods()
+    rng = np.random.default_rng(6)
+    V = 20011
+    P = rng.normal(0, 0.3, omlp.NPARAMS).astype(np.float32)
+    m = sizing.SizingModel(seed=7)
+    m.set_params(P)
+    X = rng.normal(0, 1, (V, 8)).astype(np.float32)
+    deg = rng.integers(0, 3000, V).astype(np.uint32)
+    deg[:50] = 0
+    for horizon, lf, cap in ((8.0, 0.7, 1 << 16), (32.0, 0.5, 40)):
+        B, Y = m.buckets(torch.from_numpy(X).cuda(), mk.to_device_u32(deg), horizon, lf, cap)
+        y = Y.cpu().numpy().astype(np.float64)
+        y_ref = omlp.forward(P, X)
+        assert np.allclose(y, y_ref, rtol=1e-5, atol=1e-5 * (1 + np.abs(y_ref).max()))
+        b = mk.to_numpy_u32(B)
+        b_ref = omlp.learned_buckets(y, deg, horizon, lf, cap)
+        q = (deg + horizon * np.expm1(np.maximum(y, 0.0))) / (lf * 15.0)
+        edge = np.abs(q - np.round(q)) <= 1e-5 * np.maximum(1.0, q)
+        assert np.array_equal(b[~edge], b_ref[~edge]), np.nonzero(b != b_ref)[0][:10]
+        assert np.all(np.abs(b[edge].astype(np.int64) - b_ref[edge]) <= 1)
+        assert b.min() >= 1 and b.max() <= cap
+
+
 def test_degree_trace_counts_flagged_edges(cuda_lib):
     torch, mk, sizing = _mods()
     V = 64

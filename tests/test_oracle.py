@@ -75,6 +75,17 @@ def test_store_matches_bit_matrix_model(seed):
         assert np.array_equal(ew, m.weight[ref_s, ref_d])
         assert g.num_edges == int(m.present.sum())
         assert int(g.out_degree().sum()) == g.num_edges
+        # out-degree = row sums of the adjacency bit matrix (column sums
+        # would be the in-degree)
+        assert np.array_equal(g.out_degree(), m.present.sum(axis=1))
+
+
+def test_out_degree_of_an_out_star_and_an_in_star():
+    """Vertex 0 points at 1..5 and vertices 2..4 point at 6: out-degree
+    counts edges by their source only."""
+    g = oracle.OracleGraph(8)
+    g.insert([0, 0, 0, 0, 0, 2, 3, 4], [1, 2, 3, 4, 5, 6, 6, 6])
+    assert g.out_degree().tolist() == [5, 0, 1, 1, 1, 0, 0, 0]
 
 
 def test_first_occurrence_wins_within_a_batch():
@@ -266,3 +277,30 @@ def test_wcc_partition_matches_library_components():
     first = np.full(nc, g_in.V)
     np.minimum.at(first, comp, np.arange(g_in.V))
     assert np.array_equal(lab, first[comp])
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_sharded_cpu_baseline_matches_the_oracle(threads):
+    """The all-cores CPU baseline (edge set sharded by source, one thread per
+    shard) gives the oracle's flags, hits and weights on mixed batches with
+    repeated pairs."""
+    from oracle.sharded import ShardedGraph
+
+    rng = _rng(40 + threads)
+    V = 300
+    o, p = oracle.OracleGraph(V), ShardedGraph(V, threads)
+    for step in range(9):
+        n = 5000
+        s = rng.integers(0, V, n).astype(np.uint32)
+        d = rng.integers(0, V // 10, n).astype(np.uint32)
+        if step % 3 == 0:
+            w = rng.integers(1, 100, n).astype(np.uint32)
+            assert np.array_equal(p.insert(s, d, w), o.insert(s, d, w))
+        elif step % 3 == 1:
+            assert np.array_equal(p.delete(s, d), o.delete(s, d))
+        else:
+            hit, w = p.query(s, d)
+            obm, ow = o.query(s, d)
+            assert np.array_equal(hit.astype(bool), oracle.bitmap_to_bool(obm, n))
+            assert np.array_equal(w, ow)
+        assert p.num_edges == o.num_edges

@@ -73,3 +73,47 @@ def test_features_and_bucket_rule_by_hand():
     b = mlp.learned_buckets([np.log1p(2.0), -1.0, 0.0], [10, 0, 100], 8, 0.7, 1000)
     assert b.tolist() == [3, 1, 10]
     assert mlp.learned_buckets([50.0], [0], 8, 0.7, 7).tolist() == [7]
+
+
+def test_growth_targets_by_hand():
+    """log1p(max(0, later - then) / horizon): gains 8, 0, -8 (no growth) and
+    4 over a horizon of 4 batches are 2, 0, 0 and 1 edges per batch."""
+    t = mlp.growth_targets([0, 5, 10, 3], [8, 5, 2, 7], 4.0)
+    assert np.allclose(t, [np.log(3.0), 0.0, 0.0, np.log(2.0)], rtol=0, atol=1e-15)
+    # swapping the snapshots turns growth into loss, which counts as none
+    assert np.allclose(mlp.growth_targets([8, 5, 2, 7], [0, 5, 10, 3], 4.0), [0.0, 0.0, np.log(3.0), 0.0])
+
+
+def test_adam_first_step_moves_by_the_learning_rate():
+    """Adam's first update from zero moments is lr * g / (|g| + eps) after the
+    bias corrections cancel (1 - b1) and (1 - b2): a step of lr against the
+    gradient's sign wherever |g| >> eps, and none where g = 0."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0, 3e-9])
+    P, M, V = mlp.adam_step(np.zeros(5), np.zeros(5), np.zeros(5), g, 1, lr=0.01)
+    assert np.allclose(P[:2], [-0.01, 0.01], rtol=1e-7, atol=0)
+    assert np.isclose(P[2], -0.01 * 1e-3 / (1e-3 + 1e-8), rtol=1e-12)
+    assert P[3] == 0.0
+    assert np.isclose(P[4], -0.01 * 3e-9 / (3e-9 + 1e-8))
+    assert np.allclose(M, 0.1 * g) and np.allclose(V, 0.001 * g * g)
+
+
+def test_adam_second_step_by_hand():
+    """Two steps with gradients 1 then 3 (b1 = 0.9, b2 = 0.999, eps = 0):
+    m = 0.1, then 0.39 -> m_hat = 0.39 / 0.19; v = 0.001, then 0.010 ->
+    v_hat = 0.010 / 0.001999 (Kingma and Ba, Algorithm 1)."""
+    P, M, V = mlp.adam_step(np.array([1.0]), np.zeros(1), np.zeros(1), np.array([1.0]), 1, lr=0.1, eps=0.0)
+    assert np.isclose(P[0], 0.9)
+    P, M, V = mlp.adam_step(P, M, V, np.array([3.0]), 2, lr=0.1, eps=0.0)
+    assert np.isclose(M[0], 0.39) and np.isclose(V[0], 0.999 * 0.001 + 0.001 * 9.0)
+    m_hat = 0.39 / (1 - 0.81)
+    v_hat = (0.999 * 0.001 + 0.009) / (1 - 0.999 ** 2)
+    assert np.isclose(P[0], 0.9 - 0.1 * m_hat / np.sqrt(v_hat))
+
+
+def test_adam_minimises_a_quadratic():
+    """A few hundred steps on f(p) = sum((p - c)^2) bring p to c."""
+    c = np.array([3.0, -1.0, 0.25])
+    P, M, V = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 2001):
+        P, M, V = mlp.adam_step(P, M, V, 2 * (P - c), t, lr=0.05)
+    assert np.allclose(P, c, atol=1e-3)

@@ -54,3 +54,54 @@ def test_tiny_workload_shape():
     assert len(w.g_src) == 8192 and len(w.ins_src) == 1024
     assert len(w.del_src) == 1024 and len(w.q_src) == 4096
     assert w.g_w.min() >= 1 and w.g_w.max() <= 100
+
+
+def test_powerlaw_stream_draws_live_deletes_and_half_live_queries():
+    """Replayed on the oracle, every batch of the power-law stream deletes
+    only live edges and has exactly half its queries present, at mixed batch
+    sizes and far past the point where the initial edges are used up."""
+    import oracle
+
+    G = synth.powerlaw_graph(scale=13, draws=1 << 14)
+    S = synth.PowerlawStream(G, max_batch=1 << 12)
+    o = oracle.OracleGraph(G.V)
+    o.insert(G.src, G.dst, G.w)
+    E0 = len(G.src)
+    total = 0
+    for k, B in enumerate([256, 1 << 12, 1000, 1 << 12, 1 << 12, 7, 1 << 12] * 3):
+        b = S.batch(B)
+        assert b.k == k and len(b.ins_src) == len(b.del_src) == len(b.q_src) == B
+        fi = o.insert(b.ins_src, b.ins_dst, b.ins_w)
+        assert int(fi.sum()) == b.n_inserted
+        assert o.delete(b.del_src, b.del_dst).all()
+        bm, _ = o.query(b.q_src, b.q_dst)
+        assert int(oracle.bitmap_to_bool(bm, B).sum()) == B // 2 == b.n_present
+        assert o.num_edges == S.n_live == len(S.live)
+        total += B
+    assert total > 2 * E0
+
+
+def test_edge_set_matches_a_python_set():
+    rng = np.random.default_rng(1)
+    es = synth.EdgeSet(4000)
+    ref = set()
+    for it in range(60):
+        s = rng.integers(0, 40, 200).astype(np.uint32)
+        d = rng.integers(0, 40, 200).astype(np.uint32)
+        op = it % 3
+        if op == 0:
+            got = es.add(s, d)
+        elif op == 1:
+            got = es.remove(s, d)
+        else:
+            got = es.contains(s, d)
+        want = []
+        for a, b in zip(s.tolist(), d.tolist()):
+            present = (a, b) in ref
+            want.append(not present if op == 0 else present)
+            if op == 0:
+                ref.add((a, b))
+            elif op == 1:
+                ref.discard((a, b))
+        assert got.tolist() == want
+        assert len(es) == len(ref)
