@@ -207,6 +207,32 @@ typedef struct mk_query_req {
  * are copied to the device before the call returns. */
 mk_status mk_query_multi(mk_graph *g, const mk_query_req *h_reqs, uint32_t nreq, void *stream);
 
+/* One update request of mk_update_multi. */
+typedef struct mk_update_req {
+    int kind;               /* MK_REQ_INSERT or MK_REQ_DELETE (serving request kinds, below) */
+    const uint32_t *d_src;  /* n edges (device) */
+    const uint32_t *d_dst;
+    const uint32_t *d_w;    /* insert weights (nullable = weight 1); ignored by a delete */
+    uint64_t n;
+    uint8_t *d_flags;       /* nullable: n flags as in mk_insert_batch / mk_delete_batch */
+} mk_update_req;
+
+/* Applies the host array of update requests in order, with results, flags
+ * and change log identical to one mk_insert_batch / mk_delete_batch call per
+ * request.  Each run of consecutive requests of one kind is merged into one
+ * batch: one gather launch copies the run's edges into a contiguous staging
+ * array (in request order, so the first occurrence of a repeated pair is
+ * still the one applied, which is what applying the requests one after
+ * another gives), one staged insert or delete applies it, and one scatter
+ * launch writes each request's flags; a run of one request is applied
+ * directly.  So a stream of many small requests costs a few launches per run
+ * instead of per request (the paper applies one batch per launch).  The
+ * descriptors are copied to the device before the call returns; the staging
+ * arrays are stream-ordered allocations (cudaMallocAsync) freed on `stream`.
+ * MK_ERR_INVALID_ARG (nothing enqueued) for an unknown kind or a null
+ * src/dst with n > 0. */
+mk_status mk_update_multi(mk_graph *g, const mk_update_req *h_reqs, uint32_t nreq, void *stream);
+
 /* A batcher captures the multi-request query launch (descriptor copy from
  * pinned memory + kernel) in a CUDA graph once and replays it for every
  * group of requests: mk_batcher_add_query queues a request on the host,
@@ -254,13 +280,15 @@ mk_status mk_set_tuning(mk_graph *g, const mk_tuning *t);
  * fewer than max_inflight are in flight.  A run of consecutive read requests
  * (queries, BFS/SSSP) is one group: its queries go out as one CUDA-graph
  * replay of the multi-request query kernel, its BFS/SSSP calls on a second
- * stream, overlapping on the device.  An insert or delete is a barrier: it
- * waits for every earlier read and every later read waits for it, so each
- * result equals that of running the requests one at a time in arrival
- * order.  An insert is admitted only if the slab pool has at least n free
- * slabs (the worst case of one new slab per edge); otherwise it completes
- * with MK_ERR_POOL_EXHAUSTED and changes nothing.  Every commit_every
- * updates (0 = never) the server commits the epoch (mk_commit_batch).
+ * stream, overlapping on the device.  A run of consecutive inserts (or
+ * deletes) is applied as one mk_update_multi call, up to the next commit
+ * point, and is a barrier: it waits for every earlier read and every later
+ * read waits for it, so each result equals that of running the requests one
+ * at a time in arrival order.  An insert is admitted only if the slab pool
+ * has at least n free slabs beyond those its run already claimed (the worst
+ * case of one new slab per edge); otherwise it completes with
+ * MK_ERR_POOL_EXHAUSTED and changes nothing.  Every commit_every updates
+ * (0 = never) the server commits the epoch (mk_commit_batch).
  * Buffers named in a request must stay valid until it completes.
  */
 enum { MK_REQ_QUERY = 0, MK_REQ_INSERT = 1, MK_REQ_DELETE = 2, MK_REQ_SSSP = 3, MK_REQ_BFS = 4 };
@@ -390,7 +418,9 @@ mk_status mk_graph_stats(mk_graph *g, mk_stats *out, void *stream);
 mk_status mk_pool_free(mk_graph *g, uint64_t *out, void *stream);
 
 /* Synchronises the device, returns the sticky device status (MK_OK or an
- * MK_ERR_* code) and clears it. */
+ * MK_ERR_* code) and clears it.  After an error status every incremental
+ * BFS/SSSP/WCC state of the graph recomputes statically at its next call
+ * (a failed call may have left it half updated). */
 mk_status mk_last_error(mk_graph *g);
 
 /* UpdateIterator marker of slab list `bucket` of vertex v (host outputs):
@@ -428,6 +458,21 @@ mk_status mk_profile_read(mk_graph *g, mk_kernel_time *out, int cap, int *n_out)
  * creation (scan and export-sort calls included, counted from their launch
  * plans). */
 uint64_t mk_launch_count(mk_graph *g);
+
+/* Test hooks for the failure paths (a service of this library; the paper
+ * has none).  knob MK_DEBUG_BARRIER_SPINS: value 0 restores the default
+ * poll limit of the BFS/SSSP round kernel's grid barrier (2^24 polls of
+ * about 32 ns); value v >= 1 sets it to v - 1 polls, so v = 1 makes a wait
+ * give up at once unless every block has arrived: the call then reports
+ * MK_ERR_TIMEOUT through mk_last_error.  knob MK_DEBUG_HOST_ROUNDS: value 1
+ * runs the rounds with the host-driven fallback (one launch per round, the
+ * host reading each frontier size) that is otherwise used only when the
+ * cooperative launch is refused; 0 restores the kernel.  Results are the
+ * same either way.  After mk_last_error has returned an error status, every
+ * incremental algorithm state of the graph recomputes statically at its
+ * next call. */
+enum { MK_DEBUG_BARRIER_SPINS = 1, MK_DEBUG_HOST_ROUNDS = 2 };
+mk_status mk_debug_set(mk_graph *g, int knob, uint64_t value);
 
 /* Library version string. */
 const char *mk_version(void);

@@ -231,6 +231,32 @@ class Graph:
         del keep
         return outs
 
+    def update_multi(self, requests, flags: bool = True, stream=None):
+        """Apply a list of update requests in order with one mk_update_multi
+        call.  Each request is ("insert", src, dst, w) or ("delete", src,
+        dst); returns one flag tensor per request (None when flags=False)."""
+        torch = _torch()
+        from ._native import MK_REQ_DELETE, MK_REQ_INSERT, mk_update_req
+
+        keep, outs = [], []
+        arr = (mk_update_req * max(1, len(requests)))()
+        for i, req in enumerate(requests):
+            kind = {"insert": MK_REQ_INSERT, "delete": MK_REQ_DELETE}[req[0]]
+            s, d = to_device_u32(req[1]), to_device_u32(req[2])
+            w = to_device_u32(req[3]) if kind == MK_REQ_INSERT and len(req) > 3 else None
+            n = s.numel()
+            f = torch.empty(max(n, 1), dtype=torch.uint8, device=self.device) if flags else None
+            arr[i].kind, arr[i].n = kind, n
+            arr[i].d_src, arr[i].d_dst = s.data_ptr(), d.data_ptr()
+            arr[i].d_w = None if w is None else w.data_ptr()
+            arr[i].d_flags = None if f is None else f.data_ptr()
+            keep.append((s, d, w))
+            outs.append(None if f is None else f[:n])
+        check(self._lib.mk_update_multi(self._h, arr, len(requests), _stream(stream)), "mk_update_multi")
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        del keep
+        return outs
+
     def autotune(self, src, dst, bfs_source: int, stream=None) -> dict:
         from ._native import mk_tuning
 

@@ -78,6 +78,11 @@ class mk_query_req(ctypes.Structure):
                 ("d_bitmap", ctypes.c_void_p), ("d_w", ctypes.c_void_p)]
 
 
+class mk_update_req(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p),
+                ("d_w", ctypes.c_void_p), ("n", ctypes.c_uint64), ("d_flags", ctypes.c_void_p)]
+
+
 class mk_tuning(ctypes.Structure):
     _fields_ = [("query_group", ctypes.c_int), ("query_block", ctypes.c_int), ("rounds_blocks_per_sm", ctypes.c_int),
                 ("query_best_ms", ctypes.c_float), ("rounds_best_ms", ctypes.c_float),
@@ -91,6 +96,7 @@ class mk_request(ctypes.Structure):
 
 
 MK_REQ_QUERY, MK_REQ_INSERT, MK_REQ_DELETE, MK_REQ_SSSP, MK_REQ_BFS = 0, 1, 2, 3, 4
+MK_DEBUG_BARRIER_SPINS, MK_DEBUG_HOST_ROUNDS = 1, 2
 
 
 class mk_kernel_time(ctypes.Structure):
@@ -126,12 +132,14 @@ SIGNATURES = {
     "mk_profile_read": (_INT, [_P, ctypes.POINTER(mk_kernel_time), _INT, ctypes.POINTER(_INT)]),
     "mk_launch_count": (_U64, [_P]),
     "mk_version": (ctypes.c_char_p, []),
+    "mk_debug_set": (_INT, [_P, _INT, _U64]),
     "mk_server_create": (_INT, [_P, _U32, _U32, ctypes.POINTER(_P)]),
     "mk_server_destroy": (_INT, [_P]),
     "mk_server_submit": (_INT, [_P, ctypes.POINTER(mk_request)]),
     "mk_server_progress": (_INT, [_P, _P, _P, _U32, ctypes.POINTER(_U32)]),
     "mk_server_pending": (_INT, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
     "mk_query_multi": (_INT, [_P, ctypes.POINTER(mk_query_req), _U32, _P]),
+    "mk_update_multi": (_INT, [_P, ctypes.POINTER(mk_update_req), _U32, _P]),
     "mk_batcher_create": (_INT, [_P, _U32, ctypes.POINTER(_P)]),
     "mk_batcher_destroy": (_INT, [_P]),
     "mk_batcher_add_query": (_INT, [_P, _P, _P, _U64, _P, _P]),

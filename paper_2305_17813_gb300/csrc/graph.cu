@@ -641,9 +641,30 @@ mk_status mk_last_error(mk_graph *g)
         return MK_ERR_CUDA;
     int st = 0;
     MK_CUDA(cudaMemcpy(&st, &g->d_state->status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (st != 0)
+    if (st != 0) {
         MK_CUDA(cudaMemset(&g->d_state->status, 0, sizeof(int)));
+        // a call that failed on the device may have left its algorithm
+        // state half updated: every state recomputes statically next time
+        for (auto &kv : g->consumers)
+            kv.second->epoch = ~0ull;
+    }
     return st;
+}
+
+mk_status mk_debug_set(mk_graph *g, int knob, uint64_t value)
+{
+    if (!g)
+        return MK_ERR_INVALID_ARG;
+    switch (knob) {
+    case MK_DEBUG_BARRIER_SPINS:
+        g->dbg_barrier_spins = value ? std::min<uint64_t>(value - 1, 0xFFFFFFFFull) : ~0ull;
+        return MK_OK;
+    case MK_DEBUG_HOST_ROUNDS:
+        g->dbg_host_rounds = value != 0;
+        return MK_OK;
+    default:
+        return MK_ERR_INVALID_ARG;
+    }
 }
 
 mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *slab, uint32_t *lane,

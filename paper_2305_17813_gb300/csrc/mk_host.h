@@ -82,6 +82,11 @@ struct mk_graph {
     bool epoch_has_deletes = false;
     std::map<std::pair<int, uint32_t>, mk::Consumer *> consumers;
     uint32_t *h_pinned = nullptr; // 16 pinned words for small device->host reads
+    // test hooks (mk_debug_set): grid-barrier poll limit of the round kernel
+    // (~0 = the default), and the host-driven round loop instead of the
+    // cooperative kernel
+    uint64_t dbg_barrier_spins = ~0ull;
+    bool dbg_host_rounds = false;
     // profiling
     bool prof = false;
     std::vector<mk::TimedLaunch> timed;

@@ -7,7 +7,8 @@
 // memory allow.  Consecutive read requests form one group: all its queries
 // go out as one CUDA-graph replay of the multi-request query kernel (the
 // batcher) on the query stream, its SSSP requests run on the SSSP stream, so
-// the two overlap on the device; both wait for the last update.  An update is
+// the two overlap on the device; both wait for the last update.  A run of
+// consecutive updates of one kind is one merged batch (mk_update_multi) and
 // a barrier: its stream waits for every read group launched before it, and
 // the next reads wait for it, so every request sees exactly the updates that
 // arrived before it -- the results are those of running the requests one at
@@ -47,7 +48,7 @@ struct mk_server {
     std::deque<Group> flight;
     std::vector<cudaEvent_t> spare;
     std::vector<std::pair<uint64_t, int>> finished;
-    uint64_t groups = 0, merged_queries = 0;
+    uint64_t groups = 0, merged_queries = 0, merged_updates = 0;
 };
 
 namespace {
@@ -132,43 +133,67 @@ mk_status launch_reads(mk_server *s, uint32_t room)
     return MK_OK;
 }
 
-// Launches the update at the head of the queue (a barrier).
+// Launches the run of updates of one kind at the head of the queue (a
+// barrier), up to the next commit point and the free in-flight slots, as
+// one mk_update_multi call (merged into one staged batch; results identical
+// to one call per request in order).
 mk_status launch_update(mk_server *s)
 {
-    const mk_request r = s->queue.front();
+    const int kind = s->queue.front().kind;
+    const uint32_t to_commit = s->commit_every ? s->commit_every - s->updates_since_commit : 0xFFFFFFFFu;
+    const uint32_t slots = std::max<uint32_t>(1, s->max_inflight - std::min(s->inflight, s->max_inflight));
     Group grp;
-    int st = MK_OK;
-    if (r.kind == MK_REQ_INSERT) {
-        // admission by slab-pool memory: at most one new slab per edge
-        if (s->pool_free_est < r.n)
-            MK_TRY(refresh_pool(s));
-        if (s->pool_free_est < r.n) {
-            st = MK_ERR_POOL_EXHAUSTED; // refused, nothing enqueued
+    std::vector<mk_update_req> reqs;
+    std::vector<size_t> member; // position in grp of each request in reqs
+    uint64_t need = 0;
+    while (!s->queue.empty() && s->queue.front().kind == kind && grp.tags.size() < std::min(to_commit, slots)) {
+        const mk_request r = s->queue.front();
+        int st = MK_OK;
+        if (kind == MK_REQ_INSERT) {
+            // admission by slab-pool memory: at most one new slab per edge
+            if (s->pool_free_est < need + r.n)
+                MK_TRY(refresh_pool(s));
+            if (s->pool_free_est < need + r.n)
+                st = MK_ERR_POOL_EXHAUSTED; // refused, nothing enqueued
+            else
+                need += r.n;
         }
+        s->queue.pop_front();
+        if (st == MK_OK) {
+            mk_update_req q{};
+            q.kind = kind;
+            q.d_src = r.d_src;
+            q.d_dst = r.d_dst;
+            q.d_w = r.d_w;
+            q.n = r.n;
+            q.d_flags = (uint8_t *)r.d_out0;
+            reqs.push_back(q);
+            member.push_back(grp.tags.size());
+        }
+        grp.tags.push_back(r.tag);
+        grp.status.push_back(st);
     }
-    s->queue.pop_front();
     for (cudaEvent_t e : s->reads_since_update)
         MK_CUDA(cudaStreamWaitEvent(s->su, e, 0));
     s->reads_since_update.clear();
-    if (st == MK_OK) {
-        if (r.kind == MK_REQ_INSERT) {
-            st = mk_insert_batch(s->g, r.d_src, r.d_dst, r.d_w, r.n, (uint8_t *)r.d_out0, s->su);
-            s->pool_free_est -= std::min<uint64_t>(s->pool_free_est, r.n);
-        } else {
-            st = mk_delete_batch(s->g, r.d_src, r.d_dst, r.n, (uint8_t *)r.d_out0, s->su);
-        }
-        if (st == MK_OK && s->commit_every && ++s->updates_since_commit >= s->commit_every) {
+    if (!reqs.empty()) {
+        int st = mk_update_multi(s->g, reqs.data(), (uint32_t)reqs.size(), s->su);
+        s->pool_free_est -= std::min<uint64_t>(s->pool_free_est, need);
+        s->updates_since_commit += (uint32_t)reqs.size();
+        if (st == MK_OK && s->commit_every && s->updates_since_commit >= s->commit_every) {
             st = mk_commit_batch(s->g, s->su);
             s->updates_since_commit = 0;
         }
+        if (st != MK_OK)
+            for (size_t i : member)
+                grp.status[i] = st;
+        s->merged_updates += reqs.size() > 1 ? reqs.size() : 0;
     }
     grp.done_u = ev(s);
     MK_CUDA(cudaEventRecord(grp.done_u, s->su));
     MK_CUDA(cudaEventRecord(s->last_update, s->su));
     s->have_update = true;
-    grp.tags.push_back(r.tag);
-    grp.status.push_back(st);
-    s->inflight += 1;
+    s->inflight += (uint32_t)grp.tags.size();
     s->flight.push_back(std::move(grp));
     s->groups++;
     return MK_OK;

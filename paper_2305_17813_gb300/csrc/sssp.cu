@@ -78,6 +78,7 @@ struct RoundArgs {
     uint32_t cap;
     uint32_t max_hops;
     uint32_t max_rounds;
+    uint32_t barrier_spins; // polls before a grid-barrier wait gives up
     uint32_t source;
     int unit;
     uint32_t *dist;       // the caller's outputs (nullable), written when the phase ends
@@ -209,7 +210,7 @@ __device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t *cnts, u
 // reset between barriers (the counter is zeroed before each launch).
 // `passed` is the block's count of barriers so far (thread 0's copy is the
 // one used).  Returns false when the wait gave up.
-__device__ bool grid_barrier(uint32_t *bar, uint32_t &passed)
+__device__ bool grid_barrier(uint32_t *bar, uint32_t &passed, uint32_t max_spins)
 {
     __shared__ int ok_s;
     __syncthreads();
@@ -220,7 +221,7 @@ __device__ bool grid_barrier(uint32_t *bar, uint32_t &passed)
         int ok = 1;
         uint32_t spins = 0;
         while ((int)(ld_volatile(bar) - target) < 0) {
-            if (++spins > kBarrierSpins) {
+            if (++spins > max_spins) {
                 ok = 0;
                 break;
             }
@@ -262,13 +263,15 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
         if (threadIdx.x == 0)
             s_word = ld_volatile(gcnt + r % 3);
         __syncthreads();
-        uint32_t n = s_word;
+        // a frontier never holds more than `cap` entries; a larger count
+        // (entries dropped on overflow, reported below) is read as cap
+        uint32_t n = min(s_word, a.cap);
         if (n == 0)
             break;
         if (n > kSoloLists) {
             round_step(a, gcnt, r, n, warp0, nwarps, rid, bq);
             ++bars;
-            if (!grid_barrier(a.ctr + kBar, passed)) {
+            if (!grid_barrier(a.ctr + kBar, passed, a.barrier_spins)) {
                 ok = false;
                 break;
             }
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
         }
         // every block has read n: block 0 may now change the global sizes
         bars += 2;
-        if (!grid_barrier(a.ctr + kBar, passed)) {
+        if (!grid_barrier(a.ctr + kBar, passed, a.barrier_spins)) {
             ok = false;
             break;
         }
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
                 a.ctr[kSoloR] = r;
             }
         }
-        if (!grid_barrier(a.ctr + kBar, passed)) {
+        if (!grid_barrier(a.ctr + kBar, passed, a.barrier_spins)) {
             ok = false;
             break;
         }
@@ -698,6 +701,11 @@ mk_status get_consumer(mk_graph *g, int kind, uint32_t source, Consumer **out)
         st = device_alloc(g, (void **)&c->front[0], H * 8);
     if (st == MK_OK)
         st = device_alloc(g, (void **)&c->front[1], H * 8);
+    // frontier slots hold <kNil, ...> until written, so a slot read before
+    // it is written names no list
+    if (st == MK_OK && (cudaMemset(c->front[0], 0xFF, H * 8) != cudaSuccess ||
+                        cudaMemset(c->front[1], 0xFF, H * 8) != cudaSuccess))
+        st = MK_ERR_CUDA;
     if (st == MK_OK)
         st = device_alloc(g, (void **)&c->stamp, V * 4);
     if (st == MK_OK)
@@ -760,19 +768,21 @@ mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
     const int grid = rounds_grid(g->tune.rounds_blocks_per_sm);
     const int block = rounds_block(g->tune.rounds_blocks_per_sm);
     void *args[] = {&a};
-    mk_status st = timed(g, name, s, 1, [&]() {
-        return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(block), args, 0, s);
-    });
-    if (st == MK_OK)
-        return MK_OK;
-    cudaGetLastError();
+    if (!g->dbg_host_rounds) {
+        const mk_status st = timed(g, name, s, 1, [&]() {
+            return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(block), args, 0, s);
+        });
+        if (st == MK_OK)
+            return MK_OK;
+        cudaGetLastError();
+    }
     // fallback: one launch per round, the host reads each size
     for (uint32_t r = 0;; ++r) {
         if (r > a.max_rounds)
             return MK_ERR_TIMEOUT;
         MK_CUDA(cudaMemcpyAsync(g->h_pinned, a.ctr + kCnt0 + r % 3, 4, cudaMemcpyDeviceToHost, s));
         MK_CUDA(cudaStreamSynchronize(s));
-        const uint32_t n = g->h_pinned[0];
+        const uint32_t n = std::min(g->h_pinned[0], a.cap);
         if (n == 0) {
             return timed(g, "sssp_finish", s, 2, [&]() {
                 k_sssp_finish<<<1, 1, 0, s>>>(a.ctr, g->d_state, r);
@@ -806,6 +816,7 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     a.cap = H;
     a.max_hops = g->v.P + 2;
     a.max_rounds = V + 2;
+    a.barrier_spins = g->dbg_barrier_spins != ~0ull ? (uint32_t)g->dbg_barrier_spins : kBarrierSpins;
     a.source = source;
     a.unit = kind == kBfs ? 1 : 0;
     a.dist = d_dist;

@@ -19,6 +19,8 @@
 #include "walk.cuh"
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 using namespace mk;
 
@@ -607,14 +609,59 @@ mk_status stage(mk_graph *g, const uint32_t *src, const uint32_t *dst, const uin
 
 } // namespace
 
-extern "C" {
-
-mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w,
-                          uint64_t n, uint8_t *d_inserted, void *stream)
+// Gathers the edges of the update requests [0, nreq) into contiguous
+// arrays: position i of the merged batch is edge i - prefix[r] of the
+// request r with prefix[r] <= i < prefix[r + 1] (binary search; a request
+// with no edges has prefix[r] == prefix[r + 1] and is never chosen).  A
+// null weight array stands for weight 1.
+__global__ void k_gather_updates(const mk_update_req *__restrict__ reqs, const uint64_t *__restrict__ prefix,
+                                 uint32_t nreq, uint64_t total, uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                 uint32_t *__restrict__ w)
 {
-    if (!g || (n > 0 && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
-        return MK_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
+        uint32_t lo = 0, hi = nreq;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (prefix[mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const mk_update_req &r = reqs[lo];
+        const uint64_t j = i - prefix[lo];
+        src[i] = r.d_src[j];
+        dst[i] = r.d_dst[j];
+        if (w)
+            w[i] = r.d_w ? r.d_w[j] : 1u;
+    }
+}
+
+// Writes the merged batch's flags back to the requests that asked for them.
+__global__ void k_scatter_flags(const mk_update_req *__restrict__ reqs, const uint64_t *__restrict__ prefix,
+                                uint32_t nreq, uint64_t total, const uint8_t *__restrict__ flags)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
+        uint32_t lo = 0, hi = nreq;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (prefix[mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        uint8_t *out = reqs[lo].d_flags;
+        if (out)
+            out[i - prefix[lo]] = flags[i];
+    }
+}
+
+namespace {
+
+mk_status insert_impl(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w, uint64_t n,
+                      uint8_t *d_inserted, cudaStream_t s)
+{
     g->change_seq++;
     if (n == 0)
         return MK_OK;
@@ -631,12 +678,9 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
     });
 }
 
-mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
-                          uint8_t *d_deleted, void *stream)
+mk_status delete_impl(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n, uint8_t *d_deleted,
+                      cudaStream_t s)
 {
-    if (!g || (n > 0 && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
-        return MK_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
     g->change_seq++;
     if (n == 0)
         return MK_OK;
@@ -666,6 +710,122 @@ mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
                                                   (uint32_t)g->dlog_cap, max_hops);
         return cudaSuccess;
     });
+}
+
+} // namespace
+
+extern "C" {
+
+mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w,
+                          uint64_t n, uint8_t *d_inserted, void *stream)
+{
+    if (!g || (n > 0 && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
+        return MK_ERR_INVALID_ARG;
+    return insert_impl(g, d_src, d_dst, d_w, n, d_inserted, (cudaStream_t)stream);
+}
+
+mk_status mk_delete_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                          uint8_t *d_deleted, void *stream)
+{
+    if (!g || (n > 0 && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
+        return MK_ERR_INVALID_ARG;
+    return delete_impl(g, d_src, d_dst, n, d_deleted, (cudaStream_t)stream);
+}
+
+mk_status mk_update_multi(mk_graph *g, const mk_update_req *h_reqs, uint32_t nreq, void *stream)
+{
+    if (!g || (nreq && !h_reqs))
+        return MK_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < nreq; ++i) {
+        const mk_update_req &r = h_reqs[i];
+        if ((r.kind != MK_REQ_INSERT && r.kind != MK_REQ_DELETE) || (r.n && (!r.d_src || !r.d_dst)))
+            return MK_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // runs of consecutive requests of one kind, and each run's prefix of
+    // edge counts (nreq + runs entries in all)
+    std::vector<std::pair<uint32_t, uint32_t>> runs;
+    for (uint32_t i = 0; i < nreq;) {
+        uint32_t j = i + 1;
+        while (j < nreq && h_reqs[j].kind == h_reqs[i].kind)
+            ++j;
+        runs.push_back({i, j});
+        i = j;
+    }
+    std::vector<uint64_t> prefix;
+    uint64_t max_total = 0;
+    for (auto &r : runs) {
+        uint64_t acc = 0;
+        for (uint32_t i = r.first; i < r.second; ++i) {
+            prefix.push_back(acc);
+            acc += h_reqs[i].n;
+        }
+        prefix.push_back(acc);
+        if (acc >= 0xFFFFFFFFull)
+            return MK_ERR_INVALID_ARG;
+        if (r.second - r.first > 1)
+            max_total = std::max(max_total, acc);
+    }
+    // descriptors and prefixes in one device block; staging for the largest
+    // merged run
+    const size_t desc_bytes = (size_t)nreq * sizeof(mk_update_req);
+    const size_t block_bytes = desc_bytes + prefix.size() * 8;
+    std::vector<unsigned char> img(block_bytes);
+    std::memcpy(img.data(), h_reqs, desc_bytes);
+    std::memcpy(img.data() + desc_bytes, prefix.data(), prefix.size() * 8);
+    unsigned char *d_blk = nullptr;
+    uint32_t *d_m = nullptr;
+    uint8_t *d_mf = nullptr;
+    if (max_total) {
+        MK_CUDA(cudaMallocAsync((void **)&d_blk, block_bytes, s));
+        MK_CUDA(cudaMemcpyAsync(d_blk, img.data(), block_bytes, cudaMemcpyHostToDevice, s));
+        MK_CUDA(cudaMallocAsync((void **)&d_m, max_total * 12, s));
+        MK_CUDA(cudaMallocAsync((void **)&d_mf, max_total, s));
+    }
+    mk_status st = MK_OK;
+    size_t pre = 0;
+    for (auto &r : runs) {
+        const uint32_t k = r.second - r.first;
+        const bool ins = h_reqs[r.first].kind == MK_REQ_INSERT;
+        const uint64_t total = prefix[pre + k];
+        if (k == 1) {
+            const mk_update_req &q = h_reqs[r.first];
+            st = ins ? insert_impl(g, q.d_src, q.d_dst, q.d_w, q.n, q.d_flags, s)
+                     : delete_impl(g, q.d_src, q.d_dst, q.n, q.d_flags, s);
+        } else if (total) {
+            const mk_update_req *dreq = reinterpret_cast<const mk_update_req *>(d_blk) + r.first;
+            const uint64_t *dpre = reinterpret_cast<const uint64_t *>(d_blk + desc_bytes) + pre;
+            bool want_flags = false;
+            for (uint32_t i = r.first; i < r.second; ++i)
+                want_flags |= h_reqs[i].d_flags != nullptr && h_reqs[i].n;
+            uint32_t *ms = d_m, *md = d_m + total, *mw = d_m + 2 * total;
+            const uint32_t grid = std::min<uint32_t>(grid_for(total, 256), num_sms() * 8);
+            st = timed(g, "update_gather", s, 1, [&]() {
+                k_gather_updates<<<grid, 256, 0, s>>>(dreq, dpre, k, total, ms, md, ins ? mw : nullptr);
+                return cudaSuccess;
+            });
+            if (st == MK_OK)
+                st = ins ? insert_impl(g, ms, md, mw, total, want_flags ? d_mf : nullptr, s)
+                         : delete_impl(g, ms, md, total, want_flags ? d_mf : nullptr, s);
+            if (st == MK_OK && want_flags)
+                st = timed(g, "update_scatter", s, 1, [&]() {
+                    k_scatter_flags<<<grid, 256, 0, s>>>(dreq, dpre, k, total, d_mf);
+                    return cudaSuccess;
+                });
+        } else {
+            g->change_seq++;
+        }
+        pre += k + 1;
+        if (st != MK_OK)
+            break;
+    }
+    if (d_blk)
+        cudaFreeAsync(d_blk, s);
+    if (d_m)
+        cudaFreeAsync(d_m, s);
+    if (d_mf)
+        cudaFreeAsync(d_mf, s);
+    return st;
 }
 
 } // extern "C"

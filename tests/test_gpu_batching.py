@@ -98,3 +98,76 @@ def test_every_tuned_shape_gives_identical_results(cuda_lib):
     dist, par = g.bfs(src)
     assert np.array_equal(mk.to_numpy_u32(dist), od) and np.array_equal(mk.to_numpy_u32(par), op)
     assert g.last_error() == mk.MK_OK
+
+
+def update_requests(G, seed, count=40):
+    """Mixed insert/delete requests with runs of one kind, empty requests,
+    pairs repeated inside and across requests, and deletes of pairs that an
+    earlier request of the same run inserted."""
+    rng = np.random.default_rng(seed)
+    out = []
+    recent = []
+    kinds = []
+    while len(kinds) < count:
+        kinds += [rng.choice(["insert", "delete"])] * int(rng.integers(1, 6))
+    for kind in kinds[:count]:
+        n = int(rng.choice([0, 1, 7, 64, 300, 2000]))
+        pick = rng.integers(0, len(G.src), n)
+        s = np.where(rng.random(n) < 0.5, G.src[pick], rng.integers(0, G.V, n)).astype(np.uint32)
+        d = np.where(rng.random(n) < 0.5, G.dst[pick], rng.integers(0, G.V, n)).astype(np.uint32)
+        if recent and n:
+            k = min(n // 3, len(recent[-1][0]))
+            s[:k], d[:k] = recent[-1][0][:k], recent[-1][1][:k]
+        if kind == "insert":
+            w = rng.integers(1, 100, n).astype(np.uint32)
+            out.append(("insert", s, d, w))
+        else:
+            out.append(("delete", s, d))
+        recent.append((s, d))
+    return out
+
+
+def test_update_multi_matches_one_call_per_request(cuda_lib):
+    """mk_update_multi (runs merged into one staged batch each) against one
+    mk_insert_batch / mk_delete_batch per request and the oracle: every
+    request's flags, the final edge set, and incremental SSSP/BFS/WCC after
+    the merged updates (the change log and the UpdateIterator markers)."""
+    torch, mk, G, g, o = _setup()
+    b = mk.bucket_rule(G.V, G.src, 0.7)
+    ref = mk.Graph(G.V, edge_capacity_hint=len(G.src) * 2, buckets=b)
+    ref.insert(G.src, G.dst, G.w)
+    ref.commit()
+    src = int(np.argmax(np.bincount(G.src, minlength=G.V)))
+    for x in (g, ref):
+        x.sssp(src)
+        x.bfs(src)
+        x.wcc()
+        x.commit()
+    for part in range(3):
+        reqs = update_requests(G, 20 + part)
+        flags = g.update_multi(reqs)
+        for req, f in zip(reqs, flags):
+            if req[0] == "insert":
+                rf = ref.insert(req[1], req[2], req[3])
+                of = o.insert(req[1], req[2], req[3])
+            else:
+                rf = ref.delete(req[1], req[2])
+                of = o.delete(req[1], req[2])
+            assert np.array_equal(f.cpu().numpy(), of) and torch.equal(f, rf)
+        for x in (g, ref):
+            d, p = x.sssp(src)
+            assert np.array_equal(mk.to_numpy_u32(d), o.sssp(src)[0])
+            assert np.array_equal(mk.to_numpy_u32(p), o.sssp(src)[1])
+            d, p = x.bfs(src)
+            assert np.array_equal(mk.to_numpy_u32(d), o.bfs(src)[0])
+            assert np.array_equal(mk.to_numpy_u32(x.wcc()), o.wcc())
+            x.commit()
+    es, ed, ew = g.export()
+    os_, od, ow = o.export()
+    assert np.array_equal(mk.to_numpy_u32(es), os_) and np.array_equal(mk.to_numpy_u32(ed), od)
+    assert np.array_equal(mk.to_numpy_u32(ew), ow)
+    assert g.last_error() == mk.MK_OK and ref.last_error() == mk.MK_OK
+    # no request flags asked for, and an empty list
+    g.update_multi(update_requests(G, 30), flags=False)
+    g.update_multi([])
+    assert g.last_error() == mk.MK_OK
