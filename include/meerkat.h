@@ -147,9 +147,14 @@ mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_
  *    MK_ERR_INVALID_ARG and enqueues nothing.
  *  - The staging scratch is one fixed 1 MiB device array inside the library
  *    (every GPU that loads the library holds it until the process exits).
- *    The first call on each device looks up the array's address
- *    (cudaGetSymbolAddress, no allocation); make that first call before any
- *    stream capture.
+ *    The first call on each device (with that device current) is its
+ *    set-up: it looks up the array's device address (cudaGetSymbolAddress),
+ *    which may make the runtime load the library's device code there, so
+ *    make that first call before any stream capture.  The set-up is
+ *    repeated if the device's context has changed since (cudaDeviceReset).
+ *  - With profiling on (mk_profile_enable) its kernels are counted by
+ *    mk_launch_count but not timed: the timing hook creates events and
+ *    grows a host list, which this call must not do.
  *  - Every call on a device shares the array; each call clears the part
  *    that must start empty (the hash set) on its stream.  Two calls whose work
  *    overlaps on the GPU (different streams, or different graphs at the same

@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__
 
 namespace {
 
-constexpr uint64_t kNoAllocMaxBatch = 1ull << 16;
+constexpr uint64_t kNoAllocMaxBatch = MK_NOALLOC_MAX_BATCH;
+static_assert(kNoAllocMaxBatch == (1ull << 16), "the scratch layout below is sized for 2^16 edges");
 constexpr uint64_t kTable = 2 * kNoAllocMaxBatch;            // hash-set entries (a power of two)
 constexpr size_t kTposBytes = kTable * 4;
 constexpr size_t kEdgeBytes = kNoAllocMaxBatch * 4;
@@ -44,37 +45,74 @@ constexpr size_t kScratchBytes = kTposBytes + 2 * kEdgeBytes; // 1 MiB
 // The scratch of every call on a device.  Device code could name it
 // directly; host code must not pass `g_noalloc_scratch` itself to a kernel
 // (on the host it is only a stand-in symbol), so its device address is looked
-// up once per device with cudaGetSymbolAddress.  Every GPU that loads this
-// library holds the array until the process exits.
+// up with cudaGetSymbolAddress at set-up, once per device (with that device
+// current), and that address is passed to the kernels.  Every GPU that
+// loads this library holds the array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
+typedef int (*CtxGetCurrentFn)(void **ctx);
+
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
-bool g_setup_done[kMaxDevices] = {};
+struct DeviceSetup {
+    bool done = false;
+    void *ctx = nullptr;          // context the address belongs to
+    unsigned char *addr = nullptr;
+};
+DeviceSetup g_setup[kMaxDevices];
 
-// Per-device set-up, done by the first call on each device (with that device
-// current): the array's device address.  It allocates nothing.
-mk_status setup_device(unsigned char **base)
+// The calling thread's current context, from the driver's cuCtxGetCurrent
+// fetched through the runtime (so the library needs no link against the
+// driver library); nullptr if it cannot be had.
+void *current_context()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+        cudaGetLastError();
+    }
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0)
+        ctx = nullptr;
+    return ctx;
+}
+
+// The array's device address on the current device.  The set-up (the
+// lookup) runs on the first call on each device, and again if that
+// device's context is no longer the one the address was taken in (after a
+// cudaDeviceReset the module, and the array, may be loaded elsewhere).  The
+// first lookup may make the runtime load this library's device code on the
+// device, which is why the first call on a device belongs before any stream
+// capture; nothing else here allocates.
+mk_status scratch_base(unsigned char **base)
 {
     int dev = 0;
     MK_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices)
         return MK_ERR_INTERNAL;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_setup_done[dev]) {
+    DeviceSetup &d = g_setup[dev];
+    void *ctx = current_context();
+    if (!d.done || ctx != d.ctx) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return MK_ERR_CUDA;
         }
-        g_scratch_addr[dev] = (unsigned char *)p;
-        g_setup_done[dev] = true;
+        d.addr = (unsigned char *)p;
+        d.ctx = current_context(); // the lookup may have created the context
+        d.done = true;
     }
-    *base = g_scratch_addr[dev];
+    *base = d.addr;
     return MK_OK;
 }
 
@@ -89,7 +127,7 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = nullptr;
-    MK_TRY(setup_device(&base));
+    MK_TRY(scratch_base(&base));
     g->change_seq++;
     if (n == 0)
         return MK_OK;
@@ -102,16 +140,16 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
     MK_CUDA(cudaMemsetAsync(tpos, 0xFF, kTposBytes, s));
     if (d_inserted)
         MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
-    MK_TRY(timed(g, "stage_dedup", s, 1, [&]() {
-        k_dedup<<<grid_for(n, 256), 256, 0, s>>>(d_src, d_dst, d_w, n, g->v.V, tpos, (uint32_t)(kTable - 1), slot,
-                                                 g->d_state);
-        return cudaSuccess;
-    }));
+    // launched without the profiling hook (which creates events and grows
+    // a host vector): with profiling on, these kernels are counted in the
+    // launch total but missing from the per-kernel times
+    k_dedup<<<grid_for(n, 256), 256, 0, s>>>(d_src, d_dst, d_w, n, g->v.V, tpos, (uint32_t)(kTable - 1), slot,
+                                             g->d_state);
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
-    return timed(g, "insert", s, 2, [&]() {
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, tpos, slot, d_inserted, max_hops, cand);
-        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, cand, n);
-        return cudaSuccess;
-    });
+    k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, tpos, slot, d_inserted, max_hops, cand);
+    k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, cand, n);
+    g->launches += 3;
+    MK_CUDA(cudaGetLastError());
+    return MK_OK;
 }

@@ -7,8 +7,9 @@ start-up).  For them the library offers an insert that stages its batch in a
 fixed device array instead of growing buffers with cudaMalloc.  This test
 calls it through the C ABI and checks, on two calls in a row, that its flags
 and the resulting edge set are identical to those of the ordinary insert on a
-twin graph; it also checks that an oversized batch is refused.  It lives in a
-file of its own that pytest collects last.
+twin graph, that the device's free memory and the graph's own device bytes
+are unchanged across the two calls, and that an oversized batch is refused.
+It lives in a file of its own that pytest collects last.
 """
 import ctypes
 
@@ -35,24 +36,40 @@ def test_no_alloc_insert_matches_insert_batch(cuda_lib):
         g.commit()
     rng = np.random.default_rng(7)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for n in (5003, MK_NOALLOC_MAX_BATCH):  # two calls in a row, the second at the limit
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    # two calls in a row, the second at the limit: inputs, outputs and the
+    # ordinary insert's results on the twin graph are made first, so that
+    # nothing else allocates while the allocation-free calls run
+    calls = []
+    for n in (5003, MK_NOALLOC_MAX_BATCH):
         s = rng.integers(0, w.V, n).astype(np.uint32)
         d = rng.integers(0, w.V, n).astype(np.uint32)
         ww = rng.integers(1, 100, n).astype(np.uint32)
         fa = a.insert(s, d, ww).cpu().numpy()
-        ts, td, tw = (mk.to_device_u32(x) for x in (s, d, ww))
-        fb = torch.empty(n, dtype=torch.uint8, device="cuda")
-        rc = lib.mk_insert_batch_noalloc(b.handle, ctypes.c_void_p(ts.data_ptr()), ctypes.c_void_p(td.data_ptr()),
-                                         ctypes.c_void_p(tw.data_ptr()), n, ctypes.c_void_p(fb.data_ptr()), stream)
+        calls.append((n, fa, [mk.to_device_u32(x) for x in (s, d, ww)], torch.empty(n, dtype=torch.uint8,
+                                                                                   device="cuda")))
+    ea = a.export()
+    # set-up call (the first on this device), then the two compared calls
+    one = mk.to_device_u32([0])
+    assert lib.mk_insert_batch_noalloc(b.handle, P(one), P(one), None, 0, None, stream) == mk.MK_OK
+    bytes0 = b.stats()["device_bytes"]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for n, fa, (ts, td, tw), fb in calls:
+        rc = lib.mk_insert_batch_noalloc(b.handle, P(ts), P(td), P(tw), n, P(fb), stream)
         assert rc == mk.MK_OK
-        assert b.last_error() == mk.MK_OK and a.last_error() == mk.MK_OK
+        assert b.last_error() == mk.MK_OK
         assert np.array_equal(fa, fb.cpu().numpy())
-        ea, eb = a.export(), b.export()
-        for x, y in zip(ea, eb):
-            assert torch.equal(x, y)
+    torch.cuda.synchronize()
+    # no device memory came or went, and the graph holds what it held
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert b.stats()["device_bytes"] == bytes0
+    assert a.last_error() == mk.MK_OK
+    eb = b.export()
+    for x, y in zip(ea, eb):
+        assert torch.equal(x, y)
     big = torch.zeros(MK_NOALLOC_MAX_BATCH + 1, dtype=torch.int32, device="cuda")
-    rc = lib.mk_insert_batch_noalloc(b.handle, ctypes.c_void_p(big.data_ptr()), ctypes.c_void_p(big.data_ptr()),
-                                     None, MK_NOALLOC_MAX_BATCH + 1, None, stream)
+    rc = lib.mk_insert_batch_noalloc(b.handle, P(big), P(big), None, MK_NOALLOC_MAX_BATCH + 1, None, stream)
     assert rc == mk.MK_ERR_INVALID_ARG
     a.close()
     b.close()
