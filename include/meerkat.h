@@ -351,6 +351,53 @@ mk_status mk_incr_bfs(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *
  * vertex's component. */
 mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream);
 
+/* ------------------------------------------------------------- analytics */
+
+/* PageRank (paper, Sec. "Dynamic PageRank", Algorithm "Page Rank - Static /
+ * Incremental / Decremental", Eq. 1): super-steps PR[v] = (1 - d) / V + d *
+ * (sum over live edges u -> v of PR[u] / out(u) + T / V), where T is the
+ * rank held by vertices without out-edges (the paper's teleport term), until
+ * the L1 distance between two successive rank vectors is <= eps or after
+ * max_iter super-steps.  d_pr (V floats, device): with warm_start = 0 the
+ * ranks start at 1 / V (static); with warm_start != 0 they start from
+ * d_pr's contents (the ranks before the last batch: the incremental and
+ * decremental cases); on return d_pr holds the ranks.  Ranks are kept as
+ * 64-bit fixed-point values (scale 2^48) and the contributions are pushed
+ * along out-edges with integer atomics, so the result does not depend on the
+ * order of the atomics; each super-step's rounding is below 2^-48 per term.
+ * damping in (0, 1), eps > 0, max_iter >= 1.  *h_iters / *h_delta
+ * (nullable, host): super-steps run and the last L1 delta.  Synchronises
+ * `stream` once per super-step (the host reads the delta); work arrays are
+ * stream-ordered allocations freed before the call returns. */
+mk_status mk_pagerank(mk_graph *g, float *d_pr, int warm_start, float damping, float eps, uint32_t max_iter,
+                      uint32_t *h_iters, float *h_delta, void *stream);
+
+/* Triangle counting on undirected graphs stored with both directions of
+ * every edge and no self-loops (paper, Sec. "Dynamic Triangle Counting").
+ * mk_tc_count is the paper's Count kernel: *d_total (device, one uint64)
+ * += sum over the n edges (d_src[i], d_dst[i]) of |N_g1(src) ∩ N_g2(dst)|
+ * (the walk goes over the side with fewer buckets; the sum is the same).
+ * g1 and g2 must have the same V. */
+mk_status mk_tc_count(mk_graph *g1, mk_graph *g2, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                      unsigned long long *d_total, void *stream);
+
+/* Static count: Count(g, g, every live edge) / 6 into *h_triangles (host).
+ * Synchronises `stream`. */
+mk_status mk_tc_static(mk_graph *g, uint64_t *h_triangles, void *stream);
+
+/* Change in the triangle count after a batch (paper, Algorithms "Triangle
+ * Counting - Incremental / Decremental", inclusion-exclusion): g_post is the
+ * graph after the batch, g_upd a graph holding exactly the batch's edges,
+ * and (d_src, d_dst, n) those same edges, both directions of each, every one
+ * actually inserted (deletion = 0) or actually deleted (deletion != 0).
+ * With S1 = Count(g_post, g_post), S2 = Count(g_post, g_upd) and S3 =
+ * Count(g_upd, g_upd) over the batch, *h_delta (host) = S1/2 - S2/2 + S3/6
+ * new triangles, or -(S1/2 + S2/2 + S3/6) for a deletion.  Synchronises
+ * `stream`.  MK_ERR_INTERNAL if a count is not divisible as the formula
+ * requires (the graphs break the stated conditions). */
+mk_status mk_tc_update(mk_graph *g_post, mk_graph *g_upd, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                       int deletion, int64_t *h_delta, void *stream);
+
 /* -------------------------------------------------------- learned sizing */
 /*
  * Learned slab sizing.  The paper fixes each vertex's bucket count a priori

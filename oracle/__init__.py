@@ -12,7 +12,8 @@ recomputed from scratch after every batch.
 * ``query(src, dst) -> (bitmap, weights)``;
 * ``export() -> (src, dst, w)`` sorted by (src, dst);
 * ``bfs(source)`` / ``sssp(source) -> (dist, parent)`` with the min-id tight
-  parent; ``wcc() -> labels`` (smallest vertex id per component).
+  parent; ``wcc() -> labels`` (smallest vertex id per component);
+* ``pagerank() -> (ranks, iterations)``, ``triangles() -> count``.
 """
 from __future__ import annotations
 
@@ -64,6 +65,11 @@ def _load():
             lib.orc_sssp.restype = ctypes.c_int
             lib.orc_sssp.argtypes = [ctypes.c_void_p, ctypes.c_uint32, _u32p, _u32p]
             lib.orc_wcc.argtypes = [ctypes.c_void_p, _u32p]
+            lib.orc_pagerank.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         _u32p]
+            lib.orc_triangles.restype = ctypes.c_uint64
+            lib.orc_triangles.argtypes = [ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -143,6 +149,19 @@ class OracleGraph:
         lab = np.empty(self.V, np.uint32)
         self._lib.orc_wcc(self._h, _p(lab))
         return lab
+
+    def pagerank(self, damping=0.85, eps=1e-12, max_iter=1000, init=None):
+        """(ranks as float64, iterations run)."""
+        dp = ctypes.POINTER(ctypes.c_double)
+        out = np.empty(self.V, np.float64)
+        it = np.zeros(1, np.uint32)
+        ini = None if init is None else np.ascontiguousarray(init, dtype=np.float64)
+        self._lib.orc_pagerank(self._h, damping, eps, max_iter, None if ini is None else ini.ctypes.data_as(dp),
+                               out.ctypes.data_as(dp), _p(it))
+        return out, int(it[0])
+
+    def triangles(self) -> int:
+        return int(self._lib.orc_triangles(self._h))
 
 
 def bitmap_to_bool(bitmap: np.ndarray, n: int) -> np.ndarray:

@@ -26,9 +26,17 @@
 //  * Weakly connected components (Sec. "Incremental WCC"): vertices joined by
 //    a path that ignores edge direction share a label; the label is the
 //    smallest vertex id of the component.
+//  * PageRank (Sec. "Dynamic PageRank", Eq. 1 and the teleport term of its
+//    algorithm): power iteration in double precision, PR[v] = (1 - d) / N +
+//    d * (sum over edges u -> v of PR[u] / out(u) + T / N) with T the rank of
+//    the vertices without out-edges, until the L1 change is <= eps.
+//  * Triangles (Sec. "Dynamic Triangle Counting"): the number of vertex
+//    triples pairwise joined by an edge of either direction (self-loops
+//    ignored).
 //
 // Vertex ids are 32-bit; the value 0xFFFFFFFF stands for INF / INVALID.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <functional>
@@ -273,6 +281,75 @@ void orc_wcc(void *h, uint32_t *label)
     }
     for (uint32_t v = 0; v < g->V; ++v)
         label[v] = smallest[find(v)];
+}
+
+// PageRank by power iteration (see the header).  init (nullable): starting
+// ranks, else 1 / V each.  Writes V ranks to out and the number of
+// iterations run to *iters.
+void orc_pagerank(void *h, double damping, double eps, uint32_t max_iter, const double *init, double *out,
+                  uint32_t *iters)
+{
+    OracleGraph *g = static_cast<OracleGraph *>(h);
+    const uint32_t V = g->V;
+    std::vector<uint32_t> outdeg(V, 0);
+    for (const auto &e : g->edges)
+        outdeg[e.first >> 32]++;
+    std::vector<double> pr(V), next(V);
+    for (uint32_t v = 0; v < V; ++v)
+        pr[v] = init ? init[v] : 1.0 / V;
+    uint32_t it = 0;
+    while (it < max_iter) {
+        double teleport = 0;
+        for (uint32_t v = 0; v < V; ++v)
+            if (outdeg[v] == 0)
+                teleport += pr[v];
+        std::vector<double> sum(V, 0.0);
+        for (const auto &e : g->edges) {
+            const uint32_t u = uint32_t(e.first >> 32), v = uint32_t(e.first);
+            sum[v] += pr[u] / outdeg[u];
+        }
+        double delta = 0;
+        for (uint32_t v = 0; v < V; ++v) {
+            next[v] = (1.0 - damping) / V + damping * (sum[v] + teleport / V);
+            delta += std::fabs(next[v] - pr[v]);
+        }
+        pr.swap(next);
+        ++it;
+        if (delta <= eps)
+            break;
+    }
+    for (uint32_t v = 0; v < V; ++v)
+        out[v] = pr[v];
+    *iters = it;
+}
+
+// Triangles of the undirected simple graph underlying the edge set: each
+// triple u < v < w with all three pairs adjacent is counted once.
+uint64_t orc_triangles(void *h)
+{
+    OracleGraph *g = static_cast<OracleGraph *>(h);
+    std::vector<std::vector<uint32_t>> nb(g->V);
+    for (const auto &e : g->edges) {
+        const uint32_t u = uint32_t(e.first >> 32), v = uint32_t(e.first);
+        if (u == v)
+            continue;
+        nb[u].push_back(v);
+        nb[v].push_back(u);
+    }
+    for (auto &x : nb) {
+        std::sort(x.begin(), x.end());
+        x.erase(std::unique(x.begin(), x.end()), x.end());
+    }
+    uint64_t count = 0;
+    for (uint32_t u = 0; u < g->V; ++u)
+        for (uint32_t v : nb[u]) {
+            if (v <= u)
+                continue;
+            for (uint32_t w : nb[v])
+                if (w > v && std::binary_search(nb[u].begin(), nb[u].end(), w))
+                    ++count;
+        }
+    return count;
 }
 
 } // extern "C"

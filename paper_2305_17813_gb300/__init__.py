@@ -167,6 +167,35 @@ class Graph:
         check(self._lib.mk_incr_wcc(self._h, _ptr(lab), _stream(stream)), "mk_incr_wcc")
         return lab
 
+    def pagerank(self, pr=None, damping: float = 0.85, eps: float = 1e-7, max_iter: int = 100, stream=None):
+        """PageRank (mk_pagerank).  pr: None for the static start (1 / V),
+        or a float32 CUDA tensor of V ranks to start from (updated in place).
+        Returns (ranks, super-steps, last L1 delta)."""
+        torch = _torch()
+        warm = pr is not None
+        if pr is None:
+            pr = torch.empty(self.V, dtype=torch.float32, device=self.device)
+        it, delta = ctypes.c_uint32(), ctypes.c_float()
+        check(self._lib.mk_pagerank(self._h, _ptr(pr), 1 if warm else 0, damping, eps, max_iter, ctypes.byref(it),
+                                    ctypes.byref(delta), _stream(stream)), "mk_pagerank")
+        return pr, it.value, delta.value
+
+    def triangles(self, stream=None) -> int:
+        """Triangles of the undirected graph stored with both directions."""
+        v = ctypes.c_uint64()
+        check(self._lib.mk_tc_static(self._h, ctypes.byref(v), _stream(stream)), "mk_tc_static")
+        return v.value
+
+    def triangle_delta(self, upd: "Graph", src, dst, deletion: bool, stream=None) -> int:
+        """Change in the triangle count for a batch whose edges (both
+        directions, all actually applied) are (src, dst) and are exactly the
+        edges of `upd`; self is the graph after the batch (mk_tc_update)."""
+        s, d = to_device_u32(src), to_device_u32(dst)
+        out = ctypes.c_int64()
+        check(self._lib.mk_tc_update(self._h, upd.handle, _ptr(s), _ptr(d), s.numel(), 1 if deletion else 0,
+                                     ctypes.byref(out), _stream(stream)), "mk_tc_update")
+        return out.value
+
     # ------------------------------------------------------- inspection
     def export(self, stream=None):
         """Live edges sorted by (src, dst) as three int32 tensors (uint32 bits)."""

@@ -133,6 +133,11 @@ SIGNATURES = {
     "mk_launch_count": (_U64, [_P]),
     "mk_version": (ctypes.c_char_p, []),
     "mk_debug_set": (_INT, [_P, _INT, _U64]),
+    "mk_pagerank": (_INT, [_P, _P, _INT, ctypes.c_float, ctypes.c_float, _U32, ctypes.POINTER(_U32),
+                           ctypes.POINTER(ctypes.c_float), _P]),
+    "mk_tc_count": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),
+    "mk_tc_static": (_INT, [_P, ctypes.POINTER(_U64), _P]),
+    "mk_tc_update": (_INT, [_P, _P, _P, _P, _U64, _INT, ctypes.POINTER(ctypes.c_int64), _P]),
     "mk_server_create": (_INT, [_P, _U32, _U32, ctypes.POINTER(_P)]),
     "mk_server_destroy": (_INT, [_P]),
     "mk_server_submit": (_INT, [_P, ctypes.POINTER(mk_request)]),

@@ -304,3 +304,87 @@ def test_sharded_cpu_baseline_matches_the_oracle(threads):
             assert np.array_equal(hit.astype(bool), oracle.bitmap_to_bool(obm, n))
             assert np.array_equal(w, ow)
         assert p.num_edges == o.num_edges
+
+
+def _dense_pagerank(V, s, d, damping):
+    """Closed form of the PageRank fixpoint: (I - d M) x = (1 - d) / V * 1,
+    M[v, u] = 1 / out(u) per edge u -> v, and 1 / V in every row for a
+    column u without out-edges (the teleport term)."""
+    M = np.zeros((V, V))
+    out = np.bincount(s, minlength=V)
+    for u, v in zip(s, d):
+        M[v, u] += 1.0 / out[u]
+    M[:, out == 0] = 1.0 / V
+    return np.linalg.solve(np.eye(V) - damping * M, np.full(V, (1 - damping) / V))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_pagerank_matches_the_closed_form(seed):
+    rng = _rng(70 + seed)
+    V = int(rng.integers(3, 41))
+    n = int(rng.integers(1, 4 * V))
+    s = rng.integers(0, V, n).astype(np.uint32)
+    d = rng.integers(0, V, n).astype(np.uint32)
+    g = oracle.OracleGraph(V)
+    g.insert(s, d)
+    es, ed, _ = g.export()
+    for damping in (0.85, 0.5):
+        pr, it = g.pagerank(damping=damping, eps=1e-15, max_iter=5000)
+        assert np.allclose(pr, _dense_pagerank(V, es, ed, damping), rtol=0, atol=1e-12)
+        assert abs(pr.sum() - 1.0) < 1e-12
+    # a warm start at the fixpoint stops after one step
+    pr, _ = g.pagerank(eps=1e-14, max_iter=5000)
+    _, it = g.pagerank(eps=1e-12, init=pr)
+    assert it == 1
+
+
+def test_pagerank_of_a_cycle_is_uniform_and_a_sink_takes_the_teleport():
+    g = oracle.OracleGraph(5)
+    g.insert([0, 1, 2, 3, 4], [1, 2, 3, 4, 0])
+    pr, _ = g.pagerank()
+    assert np.allclose(pr, 0.2, atol=1e-13)
+    # 0 -> 1 and a sink 1: PR1 = (1-d)/2 + d (PR0 + PR1/2), PR0 = (1-d)/2 + d PR1/2
+    g = oracle.OracleGraph(2)
+    g.insert([0], [1])
+    pr, _ = g.pagerank(damping=0.85)
+    p1 = (1 - 0.85) / 2 + 0.85 * (pr[0] + pr[1] / 2)
+    assert np.isclose(pr[1], p1, atol=1e-13) and np.isclose(pr.sum(), 1.0, atol=1e-13)
+    assert np.isclose(pr[0], 0.15 / 2 + 0.85 * pr[1] / 2, atol=1e-13)
+
+
+def test_triangles_closed_forms_and_brute_force():
+    # complete graph K_n (one direction only: the count ignores direction)
+    for n in (3, 4, 7):
+        g = oracle.OracleGraph(n)
+        s, d = np.triu_indices(n, 1)
+        g.insert(s.astype(np.uint32), d.astype(np.uint32))
+        assert g.triangles() == n * (n - 1) * (n - 2) // 6
+    # wheel: hub 0 joined to a cycle of n rim vertices has n triangles
+    n = 9
+    rim = np.arange(1, n + 1)
+    g = oracle.OracleGraph(n + 1)
+    g.insert(np.zeros(n, np.uint32), rim.astype(np.uint32))
+    g.insert(rim.astype(np.uint32), (rim % n + 1).astype(np.uint32))
+    g.insert([3], [3])  # a self-loop adds nothing
+    assert g.triangles() == n
+    # a grid and a bipartite graph have none
+    g = oracle.OracleGraph(64)
+    gs, gd = synth.grid_pairs(8, 8)
+    g.insert(gs, gd)
+    assert g.triangles() == 0
+    # brute force over all triples on random small graphs, both directions
+    for seed in range(5):
+        rng = _rng(90 + seed)
+        V = int(rng.integers(4, 30))
+        n = int(rng.integers(0, 3 * V))
+        s = rng.integers(0, V, n).astype(np.uint32)
+        d = rng.integers(0, V, n).astype(np.uint32)
+        g = oracle.OracleGraph(V)
+        g.insert(s, d)
+        A = np.zeros((V, V), bool)
+        A[s, d] = True
+        A |= A.T
+        np.fill_diagonal(A, False)
+        brute = sum(1 for a in range(V) for b in range(a + 1, V) for c in range(b + 1, V)
+                    if A[a, b] and A[b, c] and A[a, c])
+        assert g.triangles() == brute
