@@ -75,11 +75,14 @@ def parse_args(argv=None):
     p.add_argument("--no-solo", action="store_true", help="skip the steps that time every kernel alone")
     p.add_argument("--no-per-batch", action="store_true",
                    help="skip the steps at the workload's other batch sizes (2^12, 2^16, 2^22)")
-    p.add_argument("--workload", choices=["powerlaw", "growth", "served", "road"], default="powerlaw",
+    p.add_argument("--workload", choices=["powerlaw", "growth", "served", "road", "analytics", "buckets", "l2"],
+                   default="powerlaw",
                    help="powerlaw: the benchmark line; growth: the learned-sizing study on the R-MAT "
                         "scale-22 growth stream; served: plain vs continuous-batching serving on the R-MAT "
-                        "scale-21 request stream; road: incremental SSSP on the 4096^2 road-like grid "
-                        "(each prints its own JSON line)")
+                        "scale-21 request stream; road: incremental SSSP on the 4096^2 road-like grid; "
+                        "analytics: PageRank and triangle counting; buckets: the power-law step with the "
+                        "load-factor bucket rule against one bucket per vertex (hashing off); l2: the step "
+                        "with L2 persistence windows over parts of the store (each prints its own JSON line)")
     return p.parse_args(argv)
 
 
@@ -289,7 +292,7 @@ class StepRunner:
     benchmark times (see the module docstring), with per-step output buffers
     so that every timed step can be checked afterwards."""
 
-    def __init__(self, args, G, source, capacity_edges, device):
+    def __init__(self, args, G, source, capacity_edges, device, buckets=None):
         import torch
 
         import paper_2305_17813_gb300 as mk
@@ -306,7 +309,8 @@ class StepRunner:
         self.sidep = ctypes.c_void_p(self.side.cuda_stream)
         E = len(G.src)
         src_d = self.u32(G.src)
-        buckets = mk.bucket_rule(G.V, src_d, 0.7)
+        if buckets is None:
+            buckets = mk.bucket_rule(G.V, src_d, 0.7)
         self.g = mk.Graph(G.V, edge_capacity_hint=capacity_edges, buckets=buckets)
         self.h = self.g.handle
         chunk = 1 << 22
@@ -710,19 +714,21 @@ def run_e2e(R, batches, B, dist, units_total):
 
 # ------------------------------------------------------- learned sizing
 
-def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.7, keep_graphs=False):
+def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.7, keep_graphs=False, repeats=1):
     """Learned slab sizing on a growth stream S (synth.growth_stream).
 
     A graph sized by the load-factor rule at the initial load runs batches
     1..split while a degree trace records every applied insert and delete.
     The network is trained on (features at batch t, edges gained per batch
     over the next `horizon` batches) for every t with a full window, then
-    predicts each vertex's growth over the remaining batches.  Two graphs are
-    rebuilt from the live edges at `split`: one with the learned bucket
-    counts, one with the load-factor rule on the current degrees (the baseline
-    the learned counts are measured against).
-    Both run the remaining batches; the insert time, a query batch over live
-    edges, chain lengths and slabs walked per query are compared."""
+    predicts each vertex's growth over the remaining batches.  Three graphs
+    are rebuilt from the live edges at `split`: one with the learned bucket
+    counts, one with the load-factor rule on the current degrees, and one
+    with the rule on the initial load's degrees (the paper's a priori
+    sizing).  Each runs the remaining batches `repeats` times on a fresh
+    graph; the insert rate, a query batch over live edges (mean and spread
+    over the repeats), chain lengths and slabs walked per query are
+    compared, and a gain counts only when it exceeds the summed spreads."""
     import torch
 
     import paper_2305_17813_gb300 as mk
@@ -769,49 +775,73 @@ def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.
     out = {"vertices": V, "batches": n_batches, "split": split, "horizon": horizon, "train_samples": int(X.shape[0]),
            "train_losses": [round(x, 5) for x in losses], "train_s": round(train_s, 2), "source": source}
     graphs = []
-    rng = np.random.default_rng(7)
-    for name, bk in (("learned", learned_b), ("rule", rule_b)):
-        gg = mk.Graph(V, edge_capacity_hint=2 * total_edges, buckets=bk)
-        gg.insert(es, ed, ew, flags=False)
-        gg.commit()
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ins_ms = 0.0
-        n_ins = 0
-        for k in range(split, n_batches):
-            b = S.batches[k]
-            si, di, wi = u(b.ins_src), u(b.ins_dst), u(b.ins_w)
-            sd, dd = u(b.del_src), u(b.del_dst)
-            ev[0].record()
-            gg.insert(si, di, wi, flags=False)
-            ev[1].record()
-            torch.cuda.synchronize()
-            ins_ms += ev[0].elapsed_time(ev[1])
-            n_ins += len(b.ins_src)
-            gg.delete(sd, dd, flags=False)
+    # three layouts rebuilt from the same live edges at `split`: the learned
+    # bucket counts, the load-factor rule on the current degrees, and the
+    # rule on the initial load's degrees (the paper's a priori sizing, which
+    # the first graph ran with); each replays the remaining batches
+    # `repeats` times (a fresh graph each time), so the spread of the rates
+    # is measured
+    for name, bk in (("learned", learned_b), ("rule", rule_b), ("a_priori", b0)):
+        ins_rates, q_rates = [], []
+        for rep in range(repeats):
+            rng = np.random.default_rng(7)
+            gg = mk.Graph(V, edge_capacity_hint=2 * total_edges, buckets=bk)
+            gg.insert(es, ed, ew, flags=False)
             gg.commit()
-        ls, ld, _ = gg.export()
-        pick = torch.from_numpy(rng.integers(0, ls.numel(), min(ls.numel(), 1 << 20)))
-        qs, qd = ls[pick.cuda()].contiguous(), ld[pick.cuda()].contiguous()
-        gg.counters(reset=True)
-        q_times = []
-        for _ in range(7):
-            ev[0].record()
-            gg.query(qs, qd, weights=False)
-            ev[1].record()
             torch.cuda.synchronize()
-            q_times.append(ev[0].elapsed_time(ev[1]))
-        q_ms = statistics.median(q_times)
-        ctr = gg.counters()
-        st = gg.stats()
-        out[name] = {"lists": int(st["lists"]), "chain_mean": round(st["chain_mean"], 4), "chain_max": int(st["chain_max"]),
-                     "device_bytes": int(st["device_bytes"]),
-                     "query_slabs_per_query": round(ctr["query_slabs"] / 7 / qs.numel(), 4),
-                     "insert_medges_s": round(n_ins / ins_ms / 1e3, 1), "query_medges_s": round(qs.numel() / q_ms / 1e3, 1)}
-        if keep_graphs:
-            graphs.append(gg)
-        else:
-            gg.close()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ins_ms = 0.0
+            n_ins = 0
+            for k in range(split, n_batches):
+                b = S.batches[k]
+                si, di, wi = u(b.ins_src), u(b.ins_dst), u(b.ins_w)
+                sd, dd = u(b.del_src), u(b.del_dst)
+                ev[0].record()
+                gg.insert(si, di, wi, flags=False)
+                ev[1].record()
+                torch.cuda.synchronize()
+                ins_ms += ev[0].elapsed_time(ev[1])
+                n_ins += len(b.ins_src)
+                gg.delete(sd, dd, flags=False)
+                gg.commit()
+            ls, ld, _ = gg.export()
+            pick = torch.from_numpy(rng.integers(0, ls.numel(), min(ls.numel(), 1 << 20)))
+            qs, qd = ls[pick.cuda()].contiguous(), ld[pick.cuda()].contiguous()
+            gg.counters(reset=True)
+            q_times = []
+            for _ in range(7):
+                ev[0].record()
+                gg.query(qs, qd, weights=False)
+                ev[1].record()
+                torch.cuda.synchronize()
+                q_times.append(ev[0].elapsed_time(ev[1]))
+            q_ms = statistics.median(q_times)
+            ins_rates.append(n_ins / ins_ms / 1e3)
+            q_rates.append(qs.numel() / q_ms / 1e3)
+            if rep == 0:
+                ctr = gg.counters()
+                st = gg.stats()
+                out[name] = {"lists": int(st["lists"]), "chain_mean": round(st["chain_mean"], 4),
+                             "chain_max": int(st["chain_max"]), "device_bytes": int(st["device_bytes"]),
+                             "query_slabs_per_query": round(ctr["query_slabs"] / 7 / qs.numel(), 4)}
+            if keep_graphs and rep == 0 and name != "a_priori":
+                graphs.append(gg)
+            else:
+                gg.close()
+        out[name].update({
+            "repeats": repeats,
+            "insert_medges_s": round(statistics.mean(ins_rates), 1),
+            "insert_medges_s_std": round(statistics.pstdev(ins_rates), 1),
+            "query_medges_s": round(statistics.mean(q_rates), 1),
+            "query_medges_s_std": round(statistics.pstdev(q_rates), 1),
+            "insert_medges_s_all": [round(x, 1) for x in ins_rates],
+            "query_medges_s_all": [round(x, 1) for x in q_rates]})
+    for base in ("rule", "a_priori"):
+        for op in ("insert", "query"):
+            m_l, m_b = out["learned"][op + "_medges_s"], out[base][op + "_medges_s"]
+            spread = out["learned"][op + "_medges_s_std"] + out[base][op + "_medges_s_std"]
+            out["learned_vs_%s_%s" % (base, op)] = {"gain": round(m_l / m_b - 1.0, 4),
+                                                    "beyond_spread": bool(m_l - m_b > spread)}
     model.close()
     if keep_graphs:
         out["graphs"] = graphs
@@ -1232,20 +1262,193 @@ def run_growth(args):
     t0 = time.time()
     S = synth.growth_stream(scale=22, draws=1 << 26, n_batches=64)
     gen_s = time.time() - t0
-    res = growth_experiment(S, split=32, horizon=8, epochs=20)
+    res = growth_experiment(S, split=32, horizon=8, epochs=20, repeats=5)
     res.update({"workload": "R-MAT scale 22 growth stream (67,108,864 draws; first 50% loaded; 64 insert batches "
                             "with preferential source skew 0.5, each followed by 10% deletes); network trained on "
-                            "batches 1-32, graphs rebuilt at batch 32 with learned vs load-factor bucket counts",
+                            "batches 1-32, graphs rebuilt at batch 32 with learned, load-factor (current degrees) and a "
+                            "priori (initial degrees) bucket counts, 5 repeats each",
                 "gen_s": round(gen_s, 1)})
     return res
+
+
+def run_analytics(args):
+    """PageRank on the power-law graph (static, then warm-started after one
+    2^20 update batch) and triangle counting on an undirected R-MAT graph
+    (static, then the inclusion-exclusion update after a batch of new
+    undirected edges, against a static recount)."""
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+    import synth
+
+    torch.cuda.set_device(0)
+    out = {"workload": "analytics"}
+    G = synth.powerlaw_graph(scale=args.scale, draws=args.draws)
+    S = synth.PowerlawStream(G, max_batch=args.batch)
+    g = mk.Graph(G.V, edge_capacity_hint=len(G.src) + 4 * args.batch, buckets=mk.bucket_rule(G.V, G.src, 0.7))
+    g.insert(G.src, G.dst, G.w, flags=False)
+    g.commit()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed_ms(fn):
+        torch.cuda.synchronize()
+        ev[0].record()
+        r = fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), r
+
+    timed_ms(lambda: g.pagerank(eps=1e-7, max_iter=100))  # warm-up (module load, pools)
+    st = g.stats()
+    g.profile(True)
+    g.profile_read()
+    ms_static, (pr, it_static, delta) = timed_ms(lambda: g.pagerank(eps=1e-7, max_iter=100))
+    prof = g.profile_read()
+    g.profile(False)
+    bt = S.batch(args.batch)
+    g.insert(bt.ins_src, bt.ins_dst, bt.ins_w, flags=False)
+    g.delete(bt.del_src, bt.del_dst, flags=False)
+    g.commit()
+    ms_warm, (_, it_warm, _) = timed_ms(lambda: g.pagerank(pr, eps=1e-7, max_iter=100))
+    ms_cold, (_, it_cold, _) = timed_ms(lambda: g.pagerank(eps=1e-7, max_iter=100))
+    n_step, t_step = prof.get("pr_step", (0, 0.0))
+    slabs_in_use = int(st["chain_slabs"])
+    E, V = int(st["live_edges"]), G.V
+    # per super-step: every slab in use read once (128 B) with its owner
+    # (4 B), one 8-byte contribution gather and one 8-byte atomic add per
+    # edge, and the per-vertex passes (rank, degree, contribution and
+    # accumulator reads and writes: 44 B per vertex)
+    step_bytes = 132 * slabs_in_use + 16 * E + 44 * V
+    peak, _ = measured_peak()
+    gbs = step_bytes * n_step / (t_step / 1e3) / 1e9 if t_step else None
+    out["pagerank"] = {
+        "graph": "R-MAT scale %d, %d edges" % (args.scale, E), "damping": 0.85, "eps_l1": 1e-7,
+        "static_ms": round(ms_static, 3), "static_iterations": it_static,
+        "ms_per_iteration": round(t_step / max(n_step, 1), 4),
+        "after_batch_warm_ms": round(ms_warm, 3), "after_batch_warm_iterations": it_warm,
+        "after_batch_static_ms": round(ms_cold, 3), "after_batch_static_iterations": it_cold,
+        "warm_speedup": round(ms_cold / ms_warm, 2),
+        "step_algorithmic_bytes": int(step_bytes), "step_gbs": round(gbs, 1) if gbs else None,
+        "step_frac": round(gbs / peak, 4) if gbs else None,
+        "batch": "insert %d + delete %d (one power-law stream batch)" % (args.batch, args.batch)}
+    g.close()
+
+    # triangles: undirected R-MAT (both directions stored, no self-loops)
+    tscale = max(10, args.scale - 2)
+    T = synth.powerlaw_graph(scale=tscale, draws=1 << (tscale + 4))
+    keep = T.src != T.dst
+    us = np.concatenate([T.src[keep], T.dst[keep]]).astype(np.uint32)
+    ud = np.concatenate([T.dst[keep], T.src[keep]]).astype(np.uint32)
+    gt = mk.Graph(T.V, edge_capacity_hint=len(us) + (1 << 20), buckets=mk.bucket_rule(T.V, us, 0.7))
+    gt.insert(us, ud, flags=False)
+    gt.commit()
+    gt.triangles()  # warm-up
+    ms_tc, count = timed_ms(lambda: gt.triangles())
+    bs, bd = synth.rmat_pairs(tscale, 1 << 16, synth.substream(4000, 1))
+    k2 = bs != bd
+    ns = np.concatenate([bs[k2], bd[k2]]).astype(np.uint32)
+    nd = np.concatenate([bd[k2], bs[k2]]).astype(np.uint32)
+    f = gt.insert(ns, nd).cpu().numpy().astype(bool)
+    ns, nd = ns[f], nd[f]
+    upd = mk.Graph(T.V, edge_capacity_hint=len(ns) + 64, buckets=1)
+    upd.insert(ns, nd, flags=False)
+    dns, dnd = mk.to_device_u32(ns), mk.to_device_u32(nd)
+    ms_inc, delta_t = timed_ms(lambda: gt.triangle_delta(upd, dns, dnd, False))
+    ms_re, count2 = timed_ms(lambda: gt.triangles())
+    if count2 != count + delta_t:
+        raise RuntimeError("triangle update disagrees with the recount")
+    out["triangles"] = {
+        "graph": "undirected R-MAT scale %d, %d directed edges" % (tscale, len(us)), "triangles": int(count),
+        "static_ms": round(ms_tc, 3), "batch_new_undirected_edges": int(len(ns) // 2),
+        "update_ms": round(ms_inc, 3), "new_triangles": int(delta_t), "recount_ms": round(ms_re, 3),
+        "update_speedup_vs_recount": round(ms_re / ms_inc, 2)}
+    upd.close()
+    gt.close()
+    return out
+
+
+def run_buckets(args):
+    """The power-law step with the load-factor bucket rule against one bucket
+    per vertex (hashing off: every list is a vertex's whole adjacency), on
+    the same stream of batches: per-operation rates, BFS/SSSP/WCC times and
+    chain statistics (the paper's hashing and iteration-scheme trade-off)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    out = {"workload": "buckets"}
+    peak, _ = measured_peak()
+    for name, rule in (("load_factor_rule", True), ("single_bucket", False)):
+        G, source, S = make_workload(args, args.batch)
+        W, K = 3, max(3, args.steps)
+        bts = [S.batch(args.batch) for _ in range(W + K)]
+        R = StepRunner(args, G, source, len(G.src) + (W + K + 2) * args.batch, device,
+                       buckets=None if rule else 1)
+        st = R.g.stats()
+        rec, outs, timed = R.run(bts, args.batch, W, flush_tag=0)
+        check_steps(outs, timed, args.batch)
+        fam = family_table(rec["prof"], rec["ctr"], args.batch, peak)
+        out[name] = {**summarize(rec, args.batch, peak), "lists": int(st["lists"]),
+                     "chain_mean": round(st["chain_mean"], 3), "chain_max": int(st["chain_max"]),
+                     "device_bytes": int(st["device_bytes"]),
+                     "top_kernels": {k: fam[k] for k in list(fam)[:6]}}
+        R.close()
+        del R
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_l2(args):
+    """The power-law step (batch 2^20) with an L2 persistence window
+    (mk_l2_window) over one part of the store on both of the step's streams.
+    The graph changes as the stream of batches goes on, so every window run
+    sits between two runs without a window on the next batches, and each is
+    reported against the mean of its two neighbours."""
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    peak, _ = measured_peak()
+    G, source, S = make_workload(args, args.batch)
+    W, K = 2, max(3, args.steps)
+    regions = [("vertex_index", mk.MK_L2_VINFO), ("head_slabs", mk.MK_L2_HEADS), ("pool_slabs", mk.MK_L2_POOL)]
+    runs = [("none", mk.MK_L2_NONE)]
+    for r in regions:
+        runs += [r, ("none", mk.MK_L2_NONE)]
+    R = StepRunner(args, G, source, len(G.src) + (len(runs) * (W + K) + 2) * args.batch, device)
+    out = {"workload": "l2", "persisting_l2_max_bytes": None, "runs": []}
+    for name, region in runs:
+        info = {}
+        for st in (R.stream, R.side):
+            info = R.g.l2_window(region, stream=st)
+        bts = [S.batch(args.batch) for _ in range(W + K)]
+        rec, outs, timed = R.run(bts, args.batch, W, flush_tag=0)
+        check_steps(outs, timed, args.batch)
+        if region != mk.MK_L2_NONE:
+            out["persisting_l2_max_bytes"] = info.get("max_bytes")
+        out["runs"].append({"window": name, **summarize(rec, args.batch, peak),
+                            "window_bytes": info.get("window_bytes"), "hit_ratio": info.get("hit_ratio")})
+    for st in (R.stream, R.side):
+        R.g.l2_window(mk.MK_L2_NONE, stream=st)
+    R.close()
+    for i, (name, _) in enumerate(runs):
+        if name != "none":
+            base = (out["runs"][i - 1]["ms_per_step"] + out["runs"][i + 1]["ms_per_step"]) / 2
+            out[name] = {"ms_per_step": out["runs"][i]["ms_per_step"], "neighbours_ms_per_step": round(base, 3),
+                         "step_time_ratio": round(out["runs"][i]["ms_per_step"] / base, 4),
+                         "window_bytes": out["runs"][i]["window_bytes"], "hit_ratio": out["runs"][i]["hit_ratio"]}
+    return out
 
 
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
-    if args.workload in ("growth", "served", "road"):
+    if args.workload not in ("powerlaw",):
         if rank == 0:
-            res = {"growth": run_growth, "served": run_served, "road": run_road}[args.workload](args)
+            res = {"growth": run_growth, "served": run_served, "road": run_road, "analytics": run_analytics,
+                   "buckets": run_buckets, "l2": run_l2}[args.workload](args)
             print(json.dumps(res), flush=True)
         return 0
     if args.impl == "reference":

@@ -511,6 +511,27 @@ mk_status mk_profile_read(mk_graph *g, mk_kernel_time *out, int cap, int *n_out)
  * plans). */
 uint64_t mk_launch_count(mk_graph *g);
 
+/* L2 residency control (a service of this library; the paper has none): an
+ * access-policy window on `stream` (cudaStreamAttributeAccessPolicyWindow)
+ * that marks one part of the graph as persisting in L2 for the kernels
+ * later launched on that stream, with the L2 set-aside of this process's
+ * context (cudaLimitPersistingL2CacheSize) sized to the window, at most the
+ * device's maximum.  region: MK_L2_VINFO (the per-vertex index, 8 B a
+ * vertex), MK_L2_HEADS (the head slabs), MK_L2_POOL (the overflow pool
+ * slabs); a window larger than the device's window limit is cut to it, and
+ * when it is larger than the set-aside only that share of its lines
+ * (hitRatio) persists.  MK_L2_NONE removes the window from `stream`, resets
+ * the persisting lines to normal and the set-aside to 0.  Both end with the
+ * process's context.  *out (nullable, host): window bytes, hit ratio and the
+ * device's maximum set-aside. */
+enum { MK_L2_NONE = 0, MK_L2_VINFO = 1, MK_L2_HEADS = 2, MK_L2_POOL = 3 };
+typedef struct mk_l2_info {
+    uint64_t window_bytes;
+    uint64_t max_bytes;
+    float hit_ratio;
+} mk_l2_info;
+mk_status mk_l2_window(mk_graph *g, int region, void *stream, mk_l2_info *out);
+
 /* Test hooks for the failure paths (a service of this library; the paper
  * has none).  knob MK_DEBUG_BARRIER_SPINS: value 0 restores the default
  * poll limit of the BFS/SSSP round kernel's grid barrier (2^24 polls of

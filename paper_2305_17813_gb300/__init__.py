@@ -16,13 +16,13 @@ import ctypes
 import numpy as np
 
 from ._native import (MK_ERR_CUDA, MK_ERR_INTERNAL, MK_ERR_INVALID_ARG, MK_ERR_NO_MEMORY, MK_ERR_POOL_EXHAUSTED,
-                      MK_ERR_TIMEOUT, MK_INVALID_LANE, MK_NONE, MK_OK, MkError, check, load, mk_config, mk_kernel_time,
-                      mk_stats)
+                      MK_ERR_TIMEOUT, MK_INVALID_LANE, MK_L2_HEADS, MK_L2_NONE, MK_L2_POOL, MK_L2_VINFO, MK_NONE, MK_OK,
+                      MkError, check, load, mk_config, mk_kernel_time, mk_stats)
 
 __all__ = [
     "Graph", "load", "MkError", "MK_OK", "MK_ERR_INVALID_ARG", "MK_ERR_POOL_EXHAUSTED", "MK_ERR_TIMEOUT",
     "MK_ERR_CUDA", "MK_ERR_NO_MEMORY", "MK_ERR_INTERNAL", "MK_NONE", "MK_INVALID_LANE", "bucket_rule",
-    "to_device_u32", "to_numpy_u32", "Batcher", "Server",
+    "to_device_u32", "to_numpy_u32", "Batcher", "Server", "MK_L2_NONE", "MK_L2_VINFO", "MK_L2_HEADS", "MK_L2_POOL",
 ]
 
 
@@ -179,6 +179,15 @@ class Graph:
         check(self._lib.mk_pagerank(self._h, _ptr(pr), 1 if warm else 0, damping, eps, max_iter, ctypes.byref(it),
                                     ctypes.byref(delta), _stream(stream)), "mk_pagerank")
         return pr, it.value, delta.value
+
+    def l2_window(self, region: int, stream=None) -> dict:
+        """Set (or with MK_L2_NONE remove) an L2 persistence window over one
+        part of the graph on `stream` (mk_l2_window)."""
+        from ._native import mk_l2_info
+
+        info = mk_l2_info()
+        check(self._lib.mk_l2_window(self._h, int(region), _stream(stream), ctypes.byref(info)), "mk_l2_window")
+        return {"window_bytes": info.window_bytes, "max_bytes": info.max_bytes, "hit_ratio": info.hit_ratio}
 
     def triangles(self, stream=None) -> int:
         """Triangles of the undirected graph stored with both directions."""

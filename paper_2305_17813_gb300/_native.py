@@ -83,6 +83,10 @@ class mk_update_req(ctypes.Structure):
                 ("d_w", ctypes.c_void_p), ("n", ctypes.c_uint64), ("d_flags", ctypes.c_void_p)]
 
 
+class mk_l2_info(ctypes.Structure):
+    _fields_ = [("window_bytes", ctypes.c_uint64), ("max_bytes", ctypes.c_uint64), ("hit_ratio", ctypes.c_float)]
+
+
 class mk_tuning(ctypes.Structure):
     _fields_ = [("query_group", ctypes.c_int), ("query_block", ctypes.c_int), ("rounds_blocks_per_sm", ctypes.c_int),
                 ("query_best_ms", ctypes.c_float), ("rounds_best_ms", ctypes.c_float),
@@ -97,6 +101,7 @@ class mk_request(ctypes.Structure):
 
 MK_REQ_QUERY, MK_REQ_INSERT, MK_REQ_DELETE, MK_REQ_SSSP, MK_REQ_BFS = 0, 1, 2, 3, 4
 MK_DEBUG_BARRIER_SPINS, MK_DEBUG_HOST_ROUNDS = 1, 2
+MK_L2_NONE, MK_L2_VINFO, MK_L2_HEADS, MK_L2_POOL = 0, 1, 2, 3
 
 
 class mk_kernel_time(ctypes.Structure):
@@ -133,6 +138,7 @@ SIGNATURES = {
     "mk_launch_count": (_U64, [_P]),
     "mk_version": (ctypes.c_char_p, []),
     "mk_debug_set": (_INT, [_P, _INT, _U64]),
+    "mk_l2_window": (_INT, [_P, _INT, _P, ctypes.POINTER(mk_l2_info)]),
     "mk_pagerank": (_INT, [_P, _P, _INT, ctypes.c_float, ctypes.c_float, _U32, ctypes.POINTER(_U32),
                            ctypes.POINTER(ctypes.c_float), _P]),
     "mk_tc_count": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),
