@@ -240,21 +240,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "7c40a5cb5cbb9d2ac94b78f631250ad2c8dc2c74747ed419265b0b6764bb4f3a"
+NCU_TRAFFIC_SOURCES_SHA = "0c0724a4b54fc84811a5ed26c81269180e7cf9d27a4dc34ba654105f0e859b6e"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49446528,
-    "sssp_relax_into_invalid": 281274624,
-    "sssp_enqueue_invalid": 11139072,
-    "sssp_relax_updated": 149913216,
-    "sssp_invalidate_walk": 8524096,
-    "sssp_invalidate": 13739968,
-    "wcc_hook_all": 351008128,
-    "wcc_hook_updated": 139749504,
-    "insert": 241921792,
-    "delete": 198795904,
-    "query": 130562048,
-    "stage_dedup": 40166336,
-    "update_slab_pointers": 60561856,
+    "sssp_rounds": 49406688,
+    "sssp_relax_into_invalid": 280748480,
+    "sssp_enqueue_invalid": 11001984,
+    "sssp_relax_updated": 149696000,
+    "sssp_invalidate_walk": 8524224,
+    "sssp_invalidate": 13741120,
+    "wcc_hook_all": 350259968,
+    "wcc_hook_updated": 139439232,
+    "insert": 241625600,
+    "delete": 199203200,
+    "query": 131710848,
+    "stage_dedup": 40140992,
+    "update_slab_pointers": 60634816,
 }
 
 
