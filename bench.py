@@ -1010,6 +1010,24 @@ def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=
         log(out)
     mism = [i for i in store_p if not all(torch.equal(x, y) for x, y in zip(store_p[i], store_s[i]) if x is not None)]
     out["compared_requests"] = len(store_p)
+    # what the retained requests applied or found: the share of insert and
+    # delete flags set and of queries present (the stream's deletes walk a
+    # fixed order of the initial edges, so once it has gone round, a delete
+    # of an edge already deleted is a no-op; inserts re-drawn from the
+    # insert pool after their first insertion are no-ops too)
+    tally = {0: [0, 0], 1: [0, 0], 2: [0, 0]}
+    for i, outs in store_p.items():
+        k, n = int(kinds[i]), int(sizes[i])
+        if k in (1, 2) and n:
+            tally[k][0] += int(outs[0][:n].sum().item())
+            tally[k][1] += n
+        elif k == 0 and n:
+            words = outs[0].cpu().numpy().view(np.uint32)
+            tally[0][0] += int(np.unpackbits(words.view(np.uint8), bitorder="little")[:n].sum())
+            tally[0][1] += n
+    out["retained_outcomes"] = {"insert_applied_frac": round(tally[1][0] / max(tally[1][1], 1), 4),
+                                "delete_applied_frac": round(tally[2][0] / max(tally[2][1], 1), 4),
+                                "query_present_frac": round(tally[0][0] / max(tally[0][1], 1), 4)}
     out["mismatches"] = len(mism)
     if keep_outputs:
         out["outputs"] = (store_p, store_s)

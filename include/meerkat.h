@@ -342,6 +342,28 @@ mk_status mk_incr_sssp(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t 
  * read as 1); distances are hop counts.  Separate state from mk_incr_sssp. */
 mk_status mk_incr_bfs(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream);
 
+/* Several BFS/SSSP states of one graph advanced by one call (a service of
+ * this library; the paper runs one algorithm per call).  Results are those
+ * of one mk_incr_sssp / mk_incr_bfs call per request, but the passes over
+ * the change log and over the whole slab array run once for all of them:
+ * the incremental prologue walks each updated list once and relaxes its new
+ * edges into every state, the decremental relax-into-invalid scan reads each
+ * slab once and tests it against every state's invalidated vertices, and the
+ * rounds of all states share one cooperative launch and one grid barrier per
+ * round (no single-block phase for small frontiers).  Up to MK_MULTI_MAX
+ * requests, each MK_REQ_SSSP or MK_REQ_BFS (kinds of the serving section,
+ * below) with its source and nullable dist / parent outputs (V words each,
+ * device); no two requests may name the same (kind, source).  One request is
+ * the same as the single call. */
+#define MK_MULTI_MAX 4u
+typedef struct mk_algo_req {
+    int kind;
+    uint32_t source;
+    uint32_t *d_dist;
+    uint32_t *d_parent;
+} mk_algo_req;
+mk_status mk_incr_multi(mk_graph *g, const mk_algo_req *h_reqs, uint32_t n, void *stream);
+
 /* Weakly connected components (paper, Sec. "Incremental WCC"): union-find with
  * Union-Async hooking of the larger root under the smaller and full path
  * compression.  The first call, and any call whose epoch holds deletions

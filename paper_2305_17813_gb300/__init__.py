@@ -161,6 +161,25 @@ class Graph:
         check(self._lib.mk_incr_bfs(self._h, int(source), _ptr(dist), _ptr(par), _stream(stream)), "mk_incr_bfs")
         return dist, par
 
+    def incr_multi(self, requests, stream=None):
+        """Advance several BFS/SSSP states in one mk_incr_multi call.
+        requests: list of ("sssp" | "bfs", source); returns one (dist,
+        parent) pair of tensors per request."""
+        torch = _torch()
+        from ._native import MK_REQ_BFS, MK_REQ_SSSP, mk_algo_req
+
+        arr = (mk_algo_req * max(1, len(requests)))()
+        outs = []
+        for i, (kind, source) in enumerate(requests):
+            dist = torch.empty(self.V, dtype=torch.int32, device=self.device)
+            par = torch.empty(self.V, dtype=torch.int32, device=self.device)
+            arr[i].kind = {"sssp": MK_REQ_SSSP, "bfs": MK_REQ_BFS}[kind]
+            arr[i].source = int(source)
+            arr[i].d_dist, arr[i].d_parent = dist.data_ptr(), par.data_ptr()
+            outs.append((dist, par))
+        check(self._lib.mk_incr_multi(self._h, arr, len(requests), _stream(stream)), "mk_incr_multi")
+        return outs
+
     def wcc(self, stream=None):
         torch = _torch()
         lab = torch.empty(self.V, dtype=torch.int32, device=self.device)

@@ -83,6 +83,11 @@ class mk_update_req(ctypes.Structure):
                 ("d_w", ctypes.c_void_p), ("n", ctypes.c_uint64), ("d_flags", ctypes.c_void_p)]
 
 
+class mk_algo_req(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("source", ctypes.c_uint32), ("d_dist", ctypes.c_void_p),
+                ("d_parent", ctypes.c_void_p)]
+
+
 class mk_l2_info(ctypes.Structure):
     _fields_ = [("window_bytes", ctypes.c_uint64), ("max_bytes", ctypes.c_uint64), ("hit_ratio", ctypes.c_float)]
 
@@ -127,6 +132,7 @@ SIGNATURES = {
     "mk_incr_sssp": (_INT, [_P, _U32, _P, _P, _P]),
     "mk_incr_bfs": (_INT, [_P, _U32, _P, _P, _P]),
     "mk_incr_wcc": (_INT, [_P, _P, _P]),
+    "mk_incr_multi": (_INT, [_P, ctypes.POINTER(mk_algo_req), _U32, _P]),
     "mk_graph_export": (_INT, [_P, _U64, _P, _P, _P, _P, _P]),
     "mk_graph_stats": (_INT, [_P, ctypes.POINTER(mk_stats), _P]),
     "mk_last_error": (_INT, [_P]),

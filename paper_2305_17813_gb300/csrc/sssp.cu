@@ -680,6 +680,260 @@ __global__ void k_unpack(const unsigned long long *D, uint32_t V, uint32_t *dist
         parent[v] = node_parent(d);
 }
 
+// ------------------------------------------------- several states, one pass
+//
+// mk_incr_multi advances up to kMaxMulti BFS/SSSP states of one graph
+// together: the passes that read the graph's change log or its whole slab
+// array (the incremental prologue over the updated lists, the decremental
+// relax-into-invalid scan) and the round loop run once for all of them, each
+// slab or list read once and relaxed into every state, the rounds of all
+// states sharing one grid barrier per round.
+
+constexpr uint32_t kMaxMulti = 4;
+
+struct MultiArgs {
+    RoundArgs c[kMaxMulti];
+    uint32_t k; // states in use
+};
+
+// The incremental prologue (k_relax_updated) for every state at once: each
+// logged list is walked once from its UpdateIterator start and every slab's
+// new edges are relaxed into each state whose copy of the list's source has
+// a finite distance.  Dynamic shared memory: one BlockFrontier per state.
+__global__ void __launch_bounds__(256, 5) k_relax_updated_multi(MultiArgs m)
+{
+    extern __shared__ unsigned char multi_smem[];
+    BlockFrontier *bqs = reinterpret_cast<BlockFrontier *>(multi_smem);
+    const GView &g = m.c[0].g;
+    const uint32_t s4 = lane_id() & 3u, g4 = lane_id() >> 2;
+    const uint32_t n = min(__ldg(&g.st->ulog_count), g.H);
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gs = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 8;
+    for (uint32_t j = 0; j < m.k; ++j)
+        if (threadIdx.x == 0)
+            bqs[j].count = 0;
+    __syncthreads();
+    uint32_t round[kMaxMulti];
+#pragma unroll
+    for (uint32_t j = 0; j < kMaxMulti; ++j)
+        round[j] = j < m.k ? __ldg(m.c[j].ctr + kRid) + 1 : 0u;
+    unsigned long long lists = 0, slabs = 0, edges = 0, improved = 0;
+    uint64_t i = warp0 * 8 + g4;
+    uint32_t L = i < n ? g.ulog[i] : kNil;
+    uint32_t nL = i + gs < n ? g.ulog[i + gs] : kNil;
+    uint32_t src = L != kNil ? g.list_src[L] : 0;
+    unsigned long long mk = L != kNil ? g.lmark[L] : 0;
+    for (uint64_t base = warp0 * 8; base < n; base += gs, i += gs) {
+        const uint32_t nnL = i + 2 * gs < n ? g.ulog[i + 2 * gs] : kNil;
+        const uint32_t nsrc = nL != kNil ? g.list_src[nL] : 0;
+        const unsigned long long nmk = nL != kNil ? g.lmark[nL] : 0;
+        uint32_t dx[kMaxMulti];
+        bool any = false;
+#pragma unroll
+        for (uint32_t j = 0; j < kMaxMulti; ++j) {
+            dx[j] = (j < m.k && L != kNil) ? node_dist(__ldcg(&m.c[j].D[src])) : kInf32;
+            any |= dx[j] != kInf32;
+        }
+        const uint32_t mlane = (uint32_t)(mk & 0xFF);
+        const uint32_t first_lane = mlane == kInvalidLane ? 32u : mlane;
+        const bool go = L != kNil && any;
+        const uint32_t start = go ? (uint32_t)(mk >> 32) : kNil;
+        uint4 lo, hi;
+        group4_load(g, start, lo, hi);
+        lists += __popc(__ballot_sync(kFull, go && s4 == 0));
+        const uint32_t x = src;
+        slabs += walk_lists_g4_from(g, start, true, lo, hi, first_lane, m.c[0].max_hops,
+                                    [&](const uint32_t(&y)[4], const uint32_t(&w)[4], const bool(&live)[4]) {
+                                        for (uint32_t j = 0; j < m.k; ++j) {
+                                            const RoundArgs &a = m.c[j];
+                                            relax_edges4(a, x, dx[j], y, w, live, round[j], bqs[j], a.front[0],
+                                                         a.ctr + kCnt0, (int *)(a.ctr + kOverflow), edges,
+                                                         improved);
+                                        }
+                                    });
+        L = nL;
+        nL = nnL;
+        src = nsrc;
+        mk = nmk;
+    }
+    for (uint32_t j = 0; j < m.k; ++j)
+        bq_flush(bqs[j], m.c[j].front[0], m.c[j].ctr + kCnt0, m.c[j].cap, (int *)(m.c[j].ctr + kOverflow));
+    count_add(g.st, kCtrSeedLists, lists);
+    count_add(g.st, kCtrSeedSlabs, slabs);
+    count_add(g.st, kCtrSeedEdges, edges);
+    count_add(g.st, kCtrSeedImproved, improved);
+}
+
+// The decremental relax-into-invalid scan (k_relax_into_invalid_slabs) for
+// every state at once: a slab is staged when its source has a finite
+// distance in any state that invalidated something, and its live pairs are
+// then tested against each such state's invalidation bitmap.
+__global__ void __launch_bounds__(kScanWarps * 32) k_relax_into_invalid_multi(MultiArgs m)
+{
+    __shared__ ScanSmem sm;
+    const GView &g = m.c[0].g;
+    bool act[kMaxMulti];
+    bool any_act = false;
+#pragma unroll
+    for (uint32_t j = 0; j < kMaxMulti; ++j) {
+        act[j] = j < m.k && __ldg(m.c[j].ctr + kInvTotal) != 0;
+        any_act |= act[j];
+    }
+    if (!any_act)
+        return;
+    const uint32_t lane = lane_id();
+    uint32_t slabs = 0, edges = 0, owners = 0, targets = 0;
+    const bool ok = scan_slab_chunks(
+        g, sm,
+        [&](uint32_t own) {
+            owners += own != kNil;
+            uint4 dx = make_uint4(kInf32, kInf32, kInf32, kInf32);
+            if (own != kNil) {
+                dx.x = act[0] ? node_dist(__ldcg(&m.c[0].D[own])) : kInf32;
+                dx.y = act[1] ? node_dist(__ldcg(&m.c[1].D[own])) : kInf32;
+                dx.z = act[2] ? node_dist(__ldcg(&m.c[2].D[own])) : kInf32;
+                dx.w = act[3] ? node_dist(__ldcg(&m.c[3].D[own])) : kInf32;
+            }
+            return dx;
+        },
+        [](const uint4 &dx) { return dx.x != kInf32 || dx.y != kInf32 || dx.z != kInf32 || dx.w != kInf32; },
+        [&](const uint4 *buf, const uint8_t *comp, uint32_t n, uint32_t own_l, const uint4 &dx_l) {
+            const bool active = lane < n;
+            const uint32_t it = active ? comp[lane] : 0u;
+            const uint32_t own = __shfl_sync(kFull, own_l, it);
+            const uint32_t dxs[kMaxMulti] = {__shfl_sync(kFull, dx_l.x, it), __shfl_sync(kFull, dx_l.y, it),
+                                             __shfl_sync(kFull, dx_l.z, it), __shfl_sync(kFull, dx_l.w, it)};
+            slabs += active;
+            if (!__any_sync(kFull, active))
+                return;
+            const uint32_t *mine = reinterpret_cast<const uint32_t *>(buf + (active ? lane : 0) * 8);
+            uint32_t key[16];
+            uint32_t live = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t qq = (q + lane) & 7u;
+                const uint4 v = reinterpret_cast<const uint4 *>(mine)[qq];
+                const bool l0 = active && v.x < kTombKey, l1 = active && qq != 7u && v.z < kTombKey;
+                key[2 * q] = v.x;
+                key[2 * q + 1] = v.z;
+                live |= (l0 ? 1u : 0u) << (2 * q) | (l1 ? 1u : 0u) << (2 * q + 1);
+            }
+            edges += __popc(live);
+            for (uint32_t j = 0; j < m.k; ++j) {
+                const RoundArgs &a = m.c[j];
+                const uint32_t dx = dxs[j];
+                const uint32_t lj = dx != kInf32 ? live : 0u;
+                if (!__any_sync(kFull, lj != 0))
+                    continue;
+                uint32_t word[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    word[k] = ((lj >> k) & 1u) ? __ldg(&a.inv[key[k] >> 5]) : 0u;
+                uint32_t hit = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    hit |= ((word[k] >> (key[k] & 31u)) & 1u) << k;
+                hit &= lj;
+                targets += __popc(hit);
+                while (hit) {
+                    const int k = __ffs(hit) - 1;
+                    hit &= hit - 1;
+                    const uint32_t at = (((uint32_t)(k >> 1) + lane) & 7u) * 4 + 2 * (k & 1);
+                    const unsigned long long nd = (unsigned long long)dx + (a.unit ? 1u : mine[at + 1]);
+                    if (nd < kInf32)
+                        atomicMin(&a.D[mine[at]], (nd << 32) | own);
+                }
+            }
+        });
+    if (!ok)
+        set_status(g.st, kErrTimeout);
+    count_add(g.st, kCtrScanOwners, __reduce_add_sync(kFull, owners));
+    count_add(g.st, kCtrScanSlabs, __reduce_add_sync(kFull, slabs));
+    count_add(g.st, kCtrScanEdges, __reduce_add_sync(kFull, edges));
+    count_add(g.st, kCtrScanTargets, __reduce_add_sync(kFull, targets));
+}
+
+// The round loop of every state in one cooperative launch: in round r each
+// state with a non-empty frontier is relaxed over the whole grid (one state
+// after another), then one grid barrier ends the round for all of them; the
+// loop ends when every frontier is empty.  Block 0 clears each state's
+// counter for round r + 2 every round, so a state whose frontier emptied
+// keeps reading zero.  No solo phase: rounds of a few lists cost a grid
+// barrier each.  Then every state's epilogue (dist/parent, round stamp).
+// Dynamic shared memory: one BlockFrontier per state.
+__global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds_multi(MultiArgs m)
+{
+    extern __shared__ unsigned char multi_smem[];
+    BlockFrontier *bqs = reinterpret_cast<BlockFrontier *>(multi_smem);
+    __shared__ uint32_t s_n[kMaxMulti];
+    for (uint32_t j = 0; j < m.k; ++j)
+        if (threadIdx.x == 0)
+            bqs[j].count = 0;
+    __syncthreads();
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const RoundArgs &a0 = m.c[0];
+    uint32_t r = 0, bars = 0, passed = 0;
+    bool ok = true;
+    while (r < a0.max_rounds) {
+        if (threadIdx.x == 0)
+            for (uint32_t j = 0; j < m.k; ++j)
+                s_n[j] = min(ld_volatile(m.c[j].ctr + kCnt0 + r % 3), m.c[j].cap);
+        __syncthreads();
+        uint32_t total = 0;
+        for (uint32_t j = 0; j < m.k; ++j)
+            total += s_n[j];
+        if (total == 0)
+            break;
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            for (uint32_t j = 0; j < m.k; ++j)
+                m.c[j].ctr[kCnt0 + (r + 2) % 3] = 0;
+        for (uint32_t j = 0; j < m.k; ++j) {
+            const uint32_t n = s_n[j];
+            if (n == 0)
+                continue;
+            const RoundArgs &a = m.c[j];
+            const uint32_t in = r & 1;
+            uint32_t *cnt = a.ctr + kCnt0 + (r + 1) % 3;
+            relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, __ldg(a.ctr + kRid) + 2 + r, warp0, nwarps, bqs[j]);
+            bq_flush(bqs[j], a.front[in ^ 1], cnt, a.cap, (int *)(a.ctr + kOverflow));
+        }
+        ++bars;
+        if (!grid_barrier(a0.ctr + kBar, passed, a0.barrier_spins)) {
+            ok = false;
+            break;
+        }
+        ++r;
+    }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t j = 0; j < m.k; ++j) {
+        const RoundArgs &a = m.c[j];
+        if (a.dist || a.parent)
+            for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < a.g.V; v += stride) {
+                const unsigned long long d = __ldcg(&a.D[v]);
+                if (a.dist)
+                    a.dist[v] = node_dist(d);
+                if (a.parent)
+                    a.parent[v] = node_parent(d);
+            }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bool bad = !ok || r >= a0.max_rounds;
+        for (uint32_t j = 0; j < m.k; ++j) {
+            const RoundArgs &a = m.c[j];
+            a.ctr[kRoundsDone] = r;
+            a.ctr[kRid] += r + 2;
+            if (a.dist || a.parent)
+                atomicAdd(&a.g.st->ctr[kCtrUnpacked][0], (unsigned long long)a.g.V);
+            bad |= ld_volatile(a.ctr + kOverflow) != 0;
+        }
+        atomicAdd(&a0.g.st->ctr[kCtrRounds][0], (unsigned long long)r);
+        atomicAdd(&a0.g.st->ctr[kCtrGridBarriers][0], (unsigned long long)bars);
+        if (bad)
+            set_status(a0.g.st, kErrTimeout);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 namespace {
@@ -871,6 +1125,126 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     return MK_OK;
 }
 
+
+// Several BFS/SSSP states of one graph in one call (see k_rounds_multi).
+mk_status run_multi(mk_graph *g, const mk_algo_req *reqs, uint32_t n, cudaStream_t s)
+{
+    MultiArgs m{};
+    m.k = n;
+    Consumer *cs[kMaxMulti] = {};
+    bool incr[kMaxMulti] = {};
+    const uint32_t V = g->v.V, H = g->v.H;
+    for (uint32_t j = 0; j < n; ++j) {
+        const int kind = reqs[j].kind == MK_REQ_BFS ? kBfs : kSssp;
+        MK_TRY(get_consumer(g, kind, reqs[j].source, &cs[j]));
+        Consumer *c = cs[j];
+        RoundArgs &a = m.c[j];
+        a.g = g->v;
+        a.D = c->D;
+        a.front[0] = c->front[0];
+        a.front[1] = c->front[1];
+        a.ctr = c->counters;
+        a.stamp = c->stamp;
+        a.inv = c->inv;
+        a.cap = H;
+        a.max_hops = g->v.P + 2;
+        a.max_rounds = V + 2;
+        a.barrier_spins = g->dbg_barrier_spins != ~0ull ? (uint32_t)g->dbg_barrier_spins : kBarrierSpins;
+        a.source = reqs[j].source;
+        a.unit = kind == kBfs ? 1 : 0;
+        a.dist = reqs[j].d_dist;
+        a.parent = reqs[j].d_parent;
+        incr[j] = c->epoch == g->epoch;
+        MK_CUDA(cudaMemsetAsync(c->counters, 0, kClearWords * 4, s));
+        MK_CUDA(cudaMemsetAsync(c->counters + kBar, 0, 4, s));
+    }
+    // the states that recompute statically start from their sources
+    for (uint32_t j = 0; j < n; ++j)
+        if (!incr[j])
+            MK_TRY(timed(g, "sssp_init", s, 1, [&]() {
+                k_sssp_init<<<grid_for(V, 256), 256, 0, s>>>(cs[j]->D, V, m.c[j].source, cs[j]->front[0],
+                                                             cs[j]->counters + kCnt0, g->v.vinfo);
+                return cudaSuccess;
+            }));
+    // decremental prologue: invalidation per state, one scan for all
+    MultiArgs dec{};
+    MultiArgs inc{};
+    for (uint32_t j = 0; j < n; ++j)
+        if (incr[j]) {
+            if (g->epoch_has_deletes)
+                dec.c[dec.k++] = m.c[j];
+            if (g->ulog_bound)
+                inc.c[inc.k++] = m.c[j];
+        }
+    for (uint32_t j = 0; j < dec.k; ++j) {
+        const RoundArgs &a = dec.c[j];
+        MK_CUDA(cudaMemsetAsync(a.inv, 0, (size_t)(V + 31) / 32 * 4, s));
+        MK_TRY(timed(g, "sssp_invalidate", s, 1, [&]() {
+            k_invalidate<<<grid_for(std::max<uint64_t>(g->dlog_bound, 1), 256), 256, 0, s>>>(g->d_dlog, g->d_state,
+                                                                                             a);
+            return cudaSuccess;
+        }));
+        MK_TRY(timed(g, "sssp_invalidate_walk", s, 1, [&]() {
+            k_inv_walk<<<grid_for(V, 256), 256, 0, s>>>(a);
+            return cudaSuccess;
+        }));
+    }
+    if (dec.k) {
+        MK_TRY(timed(g, "sssp_relax_into_invalid", s, 1, [&]() {
+            static const uint32_t grid = resident_grid(k_relax_into_invalid_multi, kScanWarps * 32);
+            k_relax_into_invalid_multi<<<grid, kScanWarps * 32, 0, s>>>(dec);
+            return cudaSuccess;
+        }));
+        for (uint32_t j = 0; j < dec.k; ++j)
+            MK_TRY(timed(g, "sssp_enqueue_invalid", s, 1, [&]() {
+                k_enqueue_invalid<<<grid_for(((uint64_t)V + 31) / 32 * 32, 256), 256, 0, s>>>(dec.c[j]);
+                return cudaSuccess;
+            }));
+    }
+    // incremental prologue: one walk over the updated lists for all states
+    if (inc.k) {
+        const size_t smem = inc.k * sizeof(BlockFrontier);
+        static bool attr = false;
+        if (!attr) {
+            MK_CUDA(cudaFuncSetAttribute(k_relax_updated_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxMulti * sizeof(BlockFrontier))));
+            attr = true;
+        }
+        MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
+            const uint64_t threads = g->ulog_bound * 4;
+            k_relax_updated_multi<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 10), 256, smem, s>>>(inc);
+            return cudaSuccess;
+        }));
+    }
+    // rounds of every state together
+    const int grid = rounds_grid(g->tune.rounds_blocks_per_sm);
+    const int block = rounds_block(g->tune.rounds_blocks_per_sm);
+    const size_t smem = n * sizeof(BlockFrontier);
+    static bool rattr = false;
+    if (!rattr) {
+        MK_CUDA(cudaFuncSetAttribute(k_rounds_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kMaxMulti * sizeof(BlockFrontier))));
+        rattr = true;
+    }
+    void *args[] = {&m};
+    mk_status st = MK_ERR_CUDA;
+    if (!g->dbg_host_rounds)
+        st = timed(g, "sssp_rounds", s, 1, [&]() {
+            return cudaLaunchCooperativeKernel((const void *)k_rounds_multi, dim3(grid), dim3(block), args, smem, s);
+        });
+    if (st != MK_OK) {
+        cudaGetLastError();
+        // one state at a time (the host-driven loop when the cooperative
+        // launch is refused)
+        for (uint32_t j = 0; j < n; ++j)
+            MK_TRY(run_phase(g, m.c[j], "sssp_rounds", s));
+    }
+    for (uint32_t j = 0; j < n; ++j) {
+        cs[j]->epoch = g->epoch;
+        cs[j]->seq = g->change_seq;
+    }
+    return MK_OK;
+}
 } // namespace
 
 namespace mk {
@@ -907,6 +1281,24 @@ mk_status mk_incr_sssp(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t 
 mk_status mk_incr_bfs(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream)
 {
     return run_sssp(g, kBfs, source, d_dist, d_parent, (cudaStream_t)stream);
+}
+
+mk_status mk_incr_multi(mk_graph *g, const mk_algo_req *h_reqs, uint32_t n, void *stream)
+{
+    if (!g || !h_reqs || n == 0 || n > kMaxMulti)
+        return MK_ERR_INVALID_ARG;
+    for (uint32_t j = 0; j < n; ++j) {
+        if ((h_reqs[j].kind != MK_REQ_SSSP && h_reqs[j].kind != MK_REQ_BFS) || h_reqs[j].source >= g->v.V)
+            return MK_ERR_INVALID_ARG;
+        for (uint32_t i = 0; i < j; ++i)
+            if (h_reqs[i].kind == h_reqs[j].kind && h_reqs[i].source == h_reqs[j].source)
+                return MK_ERR_INVALID_ARG; // one state cannot be advanced twice at once
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 1)
+        return run_sssp(g, h_reqs[0].kind == MK_REQ_BFS ? kBfs : kSssp, h_reqs[0].source, h_reqs[0].d_dist,
+                        h_reqs[0].d_parent, s);
+    return run_multi(g, h_reqs, n, s);
 }
 
 } // extern "C"

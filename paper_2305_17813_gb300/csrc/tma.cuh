@@ -101,8 +101,9 @@ struct ScanSmem {
     uint8_t comp[kScanWarps][2][kScanChunk];     // compacted position -> lane of its owner
 };
 
-// Scans every slab of the array.  aux_fn(owner) -> uint32_t is evaluated per
-// lane two chunks ahead (kNil owners included); a slab is copied and
+// Scans every slab of the array.  aux_fn(owner) -> Aux (any register-sized
+// value type) is evaluated per lane two chunks ahead (kNil owners
+// included); a slab is copied and
 // processed only if its owner is not kNil and keep_fn(aux) holds.
 // chunk_fn(buf, comp, n, owner, aux) processes one chunk: buf holds its n
 // kept slabs (slab j at buf[8j .. 8j+7]) and comp[j] the lane whose owner /
@@ -125,7 +126,8 @@ __device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, A
     __syncwarp();
     auto owner_of = [&](uint64_t c) -> uint32_t { return c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil; };
     // copies chunk c's kept slabs into buffer b; returns how many
-    auto issue = [&](uint64_t c, uint32_t own, uint32_t aux, uint32_t b) -> uint32_t {
+    using Aux = decltype(aux_fn(0u));
+    auto issue = [&](uint64_t c, uint32_t own, const Aux &aux, uint32_t b) -> uint32_t {
         if (c >= total)
             return 0;
         const bool keep = own != kNil && keep_fn(aux);
@@ -144,15 +146,15 @@ __device__ __forceinline__ bool scan_slab_chunks(const GView &g, ScanSmem &sm, A
     };
     uint64_t c = warp0 * kScanChunk;
     uint32_t own0 = owner_of(c), own1 = owner_of(c + stride), own2 = owner_of(c + 2 * stride);
-    uint32_t aux0 = aux_fn(own0);
+    Aux aux0 = aux_fn(own0);
     uint32_t n0 = issue(c, own0, aux0, 0);
-    uint32_t aux1 = aux_fn(own1);
+    Aux aux1 = aux_fn(own1);
     uint32_t k = 0;
     bool ok = true;
     for (; c < total; c += stride, ++k) {
         const uint32_t b = k & 1;
         const uint32_t n1 = issue(c + stride, own1, aux1, b ^ 1);
-        const uint32_t aux2 = aux_fn(own2);
+        const Aux aux2 = aux_fn(own2);
         const uint32_t own3 = owner_of(c + 3 * stride);
         ok = __all_sync(kFull, mbar_wait(&sm.bar[w][b], (k >> 1) & 1, kScanWaitLimit));
         if (!ok)
