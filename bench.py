@@ -224,14 +224,17 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
     if family == "sssp_enqueue_invalid":
         return ctr["scan_improved"] * (8 + 8 + 8 + 4)
     if family == "sssp_relax_updated":
+        # walk of the updated lists, or the inserted-edge log (16 B an entry
+        # plus the 8 B source node)
         return (ctr["seed_lists"] * (4 + 8 + 8) + 128 * ctr["seed_slabs"] + 16 * ctr["seed_edges"]
-                + ctr["seed_improved"] * (8 + 4 + 8))
+                + ctr["seed_improved"] * (8 + 4 + 8) + ctr.get("seed_log", 0) * (16 + 8))
     if family == "sssp_invalidate_walk":
         return ctr["walk_vertices"] * 8 + ctr["invalidated"] * 8
     if family == "wcc_hook_all":
         return 128 * ctr["wcc_slabs"] + 16 * ctr["wcc_edges"]
     if family == "wcc_hook_updated":
-        return 128 * ctr["wcc_upd_slabs"] + 16 * ctr["wcc_upd_edges"]
+        # walk of the updated lists, or the inserted-edge log (16 B an entry)
+        return 128 * ctr["wcc_upd_slabs"] + 16 * ctr["wcc_upd_edges"] + 16 * ctr.get("wcc_log", 0)
     return None
 
 
@@ -240,21 +243,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "0c0724a4b54fc84811a5ed26c81269180e7cf9d27a4dc34ba654105f0e859b6e"
+NCU_TRAFFIC_SOURCES_SHA = "13a8df5fbc39946b56087d2ab4fec155d59c798dff335c3d07036680e0529957"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49406688,
-    "sssp_relax_into_invalid": 280748480,
-    "sssp_enqueue_invalid": 11001984,
-    "sssp_relax_updated": 149696000,
-    "sssp_invalidate_walk": 8524224,
-    "sssp_invalidate": 13741120,
-    "wcc_hook_all": 350259968,
-    "wcc_hook_updated": 139439232,
-    "insert": 241625600,
-    "delete": 199203200,
-    "query": 131710848,
-    "stage_dedup": 40140992,
-    "update_slab_pointers": 60634816,
+    "sssp_rounds": 49503200,
+    "sssp_relax_into_invalid": 280735744,
+    "sssp_enqueue_invalid": 11002432,
+    "sssp_relax_updated": 149732992,
+    "sssp_invalidate_walk": 8524608,
+    "sssp_invalidate": 13739264,
+    "wcc_hook_all": 350360064,
+    "wcc_hook_updated": 139455360,
+    "insert": 241723648,
+    "delete": 199035264,
+    "query": 130961152,
+    "stage_dedup": 40160192,
+    "update_slab_pointers": 60556864,
 }
 
 
@@ -850,12 +853,13 @@ def growth_experiment(S, split=32, horizon=8, epochs=20, lr=3e-3, load_factor=0.
 
 # ---------------------------------------------------------------- serving
 
-def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=8, retain_every=16,
-                     retain_sssp_every=64, n_req=None, log=None, keep_outputs=False, query_pool=1 << 21,
-                     insert_pool=1 << 22):
+def serve_experiment(G, R, ring, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=8, retain_every=16,
+                     retain_sssp_every=64, n_req=None, log=None, keep_outputs=False):
     """Plain one-launch-per-request execution against the continuous-batching
-    server on the same request stream R (synth.request_stream) over graph G.
-    First both run with every request available at once (capacity), then
+    server on the same request stream R (synth.request_stream) over graph G,
+    its updates and present queries reading the sequence of G's edges (in a
+    fixed random order) followed by `ring` (synth.new_edge_pool) and a copy
+    of the ring's first R.hi edges.  First both run with every request available at once (capacity), then
     with Poisson arrivals at each fraction of the plain capacity; latency =
     completion - arrival.  The outputs of a deterministic sample of requests
     (every retain_every-th; every retain_sssp_every-th SSSP) are kept and
@@ -870,17 +874,14 @@ def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=
     N = n_req or len(R.kind)
     kinds, sizes, offs, srcs = R.kind[:N], R.size[:N], R.offset[:N], R.source[:N]
     u = lambda a: mk.to_device_u32(a)  # noqa: E731
-    QP, IP = query_pool, insert_pool
-    rng = np.random.default_rng(11)
-    pick = rng.integers(0, E, QP)
-    live = rng.random(QP) < 0.5
-    qs = u(np.where(live, G.src[pick], rng.integers(0, V, QP)).astype(np.uint32))
-    qd = u(np.where(live, G.dst[pick], rng.integers(0, V, QP)).astype(np.uint32))
-    is_, id_ = synth.rmat_pairs(int(np.log2(V)), IP, synth.substream(3100, 1))
-    is_, id_ = u(is_), u(id_)
-    iw = u(synth.weights(IP, synth.substream(3100, 2), 1, 100))
     perm = synth.permutation(E, synth.substream(3100, 3))
-    ds, dd = u(G.src[perm]), u(G.dst[perm])
+    tail = min(int(R.hi), len(ring.src))
+    seq_s = u(np.concatenate([G.src[perm], ring.src, ring.src[:tail]]))
+    seq_d = u(np.concatenate([G.dst[perm], ring.dst, ring.dst[:tail]]))
+    seq_w = u(np.concatenate([G.w[perm], ring.w, ring.w[:tail]]))
+    AP = int(R.absent_pool)
+    abs_s, abs_d = (u(x) for x in synth.uniform_pairs(V, AP, synth.substream(3100, 4)))
+    qsrc = R.qsrc[:N]
     P_ = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
     maxn = int(sizes.max()) if N else 1
     ring = []
@@ -913,17 +914,18 @@ def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=
     def inputs(i):
         k, n, o = int(kinds[i]), int(sizes[i]), int(offs[i])
         if k == 0:
-            return qs[o:o + n], qd[o:o + n], None
+            if qsrc[i]:
+                return abs_s[o:o + n], abs_d[o:o + n], None
+            return seq_s[o:o + n], seq_d[o:o + n], None
         if k == 1:
-            return is_[o:o + n], id_[o:o + n], iw[o:o + n]
+            return seq_s[o:o + n], seq_d[o:o + n], seq_w[o:o + n]
         if k == 2:
-            o %= E
-            if o + n > E:
-                o = 0
-            return ds[o:o + n], dd[o:o + n], None
+            return seq_s[o:o + n], seq_d[o:o + n], None
         return None, None, None
 
-    pool = int((E + IP) / 15 * 1.3) + (1 << 21)
+    # every insert may claim a new slab pair: room for all of them (deleted
+    # pairs are never reused)
+    pool = int((E + int(R.inserted)) / 15 * 1.3) + (1 << 21)
 
     def fresh():
         b = mk.bucket_rule(V, u(G.src), 0.7)
@@ -1010,11 +1012,9 @@ def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=
         log(out)
     mism = [i for i in store_p if not all(torch.equal(x, y) for x, y in zip(store_p[i], store_s[i]) if x is not None)]
     out["compared_requests"] = len(store_p)
-    # what the retained requests applied or found: the share of insert and
-    # delete flags set and of queries present (the stream's deletes walk a
-    # fixed order of the initial edges, so once it has gone round, a delete
-    # of an edge already deleted is a no-op; inserts re-drawn from the
-    # insert pool after their first insertion are no-ops too)
+    # what the retained requests applied or found (the share of insert and
+    # delete flags set and of queries present), beside what the stream's
+    # live window predicts
     tally = {0: [0, 0], 1: [0, 0], 2: [0, 0]}
     for i, outs in store_p.items():
         k, n = int(kinds[i]), int(sizes[i])
@@ -1025,9 +1025,16 @@ def serve_experiment(G, R, rate_fracs=(0.5, 0.9), max_inflight=64, commit_every=
             words = outs[0].cpu().numpy().view(np.uint32)
             tally[0][0] += int(np.unpackbits(words.view(np.uint8), bitorder="little")[:n].sum())
             tally[0][1] += n
+    exp = {k: [int(R.applied[i]) for i in store_p if int(kinds[i]) == k and int(sizes[i])] for k in (1, 2)}
     out["retained_outcomes"] = {"insert_applied_frac": round(tally[1][0] / max(tally[1][1], 1), 4),
                                 "delete_applied_frac": round(tally[2][0] / max(tally[2][1], 1), 4),
-                                "query_present_frac": round(tally[0][0] / max(tally[0][1], 1), 4)}
+                                "query_present_frac": round(tally[0][0] / max(tally[0][1], 1), 4),
+                                "expected_insert_applied_frac": round(sum(exp[1]) / max(tally[1][1], 1), 4),
+                                "expected_delete_applied_frac": round(sum(exp[2]) / max(tally[2][1], 1), 4),
+                                "stream_insert_applied_frac": round(float(R.applied[R.kind == 1].sum())
+                                                                    / max(float(R.size[R.kind == 1].sum()), 1), 4),
+                                "stream_delete_applied_frac": round(float(R.applied[R.kind == 2].sum())
+                                                                    / max(float(R.size[R.kind == 2].sum()), 1), 4)}
     out["mismatches"] = len(mism)
     if keep_outputs:
         out["outputs"] = (store_p, store_s)
@@ -1201,13 +1208,16 @@ def run_served(args):
     torch.cuda.set_device(0)
     t0 = time.time()
     G = synth.powerlaw_graph(scale=21, draws=1 << 25)
-    R = synth.request_stream(100000, G.V, len(G.src))
+    ring = synth.new_edge_pool(G, 1 << 27)
+    R = synth.request_stream(100000, G.V, len(G.src), len(ring.src))
     gen_s = time.time() - t0
-    res = serve_experiment(G, R)
+    res = serve_experiment(G, R, ring)
     res.update({"workload": "R-MAT scale 21 graph (V=2,097,152, 2^25 draws, duplicates and self-loops dropped, "
-                            "weights U[1,100]) under a Poisson stream of 100,000 requests: 60% query, 15% insert, "
-                            "15% delete, 10% incremental SSSP from a pool of 16 sources; sizes log-uniform in "
-                            "[1, 2^20]; arrival rates 50% and 90% of the measured plain capacity",
+                            "weights U[1,100]) under a Poisson stream of 100,000 requests: 60%% query, 15%% insert, "
+                            "15%% delete, 10%% incremental SSSP from a pool of 16 sources; sizes log-uniform in "
+                            "[1, 2^20]; inserts of new R-MAT edges, deletes of live edges (a live window over the "
+                            "initial edges and a ring of %d new edges), half the queries inside the live window; "
+                            "arrival rates 50%% and 90%% of the measured plain capacity" % len(ring.src),
                 "gen_s": round(gen_s, 1)})
     return res
 

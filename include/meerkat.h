@@ -131,7 +131,9 @@ mk_status mk_graph_destroy(mk_graph *g);
  * d_inserted (n bytes, nullable): 1 where edge i was stored by this call.
  * If the pool runs out, the status becomes MK_ERR_POOL_EXHAUSTED and the
  * batch is applied partially: exactly the edges flagged 1 were stored.
- * Marks the touched slab lists as updated for the UpdateIterator. */
+ * Marks the touched slab lists as updated for the UpdateIterator and records
+ * each stored edge <src, dst, weight> in the epoch's inserted-edge log (grown
+ * on demand like the staging buffers). */
 mk_status mk_insert_batch(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w,
                           uint64_t n, uint8_t *d_inserted, void *stream);
 
@@ -330,8 +332,10 @@ mk_status mk_server_pending(mk_server *s, uint64_t *queued, uint64_t *inflight);
  * algorithm; later calls update the stored tree from the change log of the
  * current epoch: decremental prologue (invalidate the subtrees below deleted
  * tree edges, then relax every edge from a valid into an invalid vertex),
- * incremental prologue (relax the edges inserted since the last commit, found
- * with the UpdateIterator), then frontier rounds until no distance improves.
+ * incremental prologue (relax the edges inserted since the last commit: read
+ * from the epoch's inserted-edge log when the epoch holds no deletes, the
+ * paper's frontier of inserted edges, else found with the UpdateIterator),
+ * then frontier rounds until no distance improves.
  * Writes V entries to d_dist (distance, MK_NONE if unreachable) and d_parent
  * (the smallest-id vertex u with dist(u) + w(u,v) = dist(v); the source is
  * its own parent; MK_NONE if unreachable).  Either output may be NULL.  Path
@@ -368,8 +372,9 @@ mk_status mk_incr_multi(mk_graph *g, const mk_algo_req *h_reqs, uint32_t n, void
  * Union-Async hooking of the larger root under the smaller and full path
  * compression.  The first call, and any call whose epoch holds deletions
  * (the paper has no decremental WCC), runs the static pass over every edge;
- * otherwise only the edges inserted since the last commit are united, found
- * with the UpdateIterator.  d_label (V words): the smallest vertex id of each
+ * otherwise only the edges inserted since the last commit are united, read
+ * from the epoch's inserted-edge log (or found with the UpdateIterator when
+ * an insert of the epoch could not log).  d_label (V words): the smallest vertex id of each
  * vertex's component. */
 mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream);
 
@@ -515,7 +520,9 @@ mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *sla
  * decremental scan: slabs in use copied, slabs relaxed, live edges examined, edges
  * into invalidated vertices, invalidated vertices given a finite distance;
  * vertices visited by the invalidation pass; BFS/SSSP tree nodes written to
- * the caller's dist/parent arrays (then reserved words up to 32).
+ * the caller's dist/parent arrays; inserted-edge log entries read by the
+ * incremental BFS/SSSP prologue and by the incremental WCC pass (then
+ * reserved words up to 32).
  * The BFS/SSSP prologue words above count the inserted-edge prologue only.  Copies up to n
  * (<= 32) values to out (host); reset != 0 zeroes them.  Synchronises
  * `stream`. */

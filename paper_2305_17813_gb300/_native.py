@@ -28,7 +28,7 @@ COUNTER_NAMES = ["query_slabs", "insert_slabs", "insert_new_slabs", "delete_slab
                  "relax_edges", "relax_improved", "invalidated", "wcc_slabs", "wcc_edges", "commit_slabs",
                  "seed_lists", "seed_slabs", "seed_edges", "seed_improved", "wcc_upd_slabs", "wcc_upd_edges",
                  "rounds", "grid_barriers", "scan_owners", "scan_slabs", "scan_edges", "scan_targets", "scan_improved",
-                 "walk_vertices", "unpacked"]
+                 "walk_vertices", "unpacked", "seed_log", "wcc_log"]
 
 STATUS_NAMES = {
     MK_OK: "MK_OK",

@@ -51,11 +51,14 @@ mk_status ensure_scratch(mk_graph *g, uint64_t n, cudaStream_t s)
     device_free(g, g->d_tpos, g->table_size * 4);
     device_free(g, g->d_slot, g->scratch_cap * 4);
     device_free(g, g->d_cand, g->scratch_cap * 4);
+    device_free(g, g->d_iflags, g->scratch_cap);
     g->d_tpos = g->d_slot = g->d_cand = nullptr;
+    g->d_iflags = nullptr;
     g->scratch_cap = g->table_size = 0;
     MK_TRY(device_alloc(g, (void **)&g->d_tpos, table * 4));
     MK_TRY(device_alloc(g, (void **)&g->d_slot, cap * 4));
     MK_TRY(device_alloc(g, (void **)&g->d_cand, cap * 4));
+    MK_TRY(device_alloc(g, (void **)&g->d_iflags, cap));
     g->table_size = table;
     g->scratch_cap = cap;
     return MK_OK;
@@ -311,6 +314,7 @@ __global__ void k_clear_logs(DevState *st)
 {
     st->dlog_count = 0;
     st->ulog_count = 0;
+    st->ilog_count = 0;
 }
 
 // ---------------------------------------------------------------- host API
@@ -506,7 +510,9 @@ mk_status mk_graph_destroy(mk_graph *g)
     cudaFree(g->d_tpos);
     cudaFree(g->d_slot);
     cudaFree(g->d_cand);
+    cudaFree(g->d_iflags);
     cudaFree(g->d_dlog);
+    cudaFree(g->d_ilog);
     if (g->h_pinned)
         cudaFreeHost(g->h_pinned);
     for (auto &t : g->timed) {
@@ -541,6 +547,8 @@ mk_status mk_commit_batch(mk_graph *g, void *stream)
     g->epoch++;
     g->dlog_bound = 0;
     g->ulog_bound = 0;
+    g->ilog_bound = 0;
+    g->ilog_ok = true;
     g->epoch_has_deletes = false;
     return MK_OK;
 }

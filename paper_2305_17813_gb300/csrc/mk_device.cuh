@@ -33,6 +33,7 @@ constexpr uint8_t kInvalidLane = 0xFF;
 constexpr int kErrInvalid = -1;
 constexpr int kErrPool = -2;
 constexpr int kErrTimeout = -3;
+constexpr int kErrInternal = -6;
 
 // Work counters (slabs loaded, edges examined, ...) accumulated by the
 // kernels with one atomicAdd per warp; they give the algorithmic byte counts
@@ -65,6 +66,8 @@ enum Counter {
     kCtrScanImproved = 24, //   invalidated vertices given a finite distance
     kCtrWalkVertices = 25, // vertices visited by the invalidation pass
     kCtrUnpacked = 26,     // BFS/SSSP tree nodes written to the caller's dist/parent arrays
+    kCtrSeedLog = 27,      // inserted-edge log entries read by the incremental prologue
+    kCtrWccLog = 28,       // inserted-edge log entries read by the incremental WCC pass
     kNumCounters = 32
 };
 
@@ -79,7 +82,7 @@ struct DevState {
     int status;                    // sticky error word
     uint32_t dlog_count;           // entries in the delete log
     uint32_t ulog_count;           // entries in the updated-list log
-    uint32_t pad;
+    uint32_t ilog_count;           // entries in the inserted-edge log
     long long pool_used[kSlots];   // pool slabs allocated minus freed (kept with the bitmap), per slot
     unsigned long long ctr[kNumCounters][kSlots];
 };

@@ -74,10 +74,17 @@ struct mk_graph {
     uint64_t scratch_cap = 0;
     uint64_t table_size = 0;
     uint32_t *d_tpos = nullptr, *d_slot = nullptr, *d_cand = nullptr;
+    uint8_t *d_iflags = nullptr;  // an insert's per-edge stored flags when the caller asks for none
     // change log of the current epoch: deleted (src << 32 | dst)
     unsigned long long *d_dlog = nullptr;
     uint64_t dlog_cap = 0, dlog_bound = 0;
     uint64_t ulog_bound = 0;      // upper bound on the updated-list log's entries (<= H)
+    // inserted-edge log of the current epoch: <src, dst, stored weight, 0>
+    // of every edge an insert stored (ilog_ok false once an insert of the
+    // epoch could not log: the prologues then walk the updated lists)
+    uint4 *d_ilog = nullptr;
+    uint64_t ilog_cap = 0, ilog_bound = 0;
+    bool ilog_ok = true;
     uint64_t epoch = 0, change_seq = 0;
     bool epoch_has_deletes = false;
     std::map<std::pair<int, uint32_t>, mk::Consumer *> consumers;

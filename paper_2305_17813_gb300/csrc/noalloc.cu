@@ -29,7 +29,10 @@ __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__re
                                                    uint64_t n, const uint32_t *__restrict__ tpos,
                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
                                                    uint32_t max_hops, uint32_t *__restrict__ cand);
-__global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n);
+__global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n,
+                                                     const uint8_t *__restrict__ stored, const uint32_t *__restrict__ src,
+                                                     const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w,
+                                                     uint4 *ilog, uint32_t ilog_cap);
 
 namespace {
 
@@ -148,7 +151,10 @@ extern "C" mk_status mk_insert_batch_noalloc(mk_graph *g, const uint32_t *d_src,
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
     const uint32_t max_hops = g->v.P + 2;
     k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, tpos, slot, d_inserted, max_hops, cand);
-    k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, cand, n);
+    // no inserted-edge log (growing it could allocate): this epoch's
+    // incremental prologues walk the updated lists instead
+    g->ilog_ok = false;
+    k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, cand, n, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
     g->launches += 3;
     MK_CUDA(cudaGetLastError());
     return MK_OK;

@@ -657,6 +657,84 @@ __global__ void __launch_bounds__(256, 5) k_relax_updated(RoundArgs a)
     count_add(g.st, kCtrSeedImproved, improved);
 }
 
+// Incremental seeds from the inserted-edge log (the paper's incremental
+// frontier is the batch's inserted edges), used when the epoch holds no
+// deletes, so every logged edge is still live with its stored weight: each
+// lane takes four consecutive log entries <src, dst, w> and relaxes them
+// together, as relax_edges4 does a slab's four pairs (the sources' tree
+// nodes, the targets' tree nodes, the atomic minima of the candidates that
+// beat them, then the improved targets' vertex index entries and round
+// stamps), and enqueues the lists of each vertex it lowered first in this
+// round.  Two dependent gathers per edge instead of the walk's five loads
+// per updated list (log entry, list source, marker, source node, slab).
+__global__ void __launch_bounds__(256) k_relax_inserted(RoundArgs a, const uint4 *__restrict__ ilog, uint32_t cap)
+{
+    __shared__ BlockFrontier bq;
+    bq_init(bq);
+    const uint32_t n = min(__ldg(&a.g.st->ilog_count), cap);
+    const uint32_t round = __ldg(a.ctr + kRid) + 1;
+    int *overflow = (int *)(a.ctr + kOverflow);
+    unsigned long long entries = 0, edges = 0, improved = 0;
+    const uint64_t lane4 = (uint64_t)lane_id() * 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 4;
+    for (uint64_t wb = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull) * 4; wb < n; wb += stride) {
+        uint32_t x[4], y[4], nd[4];
+        bool up[4];
+        unsigned long long cur[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t i = wb + lane4 + k;
+            const uint4 e = i < n ? __ldcs(&ilog[i]) : make_uint4(0, 0, 0, 0);
+            x[k] = e.x;
+            y[k] = e.y;
+            nd[k] = e.z;
+            up[k] = i < n;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            entries += __popc(__ballot_sync(kFull, up[k]));
+            const uint32_t dx = up[k] ? node_dist(__ldcg(&a.D[x[k]])) : kInf32;
+            const unsigned long long d = (unsigned long long)dx + (a.unit ? 1u : nd[k]);
+            up[k] = up[k] && dx != kInf32 && d < kInf32;
+            nd[k] = (uint32_t)d;
+        }
+        auto cand = [&](int k) { return ((unsigned long long)nd[k] << 32) | x[k]; };
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            edges += __popc(__ballot_sync(kFull, up[k]));
+            cur[k] = up[k] ? __ldcg(&a.D[y[k]]) : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (up[k] && cand(k) < cur[k])
+                cur[k] = atomicMin(&a.D[y[k]], cand(k));
+            else
+                up[k] = false;
+        uint2 vi[4];
+        uint32_t st[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            up[k] = up[k] && cand(k) < cur[k];
+            vi[k] = make_uint2(0, 0);
+            st[k] = round;
+            if (up[k]) {
+                vi[k] = a.g.vinfo[y[k]];
+                st[k] = atomicExch(&a.stamp[y[k]], round);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            up[k] = up[k] && st[k] != round;
+            improved += __popc(__ballot_sync(kFull, up[k]));
+            enqueue_lists_block(bq, y[k], up[k], vi[k], a.front[0], a.ctr + kCnt0, a.cap, overflow);
+        }
+    }
+    bq_flush(bq, a.front[0], a.ctr + kCnt0, a.cap, overflow);
+    count_add(a.g.st, kCtrSeedLog, entries);
+    count_add(a.g.st, kCtrSeedEdges, edges);
+    count_add(a.g.st, kCtrSeedImproved, improved);
+}
+
 // Ends a call of the host-driven fallback (the round kernel does this
 // itself): advances the round stamp past every id used (`rounds` rounds),
 // reports an overflowed frontier.
@@ -1108,8 +1186,18 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
                 return cudaSuccess;
             }));
         }
-        // incremental prologue: edges inserted since the last commit
-        if (g->ulog_bound) {
+        // incremental prologue: edges inserted since the last commit, from
+        // the inserted-edge log when the epoch holds no deletes (every
+        // logged edge still live), else by walking the updated lists from
+        // their UpdateIterator markers
+        if (g->ulog_bound && !g->epoch_has_deletes && g->ilog_ok && g->d_ilog) {
+            MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
+                const uint64_t threads = (g->ilog_bound + 3) / 4;
+                k_relax_inserted<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 8), 256, 0, s>>>(
+                    a, g->d_ilog, (uint32_t)g->ilog_cap);
+                return cudaSuccess;
+            }));
+        } else if (g->ulog_bound) {
             MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
                 // one 4-lane group per logged list
                 const uint64_t threads = g->ulog_bound * 4;

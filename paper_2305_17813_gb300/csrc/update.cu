@@ -505,12 +505,23 @@ __global__ void __launch_bounds__(256, 6) k_insert(GView g, const uint32_t *__re
 
 // Appends the lists nominated by k_insert (cand[i] != kNil) to the
 // updated-list log, with one global atomicAdd per block.
-__global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n)
+__global__ void __launch_bounds__(256) k_log_updated(GView g, const uint32_t *__restrict__ cand, uint64_t n,
+                                                     const uint8_t *__restrict__ stored, const uint32_t *__restrict__ src,
+                                                     const uint32_t *__restrict__ dst, const uint32_t *__restrict__ w,
+                                                     uint4 *ilog, uint32_t ilog_cap)
 {
     __shared__ uint32_t s2[2];
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint32_t L = i < n ? cand[i] : kNil;
     block_enqueue(g.ulog, &g.st->ulog_count, g.H, L, L != kNil, s2); // a list is logged once per epoch: fits
+    // the inserted-edge log: <src, dst, stored weight> of each edge stored
+    // by this batch (the host sized the log for every insert of the epoch)
+    if (stored) {
+        const bool ins = i < n && stored[i] != 0;
+        const uint4 rec = ins ? make_uint4(src[i], dst[i], w ? w[i] : 1u, 0u) : make_uint4(0, 0, 0, 0);
+        if (!block_enqueue(ilog, &g.st->ilog_count, ilog_cap, rec, ins, s2))
+            set_status(g.st, kErrInternal);
+    }
 }
 
 // One block per tile of 256 edges, one warp per 32 sorted edges: find each
@@ -665,15 +676,38 @@ mk_status insert_impl(mk_graph *g, const uint32_t *d_src, const uint32_t *d_dst,
     g->change_seq++;
     if (n == 0)
         return MK_OK;
-    if (d_inserted)
-        MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
+    // the inserted-edge log must hold every insert of the epoch
+    const uint64_t need = g->ilog_bound + n;
+    if (g->ilog_ok && need > g->ilog_cap) {
+        uint64_t cap = std::max<uint64_t>(need, g->ilog_cap * 2);
+        cap = std::min<uint64_t>(cap, 0xFFFFFFFFull);
+        uint4 *nl = nullptr;
+        if (need > cap || device_alloc(g, (void **)&nl, cap * 16) != MK_OK) {
+            g->ilog_ok = false; // the prologues walk the updated lists instead
+        } else {
+            if (g->d_ilog) {
+                MK_CUDA(cudaMemcpyAsync(nl, g->d_ilog, g->ilog_bound * 16, cudaMemcpyDeviceToDevice, s));
+                MK_CUDA(cudaStreamSynchronize(s));
+                device_free(g, g->d_ilog, g->ilog_cap * 16);
+            }
+            g->d_ilog = nl;
+            g->ilog_cap = cap;
+        }
+    }
     MK_TRY(stage(g, d_src, d_dst, d_w, n, s));
+    // the stored flags feed the log: the caller's array or the staging one
+    uint8_t *fl = d_inserted ? d_inserted : g->d_iflags;
+    MK_CUDA(cudaMemsetAsync(fl, 0, n, s));
     g->ulog_bound = std::min<uint64_t>(g->v.H, g->ulog_bound + n);
+    const bool log = g->ilog_ok;
+    if (log)
+        g->ilog_bound = need;
     const uint32_t max_hops = g->v.P + 2;
     return timed(g, "insert", s, 2, [&]() {
-        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, g->d_tpos, g->d_slot, d_inserted,
-                                                  max_hops, g->d_cand);
-        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_cand, n);
+        k_insert<<<grid_for(n, 256), 256, 0, s>>>(g->v, d_src, d_dst, d_w, n, g->d_tpos, g->d_slot, fl, max_hops,
+                                                  g->d_cand);
+        k_log_updated<<<grid_for(n, 256), 256, 0, s>>>(g->v, g->d_cand, n, log ? fl : nullptr, d_src, d_dst, d_w,
+                                                       g->d_ilog, (uint32_t)g->ilog_cap);
         return cudaSuccess;
     });
 }

@@ -250,6 +250,29 @@ __global__ void __launch_bounds__(256, 5) k_uf_hook(GView g, uint32_t *p, uint32
     count_add(g.st, kCtrWccUpdEdges, edges);
 }
 
+// Incremental pass from the inserted-edge log (insert-only epochs, so every
+// logged edge is live): each lane unites the two ends of one logged edge
+// (a one-lane group_union: both roots found in lockstep, the larger hooked
+// under the smaller).
+__global__ void __launch_bounds__(256) k_uf_hook_log(DevState *st, const uint4 *__restrict__ ilog, uint32_t cap,
+                                                     uint32_t *p, int *failed)
+{
+    const uint32_t n = min(__ldg(&st->ilog_count), cap);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long entries = 0;
+    for (uint64_t wb = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; wb < n; wb += stride) {
+        const uint64_t i = wb + lane_id();
+        const uint4 e = i < n ? __ldcs(&ilog[i]) : make_uint4(0, 0, 0, 0);
+        const uint32_t x[2] = {e.x, e.y};
+        const bool act[2] = {i < n, i < n};
+        entries += __popc(__ballot_sync(kFull, i < n));
+        if (!group_union<1, 2>(p, x, act, 1u << 20) && lane_id() == 0)
+            *failed = 1;
+    }
+    count_add(st, kCtrWccLog, entries);
+    count_add(st, kCtrWccUpdEdges, entries);
+}
+
 // Static pass as a streaming scan over the whole slab array instead of chain
 // walks.  A warp takes 32 consecutive slabs at a time: one coalesced load of
 // their owners (per-slab source, kNil for an unused pool slab; read a chunk
@@ -372,7 +395,14 @@ extern "C" mk_status mk_incr_wcc(mk_graph *g, uint32_t *d_label, void *stream)
             return cudaSuccess;
         }));
     }
-    if (incremental) {
+    if (incremental && g->ilog_ok && g->d_ilog) {
+        MK_TRY(timed(g, "wcc_hook_updated", s, 1, [&]() {
+            const uint64_t threads = std::max<uint64_t>(g->ilog_bound, 1);
+            k_uf_hook_log<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 8), 256, 0, s>>>(
+                g->d_state, g->d_ilog, (uint32_t)g->ilog_cap, c->uf, failed);
+            return cudaSuccess;
+        }));
+    } else if (incremental) {
         MK_TRY(timed(g, "wcc_hook_updated", s, 1, [&]() {
             // one 4-lane group per logged list
             const uint64_t threads = std::max<uint64_t>(g->ulog_bound, 1) * 4;

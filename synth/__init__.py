@@ -452,37 +452,84 @@ def growth_stream(scale: int = 22, draws: int = 1 << 26, n_batches: int = 64, de
     return Batch(V=V, scale=scale, init=init, batches=batches)
 
 
-def request_stream(n_req: int, V: int, n_edges: int, mix=(0.6, 0.15, 0.15, 0.1), lo: int = 1, hi: int = 1 << 20,
-                   n_sources: int = 16, query_pool: int = 1 << 21, insert_pool: int = 1 << 22,
-                   seed: int = 3000) -> Batch:
+def new_edge_pool(g: Batch, draws: int, seed: int = 3100, wlo: int = 1, whi: int = 100) -> Batch:
+    """Distinct R-MAT edges of g's scale that are not edges of g, self-loops
+    dropped, in draw order (seed `seed`), with weights U[wlo, whi]."""
+    s, d = rmat_pairs(g.scale, draws, substream(seed, TAG_PAIRS))
+    s, d = dedup_pairs(s, d, g.V, drop_self=True)
+    live = EdgeSet(len(g.src))
+    live.add(g.src, g.dst)
+    keep = ~live.contains(s, d)
+    s, d = s[keep].copy(), d[keep].copy()
+    return Batch(src=s, dst=d, w=weights(len(s), substream(seed, TAG_W), wlo, whi))
+
+
+def request_stream(n_req: int, V: int, E0: int, ring: int, mix=(0.6, 0.15, 0.15, 0.1), lo: int = 1,
+                   hi: int = 1 << 20, n_sources: int = 16, absent_pool: int = 1 << 21, seed: int = 3000) -> Batch:
     """Mixed request stream for the serving workload (seed `seed`).
 
     kinds: 0 query, 1 insert, 2 delete, 3 incremental SSSP with probabilities
-    `mix`; sizes log-uniform in [lo, hi] (update and query requests);
-    SSSP sources drawn from a fixed pool of n_sources random vertices (so a
+    `mix`; sizes log-uniform in [lo, hi] (update and query requests); SSSP
+    sources drawn from a fixed pool of n_sources random vertices (so a
     source recurs and its tree is kept incrementally); `gaps`: unit-rate
-    exponential inter-arrival times (scale by 1 / rate).  Request inputs are
-    slices of pools: queries at a random offset of a query pool, inserts at
-    a random offset of an insert pool, deletes at consecutive offsets of a
-    fixed permutation of the initial edges (so they hit live edges until it
-    wraps around)."""
+    exponential inter-arrival times (scale by 1 / rate).
+
+    Update requests and the present queries read slices of one sequence of
+    edges: the E0 initial edges in a fixed random order, then a ring of
+    `ring` distinct new edges (`new_edge_pool`), stored followed by a copy of
+    its first `hi` edges so that every slice of at most `hi` edges starting
+    in the ring is contiguous (`seq_index` maps a position of the unrolled
+    sequence to the stored one).  In arrival order an insert cursor i
+    (starting at E0) and a delete cursor d (starting at 0) walk the unrolled
+    sequence, and the live edges are exactly its positions [d, i):
+
+    * an insert takes [i, i + n) and i advances by n: new edges, unless the
+      window [d, i) outgrew the ring (`applied` counts the new ones);
+    * a delete takes [d, d + n): its first min(n, i - d) edges are live, the
+      rest not yet inserted (no-ops); d advances to min(d + n, i);
+    * a query takes, with probability 1/2, a slice inside [d, i) (every
+      edge present), and otherwise a slice of a pool of `absent_pool`
+      uniform pairs (absent but for chance hits); `qsrc` = 0 / 1.
+
+    `offset` is the stored position (sequence or absent pool) of each
+    request's slice; `applied` the expected count of applied updates."""
     u = np.frombuffer(np.ascontiguousarray(weights(n_req, substream(seed, TAG_PAIRS), 0, 999999)).tobytes(),
                       np.uint32).astype(np.float64) / 1e6
     cum = np.cumsum(mix)
-    kind = np.searchsorted(cum, u, side="right").astype(np.uint8)
-    kind = np.minimum(kind, 3)
+    kind = np.minimum(np.searchsorted(cum, u, side="right"), 3).astype(np.uint8)
     size = log_uniform(n_req, lo, hi, substream(seed, TAG_W)).astype(np.int64)
     srcs = uniform_pairs(V, n_sources, substream(seed, TAG_LONG))[0]
     pick = weights(n_req, substream(seed, TAG_LOCAL), 0, n_sources - 1)
     source = srcs[pick]
-    off_raw = uniform_pairs(0xFFFFFFFF, n_req, substream(seed, TAG_QRY))[0].astype(np.int64)
-    offset = np.zeros(n_req, np.int64)
-    q = kind == 0
-    offset[q] = off_raw[q] % np.maximum(query_pool - size[q], 1)
-    ins = kind == 1
-    offset[ins] = off_raw[ins] % np.maximum(insert_pool - size[ins], 1)
-    dl = kind == 2
-    offset[dl] = (np.cumsum(np.where(dl, size, 0)) - size)[dl] % max(1, n_edges)
+    coin = weights(n_req, substream(seed, TAG_QPERM), 0, 1)
+    raw = uniform_pairs(0xFFFFFFFF, n_req, substream(seed, TAG_QRY))[0].astype(np.int64)
     size[kind == 3] = 0
-    gaps = exponential_gaps(n_req, 1.0, substream(seed, TAG_QPERM))
-    return Batch(kind=kind, size=size, source=source, offset=offset, gaps=gaps, sources=srcs)
+    offset = np.zeros(n_req, np.int64)
+    qsrc = np.zeros(n_req, np.uint8)
+    applied = np.zeros(n_req, np.int64)
+    i_cur, d_cur = E0, 0
+    for r in range(n_req):
+        k, n = int(kind[r]), int(size[r])
+        if k == 1:
+            offset[r] = seq_index(i_cur, E0, ring)
+            applied[r] = n - min(n, max(0, i_cur + n - ring - d_cur))
+            i_cur += n
+        elif k == 2:
+            offset[r] = seq_index(d_cur, E0, ring)
+            applied[r] = min(n, max(0, i_cur - d_cur))
+            d_cur = min(d_cur + n, i_cur)
+        elif k == 0:
+            if coin[r] == 0 and i_cur - d_cur >= n:
+                offset[r] = seq_index(d_cur + int(raw[r] % (i_cur - d_cur - n + 1)), E0, ring)
+            else:
+                qsrc[r] = 1
+                offset[r] = int(raw[r] % max(absent_pool - n, 1))
+    gaps = exponential_gaps(n_req, 1.0, substream(seed, TAG_QPERM + 16))
+    return Batch(kind=kind, size=size, source=source, offset=offset, qsrc=qsrc, applied=applied, gaps=gaps,
+                 sources=srcs, inserted=int(size[kind == 1].sum()), E0=E0, ring=ring, hi=hi,
+                 absent_pool=absent_pool)
+
+
+def seq_index(v: int, E0: int, ring: int) -> int:
+    """Stored position of position v of the unrolled request sequence."""
+    return v if v < E0 else E0 + (v - E0) % ring

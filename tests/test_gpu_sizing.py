@@ -159,7 +159,7 @@ def test_learned_sizing_shortens_chains_with_identical_results(cuda_lib):
     import synth
 
     torch, mk, sizing = _mods()
-    S = synth.growth_stream(scale=15, draws=1 << 19, n_batches=16)
+    S = synth.growth_stream(scale=18, draws=1 << 22, n_batches=16)
     res = bench.growth_experiment(S, split=8, horizon=2, epochs=12, keep_graphs=True)
     gl, gr = res.pop("graphs")
     # identical results on both layouts, and identical to the oracle

@@ -105,3 +105,34 @@ def test_edge_set_matches_a_python_set():
                 ref.discard((a, b))
         assert got.tolist() == want
         assert len(es) == len(ref)
+
+
+def test_serving_stream_live_window_on_the_oracle():
+    """Replayed on the oracle in arrival order, the serving stream's inserts
+    add exactly the predicted new edges, its deletes remove the predicted
+    live ones, and its live-window queries are all present."""
+    import oracle
+
+    G = synth.powerlaw_graph(scale=12, draws=1 << 15)
+    ring = synth.new_edge_pool(G, 1 << 17)
+    R = synth.request_stream(600, G.V, len(G.src), len(ring.src), hi=1 << 11, n_sources=4, absent_pool=1 << 14)
+    perm = synth.permutation(len(G.src), synth.substream(3100, 3))
+    tail = min(R.hi, len(ring.src))
+    ss = np.concatenate([G.src[perm], ring.src, ring.src[:tail]])
+    sd = np.concatenate([G.dst[perm], ring.dst, ring.dst[:tail]])
+    sw = np.concatenate([G.w[perm], ring.w, ring.w[:tail]])
+    o = oracle.OracleGraph(G.V)
+    o.insert(G.src, G.dst, G.w)
+    n_present = 0
+    for i in range(600):
+        k, n, off = int(R.kind[i]), int(R.size[i]), int(R.offset[i])
+        if k == 1:
+            assert int(o.insert(ss[off:off + n], sd[off:off + n], sw[off:off + n]).sum()) == R.applied[i] == n
+        elif k == 2:
+            assert int(o.delete(ss[off:off + n], sd[off:off + n]).sum()) == R.applied[i]
+        elif k == 0 and not R.qsrc[i] and n:
+            bm, _ = o.query(ss[off:off + n], sd[off:off + n])
+            assert oracle.bitmap_to_bool(bm, n).all()
+            n_present += 1
+    assert n_present > 50
+    assert R.applied[R.kind == 2].sum() == R.size[R.kind == 2].sum()
