@@ -243,21 +243,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "13a8df5fbc39946b56087d2ab4fec155d59c798dff335c3d07036680e0529957"
+NCU_TRAFFIC_SOURCES_SHA = "4a52c118a3d4eeeb0ca653389a2bab5e48a4c0dcf12c0bdb492b99fc18218a2b"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49503200,
-    "sssp_relax_into_invalid": 280735744,
-    "sssp_enqueue_invalid": 11002432,
-    "sssp_relax_updated": 149732992,
-    "sssp_invalidate_walk": 8524608,
-    "sssp_invalidate": 13739264,
-    "wcc_hook_all": 350360064,
-    "wcc_hook_updated": 139455360,
-    "insert": 241723648,
-    "delete": 199035264,
-    "query": 130961152,
-    "stage_dedup": 40160192,
-    "update_slab_pointers": 60556864,
+    "sssp_rounds": 49606144,
+    "sssp_relax_into_invalid": 280873088,
+    "sssp_enqueue_invalid": 11004928,
+    "sssp_relax_updated": 26477504,
+    "sssp_invalidate_walk": 8524288,
+    "sssp_invalidate": 13743552,
+    "wcc_hook_all": 350659840,
+    "wcc_hook_updated": 19097216,
+    "insert": 255045120,
+    "delete": 198536320,
+    "query": 130993280,
+    "stage_dedup": 40137152,
+    "update_slab_pointers": 60560576,
 }
 
 
