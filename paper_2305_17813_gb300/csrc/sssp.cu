@@ -1292,12 +1292,9 @@ mk_status run_multi(mk_graph *g, const mk_algo_req *reqs, uint32_t n, cudaStream
     // incremental prologue: one walk over the updated lists for all states
     if (inc.k) {
         const size_t smem = inc.k * sizeof(BlockFrontier);
-        static bool attr = false;
-        if (!attr) {
-            MK_CUDA(cudaFuncSetAttribute(k_relax_updated_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxMulti * sizeof(BlockFrontier))));
-            attr = true;
-        }
+        // (a function attribute of the current device: set on every call)
+        MK_CUDA(cudaFuncSetAttribute(k_relax_updated_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kMaxMulti * sizeof(BlockFrontier))));
         MK_TRY(timed(g, "sssp_relax_updated", s, 1, [&]() {
             const uint64_t threads = g->ulog_bound * 4;
             k_relax_updated_multi<<<std::min<uint32_t>(grid_for(threads, 256), num_sms() * 10), 256, smem, s>>>(inc);
@@ -1308,12 +1305,8 @@ mk_status run_multi(mk_graph *g, const mk_algo_req *reqs, uint32_t n, cudaStream
     const int grid = rounds_grid(g->tune.rounds_blocks_per_sm);
     const int block = rounds_block(g->tune.rounds_blocks_per_sm);
     const size_t smem = n * sizeof(BlockFrontier);
-    static bool rattr = false;
-    if (!rattr) {
-        MK_CUDA(cudaFuncSetAttribute(k_rounds_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kMaxMulti * sizeof(BlockFrontier))));
-        rattr = true;
-    }
+    MK_CUDA(cudaFuncSetAttribute(k_rounds_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kMaxMulti * sizeof(BlockFrontier))));
     void *args[] = {&m};
     mk_status st = MK_ERR_CUDA;
     if (!g->dbg_host_rounds)

@@ -54,6 +54,15 @@ def test_host_side_argument_errors_need_no_device(lib):
     assert L.mk_graph_create(0xFFFFFFFE, 0, 1, None, None, ctypes.byref(out)) == mk.MK_ERR_INVALID_ARG
     assert L.mk_insert_batch(None, None, None, None, 0, None, None) == mk.MK_ERR_INVALID_ARG
     assert L.mk_last_error(None) == mk.MK_ERR_INVALID_ARG
+    # the later entry points refuse a null graph the same way
+    assert L.mk_update_multi(None, None, 0, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_incr_multi(None, None, 1, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_pagerank(None, None, 0, 0.85, 1e-7, 10, None, None, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_tc_count(None, None, None, None, 0, None, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_tc_static(None, None, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_tc_update(None, None, None, None, 0, 0, None, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_l2_window(None, mk.MK_L2_VINFO, None, None) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_debug_set(None, 1, 0) == mk.MK_ERR_INVALID_ARG
     assert L.mk_version().decode().startswith("meerkat-gb300")
 
 

@@ -120,3 +120,25 @@ def test_triangles_static_and_after_batches(cuda_lib):
         assert g.triangles() == count
         g.commit()
     assert g.last_error() == mk.MK_OK
+
+
+def test_analytics_degenerate_graphs(cuda_lib):
+    """No edges: every vertex dangles, the teleport term alone gives ranks
+    1 / V.  A grid (no triangles) counts 0, and an empty batch changes
+    nothing."""
+    mk = _mk()
+    g = mk.Graph(1000, edge_capacity_hint=16, buckets=1)
+    pr, it, _ = g.pagerank(eps=1e-7)
+    assert np.allclose(pr.cpu().numpy(), 1e-3, rtol=1e-6) and it <= 2
+    g.close()
+    s, d = synth.grid_pairs(30, 30)
+    grid = mk.Graph(900, edge_capacity_hint=len(s) * 2, buckets=2)
+    grid.insert(s, d)
+    assert grid.triangles() == 0
+    upd = mk.Graph(900, edge_capacity_hint=16, buckets=1)
+    assert grid.triangle_delta(upd, np.zeros(0, np.uint32), np.zeros(0, np.uint32), False) == 0
+    lib = mk.load()
+    assert lib.mk_l2_window(grid.handle, 7, None, None) == mk.MK_ERR_INVALID_ARG
+    assert grid.last_error() == mk.MK_OK
+    upd.close()
+    grid.close()
