@@ -383,6 +383,8 @@ class StepRunner:
             hooks["before_delete"]()
         mk.check(lib.mk_delete_batch(h, P(bt["del_src"]), P(bt["del_dst"]), n, P(fl_d), sp), "del")
         ev[6].record(stream)
+        if "after_delete" in hooks:
+            hooks["after_delete"]()
         ws.wait_event(ev[6])
         wev[2].record(ws)
         mk.check(lib.mk_incr_wcc(h, P(out["lab"]), wsp), "wcc")
@@ -391,8 +393,12 @@ class StepRunner:
         # the decremental BFS/SSSP (a commit moves only update markers)
         mk.check(lib.mk_query_batch(h, P(bt["q_src"]), P(bt["q_dst"]), n, P(bm), None, wsp), "query")
         wev[4].record(ws)
+        if "after_side" in hooks:
+            hooks["after_side"](ws)
         mk.check(lib.mk_incr_bfs(h, src, P(out["bd"]), P(out["bp"]), sp), "bfs")
         ev[7].record(stream)
+        if "after_bfs" in hooks:
+            hooks["after_bfs"]()
         mk.check(lib.mk_incr_sssp(h, src, P(out["sd"]), P(out["sp"]), sp), "sssp")
         ev[8].record(stream)
         stream.wait_event(wev[3])
@@ -654,8 +660,9 @@ def run_e2e(R, batches, B, dist, units_total):
     """Steps through the C ABI with the inputs in pinned host memory: every
     step copies its inputs in and its results out inside the timed region
     (insert and delete flags, the query bitmap, BFS and SSSP distances and
-    parents, WCC labels); the copies that later phases need overlap the
-    earlier phases on a copy stream."""
+    parents, WCC labels).  The inputs of later phases come in, and every
+    result leaves as soon as the step no longer writes it, on a copy stream
+    beside the phases still running; only the SSSP tree leaves at the end."""
     torch, mk = R.torch, R.mk
     device, stream, V = R.device, R.stream, R.V
     host = [{k: torch.from_numpy(np.ascontiguousarray(bt[k]).view(np.int32)).pin_memory() for k in BATCH_KEYS}
@@ -682,20 +689,29 @@ def run_e2e(R, batches, B, dist, units_total):
             for key in ("del_src", "del_dst", "q_src", "q_dst"):
                 stage[key].copy_(host[k][key], non_blocking=True)
             ready.record(copy)
-        inserted = torch.cuda.Event()
 
-        def after_insert():
-            inserted.record(stream)
-            copy.wait_event(inserted)
+        def on_copy(src_stream, pairs):
+            """Copy stream waits for src_stream's work so far, then copies."""
+            done = torch.cuda.Event()
+            done.record(src_stream)
+            copy.wait_event(done)
             with torch.cuda.stream(copy):
-                h_fl_i.copy_(fl_i, non_blocking=True)
+                for dst, t in pairs:
+                    dst.copy_(t, non_blocking=True)
 
-        R.step(stage, B, outs, e[1:13], R.events(5),
-               {"after_insert": after_insert, "before_delete": lambda: stream.wait_event(ready)})
-        h_fl_d.copy_(fl_d, non_blocking=True)
-        h_bm.copy_(bm, non_blocking=True)
-        for key, t in R.out.items():
-            h_res[key].copy_(t, non_blocking=True)
+        hooks = {
+            "after_insert": lambda: on_copy(stream, [(h_fl_i, fl_i)]),
+            "before_delete": lambda: stream.wait_event(ready),
+            "after_delete": lambda: on_copy(stream, [(h_fl_d, fl_d)]),
+            # results that nothing later in the step rewrites leave while
+            # the rest of the step runs: the query bitmap and the WCC labels
+            # (second stream), the BFS tree (main stream, beside the SSSP)
+            "after_side": lambda ws: on_copy(ws, [(h_bm, bm), (h_res["lab"], R.out["lab"])]),
+            "after_bfs": lambda: on_copy(stream, [(h_res["bd"], R.out["bd"]), (h_res["bp"], R.out["bp"])]),
+        }
+        R.step(stage, B, outs, e[1:13], R.events(5), hooks)
+        for key in ("sd", "sp"):
+            h_res[key].copy_(R.out[key], non_blocking=True)
         stream.wait_stream(copy)
         e[13].record(stream)
         torch.cuda.synchronize()

@@ -425,6 +425,52 @@ mk_status mk_tc_static(mk_graph *g, uint64_t *h_triangles, void *stream);
 mk_status mk_tc_update(mk_graph *g_post, mk_graph *g_upd, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                        int deletion, int64_t *h_delta, void *stream);
 
+/* ------------------------------------------------ ConcurrentSet layout */
+/*
+ * An unweighted graph in the ConcurrentSet layout (paper, Sec. "Motivation":
+ * SlabHash's ConcurrentSet beside the ConcurrentMap; the paper keeps the
+ * graphs of BFS and WCC this way): each 128-byte slab holds 31 destination
+ * keys (lanes 0..30) and the next-slab index (lane 31), about twice the 15
+ * pairs of the weighted store's slab, so the slab array and the passes that
+ * stream it are about half as large.  The conventions of the weighted store
+ * hold (head slabs located by an exclusive scan of per-vertex bucket counts,
+ * a bitmap pool, EMPTY / TOMBSTONE keys never reused, set semantics with the
+ * first occurrence of a repeated pair applied, device errors in a sticky
+ * status word read by mk_set_last_error).  BFS and WCC run statically.
+ */
+typedef struct mk_set_graph mk_set_graph;
+/* Bucket counts max(1, ceil(outdeg / (load_factor * 31))) (V outputs). */
+mk_status mk_set_bucket_rule(uint32_t V, const uint32_t *d_src, uint64_t n, float load_factor, uint32_t *d_buckets,
+                             void *stream);
+/* Creates an empty set graph (every vertex `buckets` buckets, or
+ * d_bucket_per_vertex[v]); the pool holds edge_capacity_hint / 31 + lists / 8
+ * + 1024 slabs.  Synchronises `stream`. */
+mk_status mk_set_create(uint32_t V, uint64_t edge_capacity_hint, uint32_t buckets, const uint32_t *d_bucket_per_vertex,
+                        void *stream, mk_set_graph **out);
+mk_status mk_set_destroy(mk_set_graph *g);
+/* Insert / delete / query n edges as mk_insert_batch / mk_delete_batch /
+ * mk_query_batch do (no weights; flags and bitmap nullable / required
+ * alike).  One warp handles one edge at a time with 128-byte slab loads. */
+mk_status mk_set_insert_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              uint8_t *d_inserted, void *stream);
+mk_status mk_set_delete_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              uint8_t *d_deleted, void *stream);
+mk_status mk_set_query_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                             uint32_t *d_bitmap, void *stream);
+/* Static BFS from `source`, level by level (the host reads each level's
+ * frontier size): d_dist = hop counts (MK_NONE unreachable), d_parent = the
+ * smallest-id u with a live edge u -> v and dist(u) + 1 = dist(v) (the source
+ * its own parent).  Synchronises `stream` once per level. */
+mk_status mk_set_bfs(mk_set_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream);
+/* Static WCC: d_label = the smallest vertex id of each vertex's component. */
+mk_status mk_set_wcc(mk_set_graph *g, uint32_t *d_label, void *stream);
+/* Lists (head slabs), slabs in use (heads + pool slabs claimed) and device
+ * bytes held (host outputs, nullable).  Synchronises `stream`. */
+mk_status mk_set_stats(mk_set_graph *g, uint64_t *h_lists, uint64_t *h_slabs_in_use, uint64_t *h_device_bytes,
+                       void *stream);
+/* Synchronises the device, returns the sticky device status and clears it. */
+mk_status mk_set_last_error(mk_set_graph *g);
+
 /* -------------------------------------------------------- learned sizing */
 /*
  * Learned slab sizing.  The paper fixes each vertex's bucket count a priori

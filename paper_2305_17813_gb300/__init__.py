@@ -22,7 +22,7 @@ from ._native import (MK_ERR_CUDA, MK_ERR_INTERNAL, MK_ERR_INVALID_ARG, MK_ERR_N
 __all__ = [
     "Graph", "load", "MkError", "MK_OK", "MK_ERR_INVALID_ARG", "MK_ERR_POOL_EXHAUSTED", "MK_ERR_TIMEOUT",
     "MK_ERR_CUDA", "MK_ERR_NO_MEMORY", "MK_ERR_INTERNAL", "MK_NONE", "MK_INVALID_LANE", "bucket_rule",
-    "to_device_u32", "to_numpy_u32", "Batcher", "Server", "MK_L2_NONE", "MK_L2_VINFO", "MK_L2_HEADS", "MK_L2_POOL",
+    "to_device_u32", "to_numpy_u32", "Batcher", "Server", "SetGraph", "set_bucket_rule", "MK_L2_NONE", "MK_L2_VINFO", "MK_L2_HEADS", "MK_L2_POOL",
 ]
 
 
@@ -352,6 +352,90 @@ class Graph:
 
     def launch_count(self) -> int:
         return int(self._lib.mk_launch_count(self._h))
+
+
+def set_bucket_rule(V: int, src, load_factor: float = 0.7, stream=None):
+    """Per-vertex bucket counts of the set layout, max(1, ceil(outdeg / (lf * 31)))."""
+    torch = _torch()
+    lib = load()
+    s = to_device_u32(src)
+    out = torch.empty(V, dtype=torch.int32, device=s.device)
+    check(lib.mk_set_bucket_rule(V, _ptr(s), s.numel(), load_factor, _ptr(out), _stream(stream)),
+          "mk_set_bucket_rule")
+    return out
+
+
+class SetGraph:
+    """An unweighted graph in the ConcurrentSet layout (mk_set_*)."""
+
+    def __init__(self, V: int, edge_capacity_hint: int = 0, buckets=1, stream=None):
+        torch = _torch()
+        self._lib = load()
+        self.V = int(V)
+        b = None if isinstance(buckets, int) else to_device_u32(buckets)
+        h = ctypes.c_void_p()
+        check(self._lib.mk_set_create(self.V, int(edge_capacity_hint), buckets if b is None else 0, _ptr(b),
+                                      _stream(stream), ctypes.byref(h)), "mk_set_create")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mk_set_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _flags(self, fn, name, src, dst, stream):
+        torch = _torch()
+        s, d = to_device_u32(src), to_device_u32(dst)
+        f = torch.empty(s.numel(), dtype=torch.uint8, device=self.device)
+        check(fn(self._h, _ptr(s), _ptr(d), s.numel(), _ptr(f), _stream(stream)), name)
+        return f
+
+    def insert(self, src, dst, stream=None):
+        return self._flags(self._lib.mk_set_insert_batch, "mk_set_insert_batch", src, dst, stream)
+
+    def delete(self, src, dst, stream=None):
+        return self._flags(self._lib.mk_set_delete_batch, "mk_set_delete_batch", src, dst, stream)
+
+    def query(self, src, dst, stream=None):
+        torch = _torch()
+        s, d = to_device_u32(src), to_device_u32(dst)
+        bm = torch.empty((s.numel() + 31) // 32, dtype=torch.int32, device=self.device)
+        check(self._lib.mk_set_query_batch(self._h, _ptr(s), _ptr(d), s.numel(), _ptr(bm), _stream(stream)),
+              "mk_set_query_batch")
+        return bm
+
+    def bfs(self, source: int, stream=None):
+        torch = _torch()
+        dist = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        par = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        check(self._lib.mk_set_bfs(self._h, int(source), _ptr(dist), _ptr(par), _stream(stream)), "mk_set_bfs")
+        return dist, par
+
+    def wcc(self, stream=None):
+        torch = _torch()
+        lab = torch.empty(self.V, dtype=torch.int32, device=self.device)
+        check(self._lib.mk_set_wcc(self._h, _ptr(lab), _stream(stream)), "mk_set_wcc")
+        return lab
+
+    def stats(self, stream=None) -> dict:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(self._lib.mk_set_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream(stream)),
+              "mk_set_stats")
+        return {"lists": a.value, "slabs_in_use": b.value, "device_bytes": c.value}
+
+    def last_error(self) -> int:
+        return int(self._lib.mk_set_last_error(self._h))
 
 
 class Batcher:

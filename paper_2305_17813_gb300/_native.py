@@ -145,6 +145,16 @@ SIGNATURES = {
     "mk_version": (ctypes.c_char_p, []),
     "mk_debug_set": (_INT, [_P, _INT, _U64]),
     "mk_l2_window": (_INT, [_P, _INT, _P, ctypes.POINTER(mk_l2_info)]),
+    "mk_set_bucket_rule": (_INT, [_U32, _P, _U64, ctypes.c_float, _P, _P]),
+    "mk_set_create": (_INT, [_U32, _U64, _U32, _P, _P, ctypes.POINTER(_P)]),
+    "mk_set_destroy": (_INT, [_P]),
+    "mk_set_insert_batch": (_INT, [_P, _P, _P, _U64, _P, _P]),
+    "mk_set_delete_batch": (_INT, [_P, _P, _P, _U64, _P, _P]),
+    "mk_set_query_batch": (_INT, [_P, _P, _P, _U64, _P, _P]),
+    "mk_set_bfs": (_INT, [_P, _U32, _P, _P, _P]),
+    "mk_set_wcc": (_INT, [_P, _P, _P]),
+    "mk_set_stats": (_INT, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64), _P]),
+    "mk_set_last_error": (_INT, [_P]),
     "mk_pagerank": (_INT, [_P, _P, _INT, ctypes.c_float, ctypes.c_float, _U32, ctypes.POINTER(_U32),
                            ctypes.POINTER(ctypes.c_float), _P]),
     "mk_tc_count": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),

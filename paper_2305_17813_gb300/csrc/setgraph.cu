@@ -1,0 +1,755 @@
+// ConcurrentSet layout (paper, Sec. "Motivation": SlabHash's ConcurrentSet
+// beside the ConcurrentMap that the weighted store uses; the paper stores the
+// unweighted graphs of BFS and WCC this way).  An unweighted graph whose
+// slabs hold 31 destination keys (lanes 0..30) and the next-slab index
+// (lane 31): about twice the keys of a map slab's 15 pairs, so the slab
+// array, and every traversal that streams it, is about half as large.
+//
+// The store keeps the map store's conventions: one head slab per bucket of a
+// vertex in one allocation located by an exclusive scan of the bucket
+// counts, overflow slabs claimed from a bitmap pool, EMPTY and TOMBSTONE
+// keys, deleted keys never reused (so free keys exist only in a chain's last
+// slab), set semantics with the first occurrence of a repeated pair applied
+// (the batch is deduplicated by the map store's staging kernel).  One warp
+// handles one edge at a time, reading a slab with one coalesced 128-byte
+// load (the paper's warp-cooperative strategy).  BFS (hop counts, with the
+// smallest-id tight parent) and WCC (smallest-id labels) run statically,
+// level by level and as one union-find pass over the slab array.
+#include "mk_host.h"
+
+#include <algorithm>
+#include <cstring>
+
+using namespace mk;
+
+// Kernels of other translation units, launched here unchanged.
+__global__ void k_degree(const uint32_t *src, uint64_t n, uint32_t V, uint32_t *deg, int *bad);
+__global__ void k_rule(uint32_t *deg, uint32_t V, float per_bucket);
+__global__ void k_init_bitmap(uint32_t *bitmap, uint32_t words, uint32_t P);
+__global__ void k_fill_buckets(uint32_t *b, uint32_t V, uint32_t nb, const uint32_t *user, int *bad);
+__global__ void k_dedup(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
+                        const uint32_t *__restrict__ w, uint64_t n, uint32_t V, uint32_t *tpos, uint32_t mask,
+                        uint32_t *__restrict__ slot, DevState *st);
+
+namespace {
+
+constexpr uint32_t kSetKeys = 31; // key lanes 0..30, lane 31 = next
+
+__device__ __forceinline__ bool is_set_key_lane(uint32_t lane) { return lane < kSetKeys; }
+
+} // namespace
+
+struct mk_set_graph {
+    GView v{};                 // V, H, P, pool_words, vinfo, slabs, bitmap, owner, st (the rest unused)
+    uint64_t bytes = 0;
+    uint64_t cap = 0, table = 0; // staging: batch hash set (table entries) and per-edge slots (cap)
+    uint32_t *d_tpos = nullptr, *d_slot = nullptr;
+    uint32_t *h_pinned = nullptr;
+};
+
+// -------------------------------------------------------------- kernels
+
+__global__ void k_set_init_slabs(uint32_t *slabs, uint64_t count)
+{
+    const uint64_t words = count * 32;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        slabs[i] = (i & 31) == kNextLane ? kNil : kEmptyKey;
+}
+
+// vinfo[v] = {first list, bucket count}; owner[list] = v; owner of every
+// pool slab = kNil.
+__global__ void k_set_init_lists(const uint64_t *off, const uint32_t *buckets, uint32_t V, uint2 *vinfo,
+                                 uint32_t *owner, uint64_t H, uint64_t total)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < V; v += stride) {
+        const uint32_t first = (uint32_t)off[v], nb = buckets[v];
+        vinfo[v] = make_uint2(first, nb);
+        for (uint32_t b = 0; b < nb; ++b)
+            owner[first + b] = (uint32_t)v;
+    }
+    for (uint64_t s = H + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < total; s += stride)
+        owner[s] = kNil;
+}
+
+namespace {
+
+// The list that holds (s, d).
+__device__ __forceinline__ uint32_t set_list(const GView &g, uint32_t s, uint32_t d)
+{
+    const uint2 vi = __ldg(&g.vinfo[s]);
+    return vi.x + bucket_of(d, vi.y);
+}
+
+// One warp, one edge: 1 if d was stored, 0 if present already, or a
+// negative device error code.  Walks the whole chain (a present key ends
+// the walk), claims the lowest free key of the tail with a CAS, or links a
+// pool slab holding d with a CAS on the tail's next lane.
+__device__ __forceinline__ int warp_set_insert(const GView &g, uint32_t s, uint32_t d, uint32_t max_hops,
+                                               unsigned long long &loads, unsigned long long &linked)
+{
+    const uint32_t lane = lane_id();
+    uint32_t slab = set_list(g, s, d);
+    for (uint32_t guard = 0; guard < 4 * max_hops + 64; ++guard) {
+        const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
+        ++loads;
+        if (__ballot_sync(kFull, is_set_key_lane(lane) && w == d))
+            return 0;
+        const uint32_t empty = __ballot_sync(kFull, is_set_key_lane(lane) && w == kEmptyKey);
+        const uint32_t nxt = __shfl_sync(kFull, w, kNextLane);
+        if (empty) {
+            const uint32_t l = __ffs(empty) - 1;
+            uint32_t ok = 0;
+            if (lane == l)
+                ok = atomicCAS(slab_ptr(g, slab) + l, kEmptyKey, d) == kEmptyKey;
+            if (__shfl_sync(kFull, ok, l))
+                return 1;
+            continue; // another warp took the key: read the slab again
+        }
+        if (nxt != kNil) {
+            slab = nxt;
+            continue;
+        }
+        // a full tail with nothing after it: a pool slab holding d
+        const uint32_t ns = alloc_slab(g, s * 0x9E3779B9u ^ d ^ (guard << 26));
+        if (ns == kNil)
+            return kErrPool;
+        __stcg(slab_ptr(g, ns) + lane, lane == 0 ? d : (lane == kNextLane ? kNil : kEmptyKey));
+        if (lane == 0)
+            g.owner[ns] = s;
+        __threadfence();
+        uint32_t old = kNil;
+        if (lane == 0)
+            old = atomicCAS(slab_ptr(g, slab) + kNextLane, kNil, ns);
+        old = __shfl_sync(kFull, old, 0);
+        if (old == kNil) {
+            ++linked;
+            return 1;
+        }
+        // lost the link: give the slab back and follow the winner's
+        if (lane == 0)
+            g.owner[ns] = kNil;
+        __threadfence();
+        if (lane == 0)
+            free_slab(g, ns);
+        slab = old;
+    }
+    return kErrTimeout;
+}
+
+} // namespace
+
+// One warp per chunk of 32 edges, the chunk's first occurrences one at a time.
+__global__ void __launch_bounds__(256) k_set_insert(GView g, const uint32_t *__restrict__ src,
+                                                    const uint32_t *__restrict__ dst, uint64_t n,
+                                                    const uint32_t *__restrict__ tpos,
+                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
+                                                    uint32_t max_hops)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long loads = 0, linked = 0;
+    for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
+        if (__any_sync(kFull, status_hint(g.st) != 0))
+            break;
+        const uint64_t i = q0 + lane;
+        bool first = false;
+        uint32_t s = 0, d = 0;
+        if (i < n) {
+            const uint32_t sl = slot[i];
+            first = sl != kNil && __ldcg(&tpos[sl]) == (uint32_t)i;
+            s = src[i];
+            d = dst[i];
+        }
+        uint8_t mine = 0;
+        uint32_t todo = __ballot_sync(kFull, first);
+        while (todo) {
+            const uint32_t j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int r = warp_set_insert(g, __shfl_sync(kFull, s, j), __shfl_sync(kFull, d, j), max_hops, loads,
+                                          linked);
+            if (r < 0) {
+                if (lane == 0)
+                    set_status(g.st, r);
+            } else if (lane == j) {
+                mine = (uint8_t)r;
+            }
+        }
+        if (flags && i < n)
+            flags[i] = mine;
+    }
+    count_add(g.st, kCtrInsertSlabs, loads / 32);
+    count_add(g.st, kCtrInsertNewSlabs, linked / 32);
+}
+
+// Deletes: the key becomes TOMBSTONE (never reused); the walk stops at the
+// key or at the chain's first free key.
+__global__ void __launch_bounds__(256) k_set_delete(GView g, const uint32_t *__restrict__ src,
+                                                    const uint32_t *__restrict__ dst, uint64_t n,
+                                                    const uint32_t *__restrict__ tpos,
+                                                    const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
+                                                    uint32_t max_hops)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long loads = 0;
+    for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
+        if (__any_sync(kFull, status_hint(g.st) != 0))
+            break;
+        const uint64_t i = q0 + lane;
+        bool first = false;
+        uint32_t s = 0, d = 0;
+        if (i < n) {
+            const uint32_t sl = slot[i];
+            first = sl != kNil && __ldcg(&tpos[sl]) == (uint32_t)i;
+            s = src[i];
+            d = dst[i];
+        }
+        uint8_t mine = 0;
+        uint32_t todo = __ballot_sync(kFull, first);
+        while (todo) {
+            const uint32_t j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t sj = __shfl_sync(kFull, s, j), dj = __shfl_sync(kFull, d, j);
+            uint32_t slab = set_list(g, sj, dj);
+            uint32_t removed = 0;
+            for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
+                const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
+                ++loads;
+                const uint32_t hit = __ballot_sync(kFull, is_set_key_lane(lane) && w == dj);
+                if (hit) {
+                    const uint32_t l = __ffs(hit) - 1;
+                    if (lane == l)
+                        removed = atomicCAS(slab_ptr(g, slab) + l, dj, kTombKey) == dj;
+                    removed = __shfl_sync(kFull, removed, l);
+                    break;
+                }
+                if (__ballot_sync(kFull, is_set_key_lane(lane) && w == kEmptyKey))
+                    break;
+                slab = __shfl_sync(kFull, w, kNextLane);
+            }
+            if (lane == j)
+                mine = (uint8_t)removed;
+        }
+        if (flags && i < n)
+            flags[i] = mine;
+    }
+    count_add(g.st, kCtrDeleteSlabs, loads / 32);
+}
+
+// Queries: bit i % 32 of word i / 32 is set when edge i is present (the
+// bitmap is cleared first).
+__global__ void __launch_bounds__(256) k_set_query(GView g, const uint32_t *__restrict__ src,
+                                                   const uint32_t *__restrict__ dst, uint64_t n,
+                                                   uint32_t *__restrict__ bitmap, uint32_t max_hops)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long loads = 0;
+    for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
+        const uint64_t i = q0 + lane;
+        uint32_t s = 0, d = 0;
+        bool valid = false;
+        if (i < n) {
+            s = src[i];
+            d = dst[i];
+            valid = s < g.V && d < g.V;
+            if (!valid)
+                set_status(g.st, kErrInvalid);
+        }
+        uint32_t word = 0;
+        uint32_t todo = __ballot_sync(kFull, valid);
+        while (todo) {
+            const uint32_t j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t sj = __shfl_sync(kFull, s, j), dj = __shfl_sync(kFull, d, j);
+            uint32_t slab = set_list(g, sj, dj);
+            bool found = false;
+            for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
+                const uint32_t w = __ldg(slab_ptr(g, slab) + lane);
+                ++loads;
+                if (__ballot_sync(kFull, is_set_key_lane(lane) && w == dj)) {
+                    found = true;
+                    break;
+                }
+                if (__ballot_sync(kFull, is_set_key_lane(lane) && w == kEmptyKey))
+                    break;
+                slab = __shfl_sync(kFull, w, kNextLane);
+            }
+            if (found)
+                word |= 1u << j;
+        }
+        if (lane == 0 && q0 < n)
+            bitmap[q0 / 32] = word;
+    }
+    count_add(g.st, kCtrQuerySlabs, loads / 32);
+}
+
+// One BFS level: every vertex of the frontier (one warp each) reads all its
+// lists; a destination still unreached gets level + 1 with a CAS and joins
+// the next frontier (one atomicAdd per warp per slab).
+__global__ void __launch_bounds__(256) k_set_bfs_level(GView g, const uint32_t *__restrict__ front, uint32_t n,
+                                                       uint32_t *next, uint32_t *next_count, uint32_t *dist,
+                                                       uint32_t level, uint32_t max_hops)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long loads = 0;
+    for (uint64_t k = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+        const uint32_t u = front[k];
+        const uint2 vi = __ldg(&g.vinfo[u]);
+        for (uint32_t b = 0; b < vi.y; ++b) {
+            uint32_t slab = vi.x + b;
+            for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
+                const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
+                ++loads;
+                bool grab = false;
+                if (is_set_key_lane(lane) && w < kTombKey && __ldcg(&dist[w]) == kNil)
+                    grab = atomicCAS(&dist[w], kNil, level + 1) == kNil;
+                const uint32_t m = __ballot_sync(kFull, grab);
+                uint32_t base = 0;
+                if (lane == 0 && m)
+                    base = atomicAdd(next_count, (uint32_t)__popc(m));
+                base = __shfl_sync(kFull, base, 0);
+                if (grab)
+                    next[base + __popc(m & lanemask_lt())] = w;
+                slab = __shfl_sync(kFull, w, kNextLane);
+            }
+        }
+    }
+    count_add(g.st, kCtrRelaxSlabs, loads / 32);
+}
+
+// BFS parents: the smallest u with a live edge u -> v and dist[u] + 1 ==
+// dist[v] (one warp per slab in use, the owner is u).
+__global__ void __launch_bounds__(256) k_set_bfs_parent(GView g, const uint32_t *__restrict__ dist,
+                                                        uint32_t *parent, uint32_t source)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t total = (uint64_t)g.H + g.P;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t s = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; s < total; s += warps) {
+        const uint32_t u = __ldg(&g.owner[s]);
+        if (u == kNil)
+            continue;
+        const uint32_t du = __ldg(&dist[u]);
+        if (du == kNil)
+            continue;
+        const uint32_t w = __ldcg(slab_ptr(g, (uint32_t)s) + lane);
+        if (is_set_key_lane(lane) && w < kTombKey && w != source && __ldg(&dist[w]) == du + 1)
+            atomicMin(&parent[w], u);
+    }
+}
+
+__global__ void k_set_bfs_init(uint32_t *dist, uint32_t *parent, uint32_t V, uint32_t source, uint32_t *front)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V) {
+        dist[v] = v == source ? 0u : kNil;
+        parent[v] = v == source ? source : kNil;
+    }
+    if (v == 0)
+        front[0] = source;
+}
+
+namespace {
+
+__device__ __forceinline__ uint32_t set_find(uint32_t *p, uint32_t x)
+{
+    for (;;) {
+        const uint32_t px = __ldcg(&p[x]);
+        if (px == x)
+            return x;
+        const uint32_t ppx = __ldcg(&p[px]);
+        if (ppx == px)
+            return px;
+        p[x] = ppx; // path halving: ppx is an ancestor of x
+        x = ppx;
+    }
+}
+
+} // namespace
+
+__global__ void k_set_uf_init(uint32_t *p, uint32_t V)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V)
+        p[v] = v;
+}
+
+// Static WCC: every live edge u -> v (one warp per slab in use, the owner is
+// u) unites the sets of u and v, the larger root hooked under the smaller
+// with a CAS (retried with fresh roots when it loses), so each root is its
+// set's smallest vertex.
+__global__ void __launch_bounds__(256) k_set_wcc_hook(GView g, uint32_t *p, int *failed)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t total = (uint64_t)g.H + g.P;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t s = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; s < total; s += warps) {
+        const uint32_t u = __ldg(&g.owner[s]);
+        if (u == kNil)
+            continue;
+        const uint32_t w = __ldcg(slab_ptr(g, (uint32_t)s) + lane);
+        if (!is_set_key_lane(lane) || w >= kTombKey)
+            continue;
+        uint32_t a = u, b = w;
+        bool done = false;
+        for (uint32_t it = 0; it < (1u << 20) && !done; ++it) {
+            a = set_find(p, a);
+            b = set_find(p, b);
+            if (a == b) {
+                done = true;
+            } else {
+                const uint32_t hi = max(a, b), lo = min(a, b);
+                done = atomicCAS(&p[hi], hi, lo) == hi;
+            }
+        }
+        if (!done)
+            *failed = 1;
+    }
+}
+
+__global__ void k_set_wcc_label(uint32_t *p, uint32_t V, uint32_t *label)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V)
+        label[v] = set_find(p, v);
+}
+
+__global__ void k_set_flag_status(const int *failed, DevState *st)
+{
+    if (*failed)
+        set_status(st, kErrTimeout);
+}
+
+__global__ void k_set_pool_used(const DevState *st, unsigned long long *out)
+{
+    long long t = 0;
+    for (uint32_t i = 0; i < kSlots; ++i)
+        t += st->pool_used[i];
+    *out = (unsigned long long)t;
+}
+
+// ------------------------------------------------------------- host side
+
+namespace {
+
+mk_status set_alloc(mk_set_graph *g, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (!bytes)
+        return MK_OK;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? MK_ERR_NO_MEMORY : MK_ERR_CUDA;
+    }
+    g->bytes += bytes;
+    return MK_OK;
+}
+
+void set_free(mk_set_graph *g, void *p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        g->bytes -= bytes;
+    }
+}
+
+mk_status set_stage(mk_set_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n, cudaStream_t s)
+{
+    if (n > g->cap) {
+        uint64_t cap = std::max<uint64_t>(n, std::max<uint64_t>(1024, g->cap + g->cap / 2)), table = 1;
+        while (table < 2 * cap)
+            table <<= 1;
+        MK_CUDA(cudaStreamSynchronize(s));
+        set_free(g, g->d_tpos, g->table * 4);
+        set_free(g, g->d_slot, g->cap * 4);
+        g->d_tpos = g->d_slot = nullptr;
+        g->cap = g->table = 0;
+        MK_TRY(set_alloc(g, (void **)&g->d_tpos, table * 4));
+        MK_TRY(set_alloc(g, (void **)&g->d_slot, cap * 4));
+        g->cap = cap;
+        g->table = table;
+    }
+    MK_CUDA(cudaMemsetAsync(g->d_tpos, 0xFF, g->table * 4, s));
+    k_dedup<<<grid_for(n, 256), 256, 0, s>>>(src, dst, nullptr, n, g->v.V, g->d_tpos, (uint32_t)(g->table - 1),
+                                             g->d_slot, g->v.st);
+    MK_CUDA(cudaGetLastError());
+    return MK_OK;
+}
+
+uint32_t set_grid(uint64_t items_per_warp32)
+{
+    return std::min<uint32_t>(grid_for(std::max<uint64_t>(items_per_warp32, 1) * 32, 256), num_sms() * 32);
+}
+
+} // namespace
+
+extern "C" {
+
+mk_status mk_set_bucket_rule(uint32_t V, const uint32_t *d_src, uint64_t n, float load_factor, uint32_t *d_buckets,
+                             void *stream)
+{
+    if (V == 0 || !d_buckets || (n > 0 && !d_src) || !(load_factor > 0.f) || load_factor > 1.f)
+        return MK_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d_bad = nullptr;
+    MK_CUDA(cudaMallocAsync((void **)&d_bad, sizeof(int), s));
+    MK_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    MK_CUDA(cudaMemsetAsync(d_buckets, 0, (size_t)V * 4, s));
+    if (n)
+        k_degree<<<std::min<uint64_t>(grid_for(n, 256), 4096), 256, 0, s>>>(d_src, n, V, d_buckets, d_bad);
+    k_rule<<<grid_for(V, 256), 256, 0, s>>>(d_buckets, V, load_factor * (float)kSetKeys);
+    int bad = 0;
+    MK_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MK_CUDA(cudaFreeAsync(d_bad, s));
+    MK_CUDA(cudaStreamSynchronize(s));
+    return bad ? MK_ERR_INVALID_ARG : MK_OK;
+}
+
+mk_status mk_set_destroy(mk_set_graph *g)
+{
+    if (!g)
+        return MK_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    cudaFree((void *)g->v.vinfo);
+    cudaFree(g->v.slabs);
+    cudaFree(g->v.bitmap);
+    cudaFree(g->v.owner);
+    cudaFree(g->v.st);
+    cudaFree(g->d_tpos);
+    cudaFree(g->d_slot);
+    if (g->h_pinned)
+        cudaFreeHost(g->h_pinned);
+    delete g;
+    return MK_OK;
+}
+
+mk_status mk_set_create(uint32_t V, uint64_t edge_capacity_hint, uint32_t buckets, const uint32_t *d_bucket_per_vertex,
+                        void *stream, mk_set_graph **out)
+{
+    if (!out || V == 0 || V > 0xFFFFFFFDu)
+        return MK_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    mk_set_graph *g = new mk_set_graph;
+    g->v.V = V;
+    uint32_t *d_b = nullptr;
+    uint64_t *d_off = nullptr;
+    void *d_tmp = nullptr;
+    int *d_bad = nullptr;
+    mk_status st = MK_OK;
+    auto fail = [&](mk_status code) {
+        cudaFree(d_b);
+        cudaFree(d_off);
+        cudaFree(d_tmp);
+        cudaFree(d_bad);
+        mk_set_destroy(g);
+        return code;
+    };
+    if (cudaMalloc((void **)&d_b, (size_t)V * 4) != cudaSuccess ||
+        cudaMalloc((void **)&d_off, ((size_t)V + 1) * 8) != cudaSuccess ||
+        cudaMalloc((void **)&d_bad, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&d_tmp, exclusive_scan_scratch_bytes(V + 1)) != cudaSuccess)
+        return fail(MK_ERR_NO_MEMORY);
+    cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+    k_fill_buckets<<<grid_for(V, 256), 256, 0, s>>>(d_b, V, buckets ? buckets : 1, d_bucket_per_vertex, d_bad);
+    if (exclusive_scan_u32_u64(d_b, d_off, V, d_tmp, s, nullptr) != cudaSuccess)
+        return fail(MK_ERR_CUDA);
+    // H = last offset + last bucket count
+    uint64_t last_off = 0;
+    uint32_t last_b = 0;
+    int bad = 0;
+    if (cudaMemcpyAsync(&last_off, d_off + V - 1, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&last_b, d_b + V - 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(MK_ERR_CUDA);
+    if (bad)
+        return fail(MK_ERR_INVALID_ARG);
+    const uint64_t H = last_off + last_b;
+    uint64_t P = edge_capacity_hint / kSetKeys + H / 8 + 1024;
+    P = (P + 31) / 32 * 32;
+    if (H + P >= 0xFFFFFFF0ull)
+        return fail(MK_ERR_INVALID_ARG);
+    g->v.H = (uint32_t)H;
+    g->v.P = (uint32_t)P;
+    g->v.pool_words = (uint32_t)(P / 32);
+    uint2 *vinfo = nullptr;
+    if ((st = set_alloc(g, (void **)&vinfo, (size_t)V * 8)) != MK_OK ||
+        (st = set_alloc(g, (void **)&g->v.slabs, (H + P) * 128)) != MK_OK ||
+        (st = set_alloc(g, (void **)&g->v.bitmap, (size_t)g->v.pool_words * 4)) != MK_OK ||
+        (st = set_alloc(g, (void **)&g->v.owner, (H + P) * 4)) != MK_OK ||
+        (st = set_alloc(g, (void **)&g->v.st, sizeof(DevState))) != MK_OK)
+        return fail(st);
+    g->v.vinfo = vinfo;
+    if (cudaMallocHost((void **)&g->h_pinned, 64) != cudaSuccess)
+        return fail(MK_ERR_NO_MEMORY);
+    cudaMemsetAsync(g->v.st, 0, sizeof(DevState), s);
+    k_set_init_slabs<<<std::min<uint64_t>(grid_for((H + P) * 32, 256), 65535), 256, 0, s>>>(g->v.slabs, H + P);
+    k_set_init_lists<<<std::min<uint64_t>(grid_for(std::max<uint64_t>(V, P), 256), 65535), 256, 0, s>>>(
+        d_off, d_b, V, vinfo, g->v.owner, H, H + P);
+    k_init_bitmap<<<grid_for(g->v.pool_words, 256), 256, 0, s>>>(g->v.bitmap, g->v.pool_words, (uint32_t)P);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(MK_ERR_CUDA);
+    cudaFree(d_b);
+    cudaFree(d_off);
+    cudaFree(d_tmp);
+    cudaFree(d_bad);
+    *out = g;
+    return MK_OK;
+}
+
+mk_status mk_set_insert_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              uint8_t *d_inserted, void *stream)
+{
+    if (!g || (n && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
+        return MK_ERR_INVALID_ARG;
+    if (!n)
+        return MK_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_inserted)
+        MK_CUDA(cudaMemsetAsync(d_inserted, 0, n, s));
+    MK_TRY(set_stage(g, d_src, d_dst, n, s));
+    k_set_insert<<<set_grid((n + 31) / 32), 256, 0, s>>>(g->v, d_src, d_dst, n, g->d_tpos, g->d_slot, d_inserted,
+                                                        g->v.P + 2);
+    MK_CUDA(cudaGetLastError());
+    return MK_OK;
+}
+
+mk_status mk_set_delete_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              uint8_t *d_deleted, void *stream)
+{
+    if (!g || (n && (!d_src || !d_dst)) || n >= 0xFFFFFFFFull)
+        return MK_ERR_INVALID_ARG;
+    if (!n)
+        return MK_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_deleted)
+        MK_CUDA(cudaMemsetAsync(d_deleted, 0, n, s));
+    MK_TRY(set_stage(g, d_src, d_dst, n, s));
+    k_set_delete<<<set_grid((n + 31) / 32), 256, 0, s>>>(g->v, d_src, d_dst, n, g->d_tpos, g->d_slot, d_deleted,
+                                                        g->v.P + 2);
+    MK_CUDA(cudaGetLastError());
+    return MK_OK;
+}
+
+mk_status mk_set_query_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                             uint32_t *d_bitmap, void *stream)
+{
+    if (!g || (n && (!d_src || !d_dst || !d_bitmap)))
+        return MK_ERR_INVALID_ARG;
+    if (!n)
+        return MK_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_set_query<<<set_grid((n + 31) / 32), 256, 0, s>>>(g->v, d_src, d_dst, n, d_bitmap, g->v.P + 2);
+    MK_CUDA(cudaGetLastError());
+    return MK_OK;
+}
+
+mk_status mk_set_bfs(mk_set_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream)
+{
+    if (!g || source >= g->v.V || !d_dist || !d_parent)
+        return MK_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t V = g->v.V;
+    uint32_t *front[2] = {nullptr, nullptr}, *cnt = nullptr;
+    MK_CUDA(cudaMallocAsync((void **)&front[0], (size_t)V * 4, s));
+    MK_CUDA(cudaMallocAsync((void **)&front[1], (size_t)V * 4, s));
+    MK_CUDA(cudaMallocAsync((void **)&cnt, 8, s));
+    k_set_bfs_init<<<grid_for(V, 256), 256, 0, s>>>(d_dist, d_parent, V, source, front[0]);
+    mk_status st = MK_OK;
+    uint32_t n = 1, level = 0;
+    while (n && st == MK_OK) {
+        if (level > V) {
+            st = MK_ERR_TIMEOUT;
+            break;
+        }
+        if (cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) {
+            st = MK_ERR_CUDA;
+            break;
+        }
+        k_set_bfs_level<<<set_grid(n), 256, 0, s>>>(g->v, front[level & 1], n, front[(level + 1) & 1], cnt, d_dist,
+                                                   level, g->v.P + 2);
+        if (cudaMemcpyAsync(g->h_pinned, cnt, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = MK_ERR_CUDA;
+            break;
+        }
+        n = g->h_pinned[0];
+        ++level;
+    }
+    if (st == MK_OK) {
+        k_set_bfs_parent<<<set_grid(((uint64_t)g->v.H + g->v.P + 31) / 32), 256, 0, s>>>(g->v, d_dist, d_parent,
+                                                                                     source);
+        if (cudaGetLastError() != cudaSuccess)
+            st = MK_ERR_CUDA;
+    }
+    cudaFreeAsync(front[0], s);
+    cudaFreeAsync(front[1], s);
+    cudaFreeAsync(cnt, s);
+    return st;
+}
+
+mk_status mk_set_wcc(mk_set_graph *g, uint32_t *d_label, void *stream)
+{
+    if (!g || !d_label)
+        return MK_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t V = g->v.V;
+    uint32_t *p = nullptr;
+    int *failed = nullptr;
+    MK_CUDA(cudaMallocAsync((void **)&p, (size_t)V * 4, s));
+    MK_CUDA(cudaMallocAsync((void **)&failed, sizeof(int), s));
+    MK_CUDA(cudaMemsetAsync(failed, 0, sizeof(int), s));
+    k_set_uf_init<<<grid_for(V, 256), 256, 0, s>>>(p, V);
+    k_set_wcc_hook<<<set_grid(((uint64_t)g->v.H + g->v.P + 31) / 32), 256, 0, s>>>(g->v, p, failed);
+    k_set_wcc_label<<<grid_for(V, 256), 256, 0, s>>>(p, V, d_label);
+    k_set_flag_status<<<1, 1, 0, s>>>(failed, g->v.st);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(p, s);
+    cudaFreeAsync(failed, s);
+    return e == cudaSuccess ? MK_OK : MK_ERR_CUDA;
+}
+
+mk_status mk_set_stats(mk_set_graph *g, uint64_t *h_lists, uint64_t *h_slabs_in_use, uint64_t *h_device_bytes,
+                       void *stream)
+{
+    if (!g)
+        return MK_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d = nullptr;
+    MK_CUDA(cudaMallocAsync((void **)&d, 8, s));
+    k_set_pool_used<<<1, 1, 0, s>>>(g->v.st, d);
+    unsigned long long used = 0;
+    const cudaError_t e1 = cudaMemcpyAsync(&used, d, 8, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e1 != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return MK_ERR_CUDA;
+    if (h_lists)
+        *h_lists = g->v.H;
+    if (h_slabs_in_use)
+        *h_slabs_in_use = g->v.H + used;
+    if (h_device_bytes)
+        *h_device_bytes = g->bytes;
+    return MK_OK;
+}
+
+mk_status mk_set_last_error(mk_set_graph *g)
+{
+    if (!g)
+        return MK_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return MK_ERR_CUDA;
+    int st = 0;
+    MK_CUDA(cudaMemcpy(&st, &g->v.st->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0)
+        MK_CUDA(cudaMemset(&g->v.st->status, 0, sizeof(int)));
+    return st;
+}
+
+} // extern "C"

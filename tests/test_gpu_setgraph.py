@@ -1,0 +1,83 @@
+"""The ConcurrentSet layout (31 keys a slab): batched insert, delete and
+query flags and bitmaps, static BFS (hop counts and smallest-id tight
+parents) and WCC labels against the oracle on the unweighted view, and the
+slab count against the weighted store's on the same edges."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _mk():
+    import paper_2305_17813_gb300 as mk
+
+    mk.load()
+    return mk
+
+
+def _check_algos(mk, g, o, srcs):
+    for s in srcs:
+        d, p = g.bfs(s)
+        od, op = o.bfs(s)
+        assert np.array_equal(mk.to_numpy_u32(d), od), s
+        assert np.array_equal(mk.to_numpy_u32(p), op), s
+    assert np.array_equal(mk.to_numpy_u32(g.wcc()), o.wcc())
+
+
+@pytest.mark.parametrize("buckets", [1, 3])
+def test_set_graph_tiny_against_oracle(cuda_lib, buckets):
+    mk = _mk()
+    w = synth.tiny_workload()
+    g = mk.SetGraph(w.V, edge_capacity_hint=1 << 15, buckets=buckets)
+    o = oracle.OracleGraph(w.V)
+    assert np.array_equal(g.insert(w.g_src, w.g_dst).cpu().numpy(), o.insert(w.g_src, w.g_dst))
+    _check_algos(mk, g, o, [0, 5])
+    assert np.array_equal(g.insert(w.ins_src, w.ins_dst).cpu().numpy(), o.insert(w.ins_src, w.ins_dst))
+    assert np.array_equal(g.delete(w.del_src, w.del_dst).cpu().numpy(), o.delete(w.del_src, w.del_dst))
+    bm = g.query(w.q_src, w.q_dst)
+    assert np.array_equal(mk.to_numpy_u32(bm), o.query(w.q_src, w.q_dst)[0])
+    _check_algos(mk, g, o, [0, 17])
+    assert g.last_error() == mk.MK_OK
+    g.close()
+
+
+def test_set_graph_power_law_and_slab_count(cuda_lib):
+    mk = _mk()
+    G = synth.powerlaw_graph(scale=15, draws=1 << 19)
+    sb = mk.set_bucket_rule(G.V, G.src, 0.7)
+    g = mk.SetGraph(G.V, edge_capacity_hint=2 * len(G.src), buckets=sb)
+    o = oracle.OracleGraph(G.V)
+    # a hub's edges spread over many warps and pool slabs: the initial load
+    # in one batch
+    assert np.array_equal(g.insert(G.src, G.dst).cpu().numpy(), o.insert(G.src, G.dst))
+    src = int(np.argmax(o.out_degree()))
+    _check_algos(mk, g, o, [src])
+    S = synth.PowerlawStream(G, max_batch=1 << 14)
+    for _ in range(2):
+        b = S.batch(1 << 14)
+        assert np.array_equal(g.insert(b.ins_src, b.ins_dst).cpu().numpy(), o.insert(b.ins_src, b.ins_dst))
+        assert np.array_equal(g.delete(b.del_src, b.del_dst).cpu().numpy(), o.delete(b.del_src, b.del_dst))
+        bm = g.query(b.q_src, b.q_dst)
+        assert np.array_equal(mk.to_numpy_u32(bm), o.query(b.q_src, b.q_dst)[0])
+    _check_algos(mk, g, o, [src])
+    # the same edges in the weighted store take more slabs; a list of the set
+    # layout holds 31 keys a slab
+    m = mk.Graph(G.V, edge_capacity_hint=2 * len(G.src), buckets=mk.bucket_rule(G.V, G.src, 0.7))
+    m.insert(G.src, G.dst, G.w, flags=False)
+    o2 = oracle.OracleGraph(G.V)
+    o2.insert(G.src, G.dst)
+    deg = o2.out_degree().astype(np.int64)
+    ss = g.stats()
+    ms = m.stats()
+    assert ss["lists"] == int(sb.cpu().numpy().astype(np.int64).sum())
+    assert ss["slabs_in_use"] < ms["chain_slabs"], (ss, ms)
+    g2 = mk.SetGraph(G.V, edge_capacity_hint=2 * len(G.src), buckets=sb)
+    g2.insert(G.src, G.dst)
+    assert g2.stats()["slabs_in_use"] >= int(((deg + 30) // 31).sum()) + int((deg == 0).sum())
+    g2.close()
+    assert g.last_error() == mk.MK_OK and m.last_error() == mk.MK_OK
+    g.close()
+    m.close()
