@@ -75,7 +75,7 @@ def parse_args(argv=None):
     p.add_argument("--no-solo", action="store_true", help="skip the steps that time every kernel alone")
     p.add_argument("--no-per-batch", action="store_true",
                    help="skip the steps at the workload's other batch sizes (2^12, 2^16, 2^22)")
-    p.add_argument("--workload", choices=["powerlaw", "growth", "served", "road", "analytics", "buckets", "l2"],
+    p.add_argument("--workload", choices=["powerlaw", "growth", "served", "road", "analytics", "buckets", "l2", "set"],
                    default="powerlaw",
                    help="powerlaw: the benchmark line; growth: the learned-sizing study on the R-MAT "
                         "scale-22 growth stream; served: plain vs continuous-batching serving on the R-MAT "
@@ -1486,13 +1486,120 @@ def run_l2(args):
     return out
 
 
+def run_set(args):
+    """The unweighted power-law graph in the two layouts of the paper's store:
+    the ConcurrentMap slabs of the weighted store (15 pairs a slab) and the
+    ConcurrentSet slabs (31 keys a slab), same bucket rule (load factor 0.7
+    of the slab's capacity): slabs and device bytes, the load, one batch of
+    inserts, deletes and queries, static BFS from three sources and static
+    WCC, each timed alone after an L2 flush, results compared between the
+    layouts."""
+    import torch
+
+    import paper_2305_17813_gb300 as mk
+
+    torch.cuda.set_device(0)
+    peak, _ = measured_peak()
+    G, source, S = make_workload(args, args.batch)
+    deg = np.bincount(G.src, minlength=G.V)
+    sources = [int(x) for x in np.argsort(-deg, kind="stable")[:3]]
+    bt = S.batch(args.batch)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed_ms(fn):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ev[0].record()
+        r = fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), r
+
+    cap = len(G.src) + 4 * args.batch
+    dev = {k: mk.to_device_u32(getattr(G, k)) for k in ("src", "dst", "w")}
+    b = {k: mk.to_device_u32(getattr(bt, k)) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst",
+                                                        "q_src", "q_dst")}
+    out = {"workload": "set", "graph": "R-MAT scale %d, %d edges (weights ignored by BFS/WCC)" % (args.scale,
+                                                                                                 len(G.src)),
+           "batch": "insert %d + delete %d + query %d (one power-law stream batch)" % ((args.batch,) * 3),
+           "l2": "flushed before every timed call (512 MiB write)", "bfs_sources": sources}
+    res = {}
+    for name in ("map", "set"):
+        for rep in range(2):  # the first pass loads modules and pools
+            if name == "map":
+                g = mk.Graph(G.V, edge_capacity_hint=cap, buckets=mk.bucket_rule(G.V, dev["src"], 0.7))
+                load = lambda: g.insert(dev["src"], dev["dst"], dev["w"], flags=False)
+            else:
+                g = mk.SetGraph(G.V, edge_capacity_hint=cap, buckets=mk.set_bucket_rule(G.V, dev["src"], 0.7))
+                load = lambda: g.insert(dev["src"], dev["dst"])
+            ms_load, _ = timed_ms(load)
+            if name == "map":
+                g.commit()
+            st = g.stats()
+            slabs = int(st["chain_slabs"] if name == "map" else st["slabs_in_use"])
+            bfs_ms, bfs_out = [], []
+            for src in sources:  # a new source: the map store's first call for it is static
+                t, r = timed_ms(lambda: g.bfs(src))
+                bfs_ms.append(t)
+                bfs_out.append(r)
+            if name == "map":
+                wcc_ms, lab = timed_ms(lambda: g.wcc())  # the graph's first WCC call: the static pass
+            else:
+                wcc_ms, lab = timed_ms(lambda: g.wcc())
+            if name == "map":
+                ins = lambda: g.insert(b["ins_src"], b["ins_dst"], b["ins_w"])
+                dele = lambda: g.delete(b["del_src"], b["del_dst"])
+                qry = lambda: g.query(b["q_src"], b["q_dst"], weights=False)
+            else:
+                ins = lambda: g.insert(b["ins_src"], b["ins_dst"])
+                dele = lambda: g.delete(b["del_src"], b["del_dst"])
+                qry = lambda: g.query(b["q_src"], b["q_dst"])
+            ms_ins, fi = timed_ms(ins)
+            ms_del, fd = timed_ms(dele)
+            if name == "map":
+                g.commit()
+            ms_q, qr = timed_ms(qry)
+            bm = qr[0] if isinstance(qr, tuple) else qr
+            if g.last_error() != mk.MK_OK:
+                raise RuntimeError("%s layout reported a device error" % name)
+            if rep == 1:
+                res[name] = {
+                    "slabs_in_use": slabs, "lists": int(st["lists"]), "device_bytes": int(st["device_bytes"]),
+                    "load_ms": round(ms_load, 3), "load_medges_s": round(len(G.src) / ms_load / 1e3, 1),
+                    "static_bfs_ms": [round(t, 3) for t in bfs_ms], "static_wcc_ms": round(wcc_ms, 3),
+                    "static_wcc_slab_gbs": round(slabs * 132 / (wcc_ms / 1e3) / 1e9, 1),
+                    "insert_medges_s": round(args.batch / ms_ins / 1e3, 1),
+                    "delete_medges_s": round(args.batch / ms_del / 1e3, 1),
+                    "query_medges_s": round(args.batch / ms_q / 1e3, 1),
+                    "_out": ([(mk.to_numpy_u32(d), mk.to_numpy_u32(p)) for d, p in bfs_out], mk.to_numpy_u32(lab),
+                             fi.cpu().numpy(), fd.cpu().numpy(), mk.to_numpy_u32(bm))}
+            g.close()
+            del g
+            torch.cuda.empty_cache()
+    mo, so = res["map"].pop("_out"), res["set"].pop("_out")
+    same = all(np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]) for a, c in zip(mo[0], so[0]))
+    same = same and all(np.array_equal(x, y) for x, y in zip(mo[1:], so[1:]))
+    if not same:
+        raise RuntimeError("the two layouts disagree")
+    out.update(res)
+    out["results_equal"] = True
+    out["set_over_map"] = {
+        "slabs": round(res["set"]["slabs_in_use"] / res["map"]["slabs_in_use"], 3),
+        "static_wcc_time": round(res["set"]["static_wcc_ms"] / res["map"]["static_wcc_ms"], 3),
+        "static_bfs_time": round(sum(res["set"]["static_bfs_ms"]) / sum(res["map"]["static_bfs_ms"]), 3),
+        "query_rate": round(res["set"]["query_medges_s"] / res["map"]["query_medges_s"], 3)}
+    out["peak_gbs"] = peak
+    return out
+
+
 def main(argv=None):
     args = parse_args(argv)
     world, rank, local = dist_env()
     if args.workload not in ("powerlaw",):
         if rank == 0:
             res = {"growth": run_growth, "served": run_served, "road": run_road, "analytics": run_analytics,
-                   "buckets": run_buckets, "l2": run_l2}[args.workload](args)
+                   "buckets": run_buckets, "l2": run_l2, "set": run_set}[args.workload](args)
             print(json.dumps(res), flush=True)
         return 0
     if args.impl == "reference":

@@ -457,10 +457,13 @@ mk_status mk_set_delete_batch(mk_set_graph *g, const uint32_t *d_src, const uint
                               uint8_t *d_deleted, void *stream);
 mk_status mk_set_query_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                              uint32_t *d_bitmap, void *stream);
-/* Static BFS from `source`, level by level (the host reads each level's
- * frontier size): d_dist = hop counts (MK_NONE unreachable), d_parent = the
- * smallest-id u with a live edge u -> v and dist(u) + 1 = dist(v) (the source
- * its own parent).  Synchronises `stream` once per level. */
+/* Static BFS from `source`, level by level over a frontier of lists (one
+ * warp a list; frontier sizes kept on the device, levels launched six at a
+ * time, the host reading the frontier size once per six levels): d_dist =
+ * hop counts (MK_NONE unreachable), d_parent = the smallest-id u with a live
+ * edge u -> v and dist(u) + 1 = dist(v) (the source its own parent).
+ * Synchronises `stream`; allocates two frontiers of `lists` words each from
+ * the stream-ordered pool. */
 mk_status mk_set_bfs(mk_set_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream);
 /* Static WCC: d_label = the smallest vertex id of each vertex's component. */
 mk_status mk_set_wcc(mk_set_graph *g, uint32_t *d_label, void *stream);

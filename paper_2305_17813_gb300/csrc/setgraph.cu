@@ -13,9 +13,11 @@
 // (the batch is deduplicated by the map store's staging kernel).  One warp
 // handles one edge at a time, reading a slab with one coalesced 128-byte
 // load (the paper's warp-cooperative strategy).  BFS (hop counts, with the
-// smallest-id tight parent) and WCC (smallest-id labels) run statically,
-// level by level and as one union-find pass over the slab array.
+// smallest-id tight parent) and WCC (smallest-id labels) run statically:
+// BFS level by level over a frontier of lists, WCC as one union-find pass
+// over the slab array.
 #include "mk_host.h"
+#include "uf.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -179,8 +181,8 @@ __global__ void __launch_bounds__(256) k_set_insert(GView g, const uint32_t *__r
         if (flags && i < n)
             flags[i] = mine;
     }
-    count_add(g.st, kCtrInsertSlabs, loads / 32);
-    count_add(g.st, kCtrInsertNewSlabs, linked / 32);
+    count_add(g.st, kCtrInsertSlabs, loads);
+    count_add(g.st, kCtrInsertNewSlabs, linked);
 }
 
 // Deletes: the key becomes TOMBSTONE (never reused); the walk stops at the
@@ -235,90 +237,143 @@ __global__ void __launch_bounds__(256) k_set_delete(GView g, const uint32_t *__r
         if (flags && i < n)
             flags[i] = mine;
     }
-    count_add(g.st, kCtrDeleteSlabs, loads / 32);
+    count_add(g.st, kCtrDeleteSlabs, loads);
 }
 
-// Queries: bit i % 32 of word i / 32 is set when edge i is present (the
-// bitmap is cleared first).
+// Queries: bit i % 32 of word i / 32 is set when edge i is present.  One
+// warp answers 32 consecutive queries: every lane first finds its own
+// query's list (32 gathers in flight), then the warp walks eight chains at
+// a time, one per 4-lane group, each lane loading 8 consecutive words of
+// the slab as two 16-byte vectors (the group's last lane holds the next
+// index in its last word).
 __global__ void __launch_bounds__(256) k_set_query(GView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, uint64_t n,
                                                    uint32_t *__restrict__ bitmap, uint32_t max_hops)
 {
-    const uint32_t lane = lane_id();
+    constexpr uint32_t G = 4, W = 8, kGroups = 8;
+    const uint32_t lane = lane_id(), gi = lane / G, sub = lane % G;
+    const uint32_t gmask = 0xFu << (gi * G);
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long loads = 0;
     for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
-        const uint64_t i = q0 + lane;
-        uint32_t s = 0, d = 0;
-        bool valid = false;
-        if (i < n) {
-            s = src[i];
-            d = dst[i];
-            valid = s < g.V && d < g.V;
-            if (!valid)
-                set_status(g.st, kErrInvalid);
+        const uint64_t q = q0 + lane;
+        uint32_t my_d = kNil, my_head = kNil;
+        bool bad = false;
+        if (q < n) {
+            const uint32_t s = __ldg(src + q);
+            my_d = __ldg(dst + q);
+            if (s < g.V && my_d < g.V)
+                my_head = set_list(g, s, my_d);
+            else
+                bad = true;
         }
-        uint32_t word = 0;
-        uint32_t todo = __ballot_sync(kFull, valid);
-        while (todo) {
-            const uint32_t j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t sj = __shfl_sync(kFull, s, j), dj = __shfl_sync(kFull, d, j);
-            uint32_t slab = set_list(g, sj, dj);
-            bool found = false;
-            for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
-                const uint32_t w = __ldg(slab_ptr(g, slab) + lane);
-                ++loads;
-                if (__ballot_sync(kFull, is_set_key_lane(lane) && w == dj)) {
-                    found = true;
-                    break;
+        if (__ballot_sync(kFull, bad) && lane == 0)
+            set_status(g.st, kErrInvalid);
+        uint32_t word_bits = 0;
+#pragma unroll 1
+        for (uint32_t it = 0; it < 32 / kGroups; ++it) {
+            const uint32_t who = it * kGroups + gi;
+            const uint32_t d = __shfl_sync(kFull, my_d, who);
+            uint32_t slab = __shfl_sync(kFull, my_head, who);
+            bool active = slab != kNil, found = false;
+            for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+                loads += __popc(__ballot_sync(kFull, active && sub == 0));
+                uint4 a = make_uint4(kFull, kFull, kFull, kFull), b = a;
+                if (active) {
+                    const uint4 *v = reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + sub * W);
+                    a = __ldg(v);
+                    b = __ldg(v + 1);
                 }
-                if (__ballot_sync(kFull, is_set_key_lane(lane) && w == kEmptyKey))
-                    break;
-                slab = __shfl_sync(kFull, w, kNextLane);
+                const uint32_t w[W] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                bool hit = false, emp = false;
+#pragma unroll
+                for (uint32_t k = 0; k < W; ++k)
+                    if (sub * W + k < kSetKeys) {
+                        hit |= active && w[k] == d;
+                        emp |= active && w[k] == kEmptyKey;
+                    }
+                const uint32_t hm = __ballot_sync(kFull, hit) & gmask;
+                const uint32_t em = __ballot_sync(kFull, emp) & gmask;
+                const uint32_t nxt = __shfl_sync(kFull, b.w, gi * G + G - 1);
+                if (hm)
+                    found = true;
+                if (active && (hm || em || nxt == kNil || hop >= max_hops))
+                    active = false;
+                else if (active)
+                    slab = nxt;
             }
-            if (found)
-                word |= 1u << j;
+            const uint32_t fb = __ballot_sync(kFull, sub == 0 && found);
+#pragma unroll
+            for (uint32_t k = 0; k < kGroups; ++k)
+                if (fb & (1u << (k * G)))
+                    word_bits |= 1u << (it * kGroups + k);
         }
         if (lane == 0 && q0 < n)
-            bitmap[q0 / 32] = word;
+            bitmap[q0 / 32] = word_bits;
     }
-    count_add(g.st, kCtrQuerySlabs, loads / 32);
+    count_add(g.st, kCtrQuerySlabs, loads);
 }
 
-// One BFS level: every vertex of the frontier (one warp each) reads all its
-// lists; a destination still unreached gets level + 1 with a CAS and joins
-// the next frontier (one atomicAdd per warp per slab).
-__global__ void __launch_bounds__(256) k_set_bfs_level(GView g, const uint32_t *__restrict__ front, uint32_t n,
-                                                       uint32_t *next, uint32_t *next_count, uint32_t *dist,
-                                                       uint32_t level, uint32_t max_hops)
+// One BFS level over a frontier of lists (one warp per list, so a hub's
+// buckets spread over many warps).  A destination still unreached gets
+// level + 1 with a CAS and its lists join the next frontier: one atomicAdd
+// a warp per slab for all of the slab's new vertices.  The frontier sizes
+// live on the device in three rotating counters (this level reads
+// cnt[L % 3], appends to cnt[(L + 1) % 3] and clears cnt[(L + 2) % 3], the
+// input of the level before), so several levels go out without the host.
+__global__ void __launch_bounds__(256) k_set_bfs_level(GView g, const uint32_t *__restrict__ front, uint32_t *next,
+                                                       uint32_t *cnt, uint32_t *dist, uint32_t level,
+                                                       uint32_t max_hops)
 {
     const uint32_t lane = lane_id();
+    const uint32_t n = __ldcg(&cnt[level % 3]);
+    uint32_t *next_count = &cnt[(level + 1) % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        cnt[(level + 2) % 3] = 0;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long loads = 0;
     for (uint64_t k = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
-        const uint32_t u = front[k];
-        const uint2 vi = __ldg(&g.vinfo[u]);
-        for (uint32_t b = 0; b < vi.y; ++b) {
-            uint32_t slab = vi.x + b;
-            for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
-                const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
-                ++loads;
-                bool grab = false;
-                if (is_set_key_lane(lane) && w < kTombKey && __ldcg(&dist[w]) == kNil)
-                    grab = atomicCAS(&dist[w], kNil, level + 1) == kNil;
-                const uint32_t m = __ballot_sync(kFull, grab);
-                uint32_t base = 0;
-                if (lane == 0 && m)
-                    base = atomicAdd(next_count, (uint32_t)__popc(m));
-                base = __shfl_sync(kFull, base, 0);
+        uint32_t slab = __ldcg(&front[k]);
+        for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
+            const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
+            ++loads;
+            bool grab = false;
+            if (is_set_key_lane(lane) && w < kTombKey && __ldcg(&dist[w]) == kNil)
+                grab = atomicCAS(&dist[w], kNil, level + 1) == kNil;
+            if (__any_sync(kFull, grab)) {
+                uint2 vi = make_uint2(0, 0);
                 if (grab)
-                    next[base + __popc(m & lanemask_lt())] = w;
-                slab = __shfl_sync(kFull, w, kNextLane);
+                    vi = __ldg(&g.vinfo[w]);
+                // exclusive scan of the new vertices' list counts
+                uint32_t incl = vi.y;
+                for (uint32_t o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o)
+                        incl += t;
+                }
+                const uint32_t total = __shfl_sync(kFull, incl, 31);
+                uint32_t base = 0;
+                if (lane == 0)
+                    base = atomicAdd(next_count, total);
+                base = __shfl_sync(kFull, base, 0) + incl - vi.y;
+                if (vi.y <= 8) {
+                    for (uint32_t b = 0; b < vi.y; ++b)
+                        next[base + b] = vi.x + b;
+                }
+                uint32_t big = __ballot_sync(kFull, vi.y > 8);
+                while (big) {
+                    const uint32_t j = __ffs(big) - 1;
+                    big &= big - 1;
+                    const uint32_t bj = __shfl_sync(kFull, base, j), fj = __shfl_sync(kFull, vi.x, j),
+                                   nj = __shfl_sync(kFull, vi.y, j);
+                    for (uint32_t b = lane; b < nj; b += 32)
+                        next[bj + b] = fj + b;
+                }
             }
+            slab = __shfl_sync(kFull, w, kNextLane);
         }
     }
-    count_add(g.st, kCtrRelaxSlabs, loads / 32);
+    count_add(g.st, kCtrRelaxSlabs, loads);
 }
 
 // BFS parents: the smallest u with a live edge u -> v and dist[u] + 1 ==
@@ -342,15 +397,22 @@ __global__ void __launch_bounds__(256) k_set_bfs_parent(GView g, const uint32_t 
     }
 }
 
-__global__ void k_set_bfs_init(uint32_t *dist, uint32_t *parent, uint32_t V, uint32_t source, uint32_t *front)
+// dist / parent start values; the first frontier is the source's lists.
+__global__ void k_set_bfs_init(GView g, uint32_t *dist, uint32_t *parent, uint32_t source, uint32_t *front,
+                               uint32_t *cnt)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < V) {
+    const uint2 vi = __ldg(&g.vinfo[source]);
+    if (v < g.V) {
         dist[v] = v == source ? 0u : kNil;
         parent[v] = v == source ? source : kNil;
     }
-    if (v == 0)
-        front[0] = source;
+    for (uint32_t i = v; i < vi.y; i += gridDim.x * blockDim.x)
+        front[i] = vi.x + i;
+    if (v == 0) {
+        cnt[0] = vi.y;
+        cnt[1] = cnt[2] = 0;
+    }
 }
 
 namespace {
@@ -378,37 +440,59 @@ __global__ void k_set_uf_init(uint32_t *p, uint32_t V)
         p[v] = v;
 }
 
-// Static WCC: every live edge u -> v (one warp per slab in use, the owner is
-// u) unites the sets of u and v, the larger root hooked under the smaller
-// with a CAS (retried with fresh roots when it loses), so each root is its
-// set's smallest vertex.
+// Static WCC (Union-Async, the larger root hooked under the smaller, so each
+// root is its set's smallest vertex): a warp takes 32 consecutive slabs,
+// keeps those in use (owner set) and unites four slabs at a time, one per
+// 8-lane group, each lane holding four keys of the slab (one 16-byte load);
+// the group's last lane puts the slab's owner in place of the next index,
+// so the owner and the slab's 31 destinations are hooked under the
+// smallest of their roots in one group union.  The next step's slabs are
+// loaded a step ahead.
 __global__ void __launch_bounds__(256) k_set_wcc_hook(GView g, uint32_t *p, int *failed)
 {
-    const uint32_t lane = lane_id();
+    __shared__ uint8_t comp[8][32];
+    const uint32_t lane = lane_id(), g8 = lane >> 3, s8 = lane & 7u, w = threadIdx.x >> 5;
     const uint64_t total = (uint64_t)g.H + g.P;
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t s = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; s < total; s += warps) {
-        const uint32_t u = __ldg(&g.owner[s]);
-        if (u == kNil)
-            continue;
-        const uint32_t w = __ldcg(slab_ptr(g, (uint32_t)s) + lane);
-        if (!is_set_key_lane(lane) || w >= kTombKey)
-            continue;
-        uint32_t a = u, b = w;
-        bool done = false;
-        for (uint32_t it = 0; it < (1u << 20) && !done; ++it) {
-            a = set_find(p, a);
-            b = set_find(p, b);
-            if (a == b) {
-                done = true;
-            } else {
-                const uint32_t hi = max(a, b), lo = min(a, b);
-                done = atomicCAS(&p[hi], hi, lo) == hi;
-            }
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * 32;
+    const uint4 none = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
+    auto part = [&](uint64_t s) {
+        return __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s)) + s8);
+    };
+    unsigned long long slabs = 0, edges = 0;
+    uint64_t c = warp0 * 32;
+    uint32_t own_next = c + lane < total ? __ldcg(&g.owner[c + lane]) : kNil;
+    for (; c < total; c += stride) {
+        const uint32_t own_l = own_next;
+        own_next = c + stride + lane < total ? __ldcg(&g.owner[c + stride + lane]) : kNil;
+        const uint32_t live = __ballot_sync(kFull, own_l != kNil);
+        const uint32_t n = __popc(live);
+        if (own_l != kNil)
+            comp[w][__popc(live & lanemask_lt())] = (uint8_t)lane;
+        __syncwarp();
+        uint32_t it = g8 < n ? comp[w][g8] : 32u;
+        uint4 q = it < 32 ? part(c + it) : none;
+        for (uint32_t j = g8; j - g8 < n; j += 4) {
+            const uint32_t nit = j + 4 < n ? comp[w][j + 4] : 32u;
+            const uint4 nq = nit < 32 ? part(c + nit) : none;
+            const bool active = it < 32;
+            const uint32_t own = __shfl_sync(kFull, own_l, it & 31);
+            slabs += __popc(__ballot_sync(kFull, active && s8 == 0));
+            const bool last = s8 == 7u;
+            const uint32_t e[4] = {q.x, q.y, q.z, last ? own : q.w};
+            const bool act[4] = {active && q.x < kTombKey, active && q.y < kTombKey, active && q.z < kTombKey,
+                                 last ? active : (active && q.w < kTombKey)};
+            edges += __popc(__ballot_sync(kFull, act[0])) + __popc(__ballot_sync(kFull, act[1])) +
+                     __popc(__ballot_sync(kFull, act[2])) + __popc(__ballot_sync(kFull, act[3] && !last));
+            if (!group_union<8, 4>(p, e, act, 1u << 20) && lane == 0)
+                *failed = 1;
+            q = nq;
+            it = nit;
         }
-        if (!done)
-            *failed = 1;
+        __syncwarp();
     }
+    count_add(g.st, kCtrWccSlabs, slabs);
+    count_add(g.st, kCtrWccEdges, edges);
 }
 
 __global__ void k_set_wcc_label(uint32_t *p, uint32_t V, uint32_t *label)
@@ -657,31 +741,31 @@ mk_status mk_set_bfs(mk_set_graph *g, uint32_t source, uint32_t *d_dist, uint32_
         return MK_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t V = g->v.V;
+    const uint64_t H = g->v.H;
+    // levels go out in groups; the host reads the frontier size once a group
+    constexpr uint32_t kGroup = 6;
     uint32_t *front[2] = {nullptr, nullptr}, *cnt = nullptr;
-    MK_CUDA(cudaMallocAsync((void **)&front[0], (size_t)V * 4, s));
-    MK_CUDA(cudaMallocAsync((void **)&front[1], (size_t)V * 4, s));
-    MK_CUDA(cudaMallocAsync((void **)&cnt, 8, s));
-    k_set_bfs_init<<<grid_for(V, 256), 256, 0, s>>>(d_dist, d_parent, V, source, front[0]);
+    MK_CUDA(cudaMallocAsync((void **)&front[0], H * 4, s));
+    MK_CUDA(cudaMallocAsync((void **)&front[1], H * 4, s));
+    MK_CUDA(cudaMallocAsync((void **)&cnt, 16, s));
+    k_set_bfs_init<<<grid_for(V, 256), 256, 0, s>>>(g->v, d_dist, d_parent, source, front[0], cnt);
+    const uint32_t grid = (uint32_t)num_sms() * 8;
     mk_status st = MK_OK;
-    uint32_t n = 1, level = 0;
-    while (n && st == MK_OK) {
-        if (level > V) {
+    for (uint32_t level = 0;;) {
+        if (level > V + kGroup) {
             st = MK_ERR_TIMEOUT;
             break;
         }
-        if (cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) {
-            st = MK_ERR_CUDA;
-            break;
-        }
-        k_set_bfs_level<<<set_grid(n), 256, 0, s>>>(g->v, front[level & 1], n, front[(level + 1) & 1], cnt, d_dist,
-                                                   level, g->v.P + 2);
-        if (cudaMemcpyAsync(g->h_pinned, cnt, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        for (uint32_t i = 0; i < kGroup; ++i, ++level)
+            k_set_bfs_level<<<grid, 256, 0, s>>>(g->v, front[level & 1], front[(level + 1) & 1], cnt, d_dist, level,
+                                                 g->v.P + 2);
+        if (cudaMemcpyAsync(g->h_pinned, cnt + level % 3, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = MK_ERR_CUDA;
             break;
         }
-        n = g->h_pinned[0];
-        ++level;
+        if (g->h_pinned[0] == 0)
+            break;
     }
     if (st == MK_OK) {
         k_set_bfs_parent<<<set_grid(((uint64_t)g->v.H + g->v.P + 31) / 32), 256, 0, s>>>(g->v, d_dist, d_parent,
@@ -707,7 +791,7 @@ mk_status mk_set_wcc(mk_set_graph *g, uint32_t *d_label, void *stream)
     MK_CUDA(cudaMallocAsync((void **)&failed, sizeof(int), s));
     MK_CUDA(cudaMemsetAsync(failed, 0, sizeof(int), s));
     k_set_uf_init<<<grid_for(V, 256), 256, 0, s>>>(p, V);
-    k_set_wcc_hook<<<set_grid(((uint64_t)g->v.H + g->v.P + 31) / 32), 256, 0, s>>>(g->v, p, failed);
+    k_set_wcc_hook<<<resident_grid(k_set_wcc_hook, 256), 256, 0, s>>>(g->v, p, failed);
     k_set_wcc_label<<<grid_for(V, 256), 256, 0, s>>>(p, V, d_label);
     k_set_flag_status<<<1, 1, 0, s>>>(failed, g->v.st);
     const cudaError_t e = cudaGetLastError();

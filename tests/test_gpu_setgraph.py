@@ -81,3 +81,28 @@ def test_set_graph_power_law_and_slab_count(cuda_lib):
     assert g.last_error() == mk.MK_OK and m.last_error() == mk.MK_OK
     g.close()
     m.close()
+
+
+@pytest.mark.parametrize("buckets", [1, 12])
+def test_set_graph_deep_bfs_and_isolated_source(cuda_lib, buckets):
+    """A 150-edge path (150 levels, many groups of level launches) with side
+    branches, a vertex without out-edges as source, and an empty graph."""
+    mk = _mk()
+    V = 400
+    s = np.arange(150, dtype=np.uint32)
+    d = s + 1
+    bs = np.arange(0, 150, 7, dtype=np.uint32)
+    src = np.concatenate([s, bs, [300, 300]]).astype(np.uint32)
+    dst = np.concatenate([d, bs + 200, [301, 0]]).astype(np.uint32)
+    g = mk.SetGraph(V, edge_capacity_hint=1024, buckets=buckets)
+    o = oracle.OracleGraph(V)
+    e = mk.SetGraph(V, buckets=buckets)
+    oe = oracle.OracleGraph(V)
+    _check_algos(mk, e, oe, [0, 399])
+    assert np.array_equal(g.insert(src, dst).cpu().numpy(), o.insert(src, dst))
+    _check_algos(mk, g, o, [0, 300, 399, 150])
+    assert np.array_equal(g.delete([75], [76]).cpu().numpy(), o.delete([75], [76]))
+    _check_algos(mk, g, o, [0, 300])
+    assert g.last_error() == mk.MK_OK and e.last_error() == mk.MK_OK
+    g.close()
+    e.close()
