@@ -243,21 +243,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "4a52c118a3d4eeeb0ca653389a2bab5e48a4c0dcf12c0bdb492b99fc18218a2b"
+NCU_TRAFFIC_SOURCES_SHA = "59f81cbea540d26fc57317f67445bd530bc143395cf4289242ab3afc8f23218e"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49606144,
-    "sssp_relax_into_invalid": 280873088,
-    "sssp_enqueue_invalid": 11004928,
-    "sssp_relax_updated": 26477504,
-    "sssp_invalidate_walk": 8524288,
-    "sssp_invalidate": 13743552,
-    "wcc_hook_all": 350659840,
-    "wcc_hook_updated": 19097216,
-    "insert": 255045120,
-    "delete": 198536320,
-    "query": 130993280,
-    "stage_dedup": 40137152,
-    "update_slab_pointers": 60560576,
+    "sssp_rounds": 49420160,
+    "sssp_relax_into_invalid": 280909056,
+    "sssp_enqueue_invalid": 11006080,
+    "sssp_relax_updated": 26475584,
+    "sssp_invalidate_walk": 8523968,
+    "sssp_invalidate": 13739072,
+    "wcc_hook_all": 350713984,
+    "wcc_hook_updated": 19097344,
+    "insert": 255048448,
+    "delete": 198481024,
+    "query": 130871552,
+    "stage_dedup": 40150976,
+    "update_slab_pointers": 60557760,
 }
 
 
