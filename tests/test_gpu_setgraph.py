@@ -106,3 +106,28 @@ def test_set_graph_deep_bfs_and_isolated_source(cuda_lib, buckets):
     assert g.last_error() == mk.MK_OK and e.last_error() == mk.MK_OK
     g.close()
     e.close()
+
+
+def test_set_graph_rmat18_against_oracle(cuda_lib):
+    """R-MAT scale 18 (about 3.6 M edges, hubs with thousands of lists'
+    worth of keys): load, BFS from the three largest out-degree vertices and
+    WCC, then a 2^18 stream batch of inserts, deletes of live edges and
+    half-present queries, and BFS / WCC again, all against the oracle."""
+    mk = _mk()
+    G = synth.powerlaw_graph(scale=18, draws=1 << 22)
+    g = mk.SetGraph(G.V, edge_capacity_hint=len(G.src) + (1 << 19), buckets=mk.set_bucket_rule(G.V, G.src, 0.7))
+    o = oracle.OracleGraph(G.V)
+    assert np.array_equal(g.insert(G.src, G.dst).cpu().numpy(), o.insert(G.src, G.dst))
+    top = [int(x) for x in np.argsort(-o.out_degree().astype(np.int64), kind="stable")[:3]]
+    _check_algos(mk, g, o, top)
+    b = synth.PowerlawStream(G, max_batch=1 << 18).batch(1 << 18)
+    fi = g.insert(b.ins_src, b.ins_dst).cpu().numpy()
+    assert np.array_equal(fi, o.insert(b.ins_src, b.ins_dst))
+    fd = g.delete(b.del_src, b.del_dst).cpu().numpy()
+    assert np.array_equal(fd, o.delete(b.del_src, b.del_dst)) and fd.all()
+    bm, _ = o.query(b.q_src, b.q_dst)
+    assert np.array_equal(mk.to_numpy_u32(g.query(b.q_src, b.q_dst)), bm)
+    assert int(oracle.bitmap_to_bool(bm, len(b.q_src)).sum()) == b.n_present
+    _check_algos(mk, g, o, top[:1])
+    assert g.last_error() == mk.MK_OK
+    g.close()
