@@ -665,9 +665,13 @@ def run_e2e(R, batches, B, dist, units_total):
     beside the phases still running; only the SSSP tree leaves at the end."""
     torch, mk = R.torch, R.mk
     device, stream, V = R.device, R.stream, R.V
-    host = [{k: torch.from_numpy(np.ascontiguousarray(bt[k]).view(np.int32)).pin_memory() for k in BATCH_KEYS}
-            for bt in batches]
-    stage = {k: torch.empty(B, dtype=torch.int32, device=device) for k in BATCH_KEYS}
+    # a step's seven input arrays sit back to back in one pinned buffer (the
+    # insert's three first), so they come in with two copies, not seven
+    host = [torch.from_numpy(np.concatenate([np.ascontiguousarray(bt[k]).view(np.int32) for k in BATCH_KEYS]))
+            .pin_memory() for bt in batches]
+    stage_all = torch.empty(len(BATCH_KEYS) * B, dtype=torch.int32, device=device)
+    stage = {k: stage_all[i * B:(i + 1) * B] for i, k in enumerate(BATCH_KEYS)}
+    n_ins = 3 * B
     outs = R.outputs(B, 1)[0]
     fl_i, fl_d, bm = outs
     h_fl_i = torch.empty(B, dtype=torch.uint8).pin_memory()
@@ -675,19 +679,22 @@ def run_e2e(R, batches, B, dist, units_total):
     h_bm = torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory()
     h_res = {k: torch.empty(V, dtype=torch.int32).pin_memory() for k in R.out}
     copy = torch.cuda.Stream(device=device)
-    e2e_ms = []
+    e2e_ms, parts = [], []
     for k in range(len(batches)):
         R.flush.fill_(100 + k)
         e = R.events(14)
         torch.cuda.synchronize()
         e[0].record(stream)
-        for key in ("ins_src", "ins_dst", "ins_w"):
-            stage[key].copy_(host[k][key], non_blocking=True)
-        copy.wait_event(e[0])
+        with torch.cuda.stream(stream):
+            stage_all[:n_ins].copy_(host[k][:n_ins], non_blocking=True)
+        # the later phases' inputs follow the insert's on the link (copies
+        # that share it would delay the insert's), while the insert runs
+        ins_in = torch.cuda.Event()
+        ins_in.record(stream)
+        copy.wait_event(ins_in)
         ready = torch.cuda.Event()
         with torch.cuda.stream(copy):
-            for key in ("del_src", "del_dst", "q_src", "q_dst"):
-                stage[key].copy_(host[k][key], non_blocking=True)
+            stage_all[n_ins:].copy_(host[k][n_ins:], non_blocking=True)
             ready.record(copy)
 
         def on_copy(src_stream, pairs):
@@ -716,6 +723,7 @@ def run_e2e(R, batches, B, dist, units_total):
         e[13].record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(e[0].elapsed_time(e[13]))
+        parts.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[12]), e[12].elapsed_time(e[13])))
         bt = batches[k]
         nq = int(np.unpackbits(h_bm.numpy().view(np.uint8)).sum())
         if (int(h_fl_i.sum()) != bt["n_inserted"] or int(h_fl_d.sum()) != B or nq != bt["n_present"]):
@@ -727,7 +735,12 @@ def run_e2e(R, batches, B, dist, units_total):
             "h2d_bytes_per_step": int(B * 4 * len(BATCH_KEYS)),
             "d2h_bytes_per_step": int(2 * B + 4 * ((B + 31) // 32) + 4 * V * len(R.out)),
             "ms_per_step": round(e2e_max, 3), "batches": [int(bt["k"]) for bt in batches],
-            "copies": "in: the step's 7 input arrays from pinned host memory; out: insert and delete flags, query "
+            # the step's own span split in three: the insert inputs coming in
+            # before the first call, the calls (with the other copies beside
+            # them), and the SSSP tree (with any copy still running) after
+            "split_ms": {name: round(statistics.mean(p[i] for p in parts), 3)
+                         for i, name in enumerate(("inputs_in", "calls", "tail_out"))},
+            "copies": "in: the step's 7 input arrays, back to back in one pinned host buffer (two copies); out: insert and delete flags, query "
                       "bitmap, BFS and SSSP distances and parents, WCC labels"}
 
 
