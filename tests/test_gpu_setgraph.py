@@ -131,3 +131,37 @@ def test_set_graph_rmat18_against_oracle(cuda_lib):
     _check_algos(mk, g, o, top[:1])
     assert g.last_error() == mk.MK_OK
     g.close()
+
+
+def test_set_graph_invalid_ids_and_pool_exhaustion(cuda_lib):
+    """Invalid vertex ids set the sticky status; an exhausted pool reports
+    MK_ERR_POOL_EXHAUSTED with exactly the flagged edges stored, and the
+    traversals still run on what was stored."""
+    mk = _mk()
+    g = mk.SetGraph(4, buckets=1)
+    f = g.insert([0, 5, 1], [1, 2, 2]).cpu().numpy()
+    assert f[1] == 0
+    assert g.last_error() == mk.MK_ERR_INVALID_ARG
+    bm = g.query([0, 1], [1, 2])
+    assert g.last_error() == mk.MK_OK
+    got = oracle.bitmap_to_bool(mk.to_numpy_u32(bm), 2)
+    assert np.array_equal(got, f[[0, 2]].astype(bool))
+    g.query([7], [0])
+    assert g.last_error() == mk.MK_ERR_INVALID_ARG
+    g.close()
+
+    V = 50000
+    src = np.repeat(np.arange(40, dtype=np.uint32), V)
+    dst = np.tile(np.arange(V, dtype=np.uint32), 40)
+    g = mk.SetGraph(V, edge_capacity_hint=0, buckets=1)
+    f = g.insert(src, dst).cpu().numpy()
+    assert g.last_error() == mk.MK_ERR_POOL_EXHAUSTED
+    assert 0 < int(f.sum()) < len(src)
+    bm = g.query(src, dst)
+    assert np.array_equal(oracle.bitmap_to_bool(mk.to_numpy_u32(bm), len(src)), f.astype(bool))
+    o = oracle.OracleGraph(V)
+    keep = f.astype(bool)
+    o.insert(src[keep], dst[keep])
+    _check_algos(mk, g, o, [0, 39])
+    assert g.last_error() == mk.MK_OK
+    g.close()
