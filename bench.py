@@ -658,13 +658,18 @@ def o_e_share(kernels):
 
 def run_e2e(R, batches, B, dist, units_total):
     """Steps through the C ABI with the inputs in pinned host memory: every
-    step copies its inputs in and its results out inside the timed region
+    step copies its inputs in and its results out inside its timed span
     (insert and delete flags, the query bitmap, BFS and SSSP distances and
     parents, WCC labels).  The inputs of later phases come in, and every
     result leaves as soon as the step no longer writes it, on a copy stream
-    beside the phases still running; only the SSSP tree leaves at the end."""
+    beside the phases still running; only the SSSP tree leaves at the end.
+    The steps are queued back to back, as the device-resident steps are
+    (each step's span runs from before its first copy in to after its last
+    copy out, and the next step's copies wait for it), and every step's
+    results are checked on the host after the last one."""
     torch, mk = R.torch, R.mk
     device, stream, V = R.device, R.stream, R.V
+    K = len(batches)
     # a step's seven input arrays sit back to back in one pinned buffer (the
     # insert's three first), so they come in with two copies, not seven
     host = [torch.from_numpy(np.concatenate([np.ascontiguousarray(bt[k]).view(np.int32) for k in BATCH_KEYS]))
@@ -674,16 +679,28 @@ def run_e2e(R, batches, B, dist, units_total):
     n_ins = 3 * B
     outs = R.outputs(B, 1)[0]
     fl_i, fl_d, bm = outs
-    h_fl_i = torch.empty(B, dtype=torch.uint8).pin_memory()
-    h_fl_d = torch.empty(B, dtype=torch.uint8).pin_memory()
-    h_bm = torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory()
-    h_res = {k: torch.empty(V, dtype=torch.int32).pin_memory() for k in R.out}
+    # one set of pinned result buffers per step
+    h_out = [{"fl_i": torch.empty(B, dtype=torch.uint8).pin_memory(),
+              "fl_d": torch.empty(B, dtype=torch.uint8).pin_memory(),
+              "bm": torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory(),
+              **{key: torch.empty(V, dtype=torch.int32).pin_memory() for key in R.out}} for _ in range(K)]
     copy = torch.cuda.Stream(device=device)
-    e2e_ms, parts = [], []
-    for k in range(len(batches)):
+    evs = [R.events(14) for _ in range(K)]
+    wevs = [R.events(5) for _ in range(K)]
+
+    def on_copy(src_stream, pairs):
+        """Copy stream waits for src_stream's work so far, then copies."""
+        done = torch.cuda.Event()
+        done.record(src_stream)
+        copy.wait_event(done)
+        with torch.cuda.stream(copy):
+            for dst, t in pairs:
+                dst.copy_(t, non_blocking=True)
+
+    torch.cuda.synchronize()
+    for k in range(K):
+        e, h = evs[k], h_out[k]
         R.flush.fill_(100 + k)
-        e = R.events(14)
-        torch.cuda.synchronize()
         e[0].record(stream)
         with torch.cuda.stream(stream):
             stage_all[:n_ins].copy_(host[k][:n_ins], non_blocking=True)
@@ -696,37 +713,31 @@ def run_e2e(R, batches, B, dist, units_total):
         with torch.cuda.stream(copy):
             stage_all[n_ins:].copy_(host[k][n_ins:], non_blocking=True)
             ready.record(copy)
-
-        def on_copy(src_stream, pairs):
-            """Copy stream waits for src_stream's work so far, then copies."""
-            done = torch.cuda.Event()
-            done.record(src_stream)
-            copy.wait_event(done)
-            with torch.cuda.stream(copy):
-                for dst, t in pairs:
-                    dst.copy_(t, non_blocking=True)
-
         hooks = {
-            "after_insert": lambda: on_copy(stream, [(h_fl_i, fl_i)]),
-            "before_delete": lambda: stream.wait_event(ready),
-            "after_delete": lambda: on_copy(stream, [(h_fl_d, fl_d)]),
+            "after_insert": lambda h=h: on_copy(stream, [(h["fl_i"], fl_i)]),
+            "before_delete": lambda ready=ready: stream.wait_event(ready),
+            "after_delete": lambda h=h: on_copy(stream, [(h["fl_d"], fl_d)]),
             # results that nothing later in the step rewrites leave while
             # the rest of the step runs: the query bitmap and the WCC labels
             # (second stream), the BFS tree (main stream, beside the SSSP)
-            "after_side": lambda ws: on_copy(ws, [(h_bm, bm), (h_res["lab"], R.out["lab"])]),
-            "after_bfs": lambda: on_copy(stream, [(h_res["bd"], R.out["bd"]), (h_res["bp"], R.out["bp"])]),
+            "after_side": lambda ws, h=h: on_copy(ws, [(h["bm"], bm), (h["lab"], R.out["lab"])]),
+            "after_bfs": lambda h=h: on_copy(stream, [(h["bd"], R.out["bd"]), (h["bp"], R.out["bp"])]),
         }
-        R.step(stage, B, outs, e[1:13], R.events(5), hooks)
+        R.step(stage, B, outs, e[1:13], wevs[k], hooks)
         for key in ("sd", "sp"):
-            h_res[key].copy_(R.out[key], non_blocking=True)
+            h[key].copy_(R.out[key], non_blocking=True)
+        # the next step rewrites the device buffers only after every copy
+        # of this one
         stream.wait_stream(copy)
         e[13].record(stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(e[0].elapsed_time(e[13]))
-        parts.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[12]), e[12].elapsed_time(e[13])))
-        bt = batches[k]
-        nq = int(np.unpackbits(h_bm.numpy().view(np.uint8)).sum())
-        if (int(h_fl_i.sum()) != bt["n_inserted"] or int(h_fl_d.sum()) != B or nq != bt["n_present"]):
+    torch.cuda.synchronize()
+    e2e_ms = [evs[k][0].elapsed_time(evs[k][13]) for k in range(K)]
+    parts = [(evs[k][0].elapsed_time(evs[k][1]), evs[k][1].elapsed_time(evs[k][12]),
+              evs[k][12].elapsed_time(evs[k][13])) for k in range(K)]
+    for k, bt in enumerate(batches):
+        h = h_out[k]
+        nq = int(np.unpackbits(h["bm"].numpy().view(np.uint8)).sum())
+        if (int(h["fl_i"].sum()) != bt["n_inserted"] or int(h["fl_d"].sum()) != B or nq != bt["n_present"]):
             raise RuntimeError("e2e batch %d is off the workload" % bt["k"])
     if R.g.last_error() != mk.MK_OK:
         raise RuntimeError("device status in the e2e pass")
@@ -740,8 +751,9 @@ def run_e2e(R, batches, B, dist, units_total):
             # them), and the SSSP tree (with any copy still running) after
             "split_ms": {name: round(statistics.mean(p[i] for p in parts), 3)
                          for i, name in enumerate(("inputs_in", "calls", "tail_out"))},
-            "copies": "in: the step's 7 input arrays, back to back in one pinned host buffer (two copies); out: insert and delete flags, query "
-                      "bitmap, BFS and SSSP distances and parents, WCC labels"}
+            "copies": "in: the step's 7 input arrays, back to back in one pinned host buffer (two copies); out: "
+                      "insert and delete flags, query bitmap, BFS and SSSP distances and parents, WCC labels, "
+                      "into pinned buffers of each step, checked after the run"}
 
 
 # ------------------------------------------------------- learned sizing
