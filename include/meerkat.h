@@ -450,7 +450,8 @@ mk_status mk_set_create(uint32_t V, uint64_t edge_capacity_hint, uint32_t bucket
 mk_status mk_set_destroy(mk_set_graph *g);
 /* Insert / delete / query n edges as mk_insert_batch / mk_delete_batch /
  * mk_query_batch do (no weights; flags and bitmap nullable / required
- * alike).  One warp handles one edge at a time with 128-byte slab loads. */
+ * alike).  A warp walks eight chains at once, one per 4-lane group (32
+ * bytes of the slab a lane). */
 mk_status mk_set_insert_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                               uint8_t *d_inserted, void *stream);
 mk_status mk_set_delete_batch(mk_set_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,

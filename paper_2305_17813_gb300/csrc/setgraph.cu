@@ -10,12 +10,12 @@
 // counts, overflow slabs claimed from a bitmap pool, EMPTY and TOMBSTONE
 // keys, deleted keys never reused (so free keys exist only in a chain's last
 // slab), set semantics with the first occurrence of a repeated pair applied
-// (the batch is deduplicated by the map store's staging kernel).  One warp
-// handles one edge at a time, reading a slab with one coalesced 128-byte
-// load (the paper's warp-cooperative strategy).  BFS (hop counts, with the
-// smallest-id tight parent) and WCC (smallest-id labels) run statically:
-// BFS level by level over a frontier of lists, WCC as one union-find pass
-// over the slab array.
+// (the batch is deduplicated by the map store's staging kernel).  Inserts,
+// deletes and queries walk eight chains per warp in 4-lane groups, each
+// lane reading 32 bytes of a slab (the whole group one 128-byte slab).  BFS
+// (hop counts, with the smallest-id tight parent) and WCC (smallest-id
+// labels) run statically: BFS level by level over a frontier of lists, WCC
+// as one union-find pass over the slab array.
 #include "mk_host.h"
 #include "uf.cuh"
 
@@ -84,72 +84,170 @@ __device__ __forceinline__ uint32_t set_list(const GView &g, uint32_t s, uint32_
     return vi.x + bucket_of(d, vi.y);
 }
 
-// One warp, one edge: 1 if d was stored, 0 if present already, or a
-// negative device error code.  Walks the whole chain (a present key ends
-// the walk), claims the lowest free key of the tail with a CAS, or links a
-// pool slab holding d with a CAS on the tail's next lane.
-__device__ __forceinline__ int warp_set_insert(const GView &g, uint32_t s, uint32_t d, uint32_t max_hops,
-                                               unsigned long long &loads, unsigned long long &linked)
+// Lanes of the calling lane's 4-lane group in a warp-wide ballot.
+__device__ __forceinline__ uint32_t set_group_bits(uint32_t ballot) { return (ballot >> (lane_id() & ~3u)) & 0xFu; }
+
+// Lane s4 of a 4-lane group holds words 8*s4 .. 8*s4+7 of a slab as two
+// 16-byte vectors; word 31 (the last of lane 3) is the next index.
+__device__ __forceinline__ void set_group_load(const GView &g, uint32_t slab, uint4 &lo, uint4 &hi)
 {
-    const uint32_t lane = lane_id();
-    uint32_t slab = set_list(g, s, d);
-    for (uint32_t guard = 0; guard < 4 * max_hops + 64; ++guard) {
-        const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
-        ++loads;
-        if (__ballot_sync(kFull, is_set_key_lane(lane) && w == d))
-            return 0;
-        const uint32_t empty = __ballot_sync(kFull, is_set_key_lane(lane) && w == kEmptyKey);
-        const uint32_t nxt = __shfl_sync(kFull, w, kNextLane);
-        if (empty) {
-            const uint32_t l = __ffs(empty) - 1;
-            uint32_t ok = 0;
-            if (lane == l)
-                ok = atomicCAS(slab_ptr(g, slab) + l, kEmptyKey, d) == kEmptyKey;
-            if (__shfl_sync(kFull, ok, l))
-                return 1;
-            continue; // another warp took the key: read the slab again
-        }
-        if (nxt != kNil) {
-            slab = nxt;
-            continue;
-        }
+    const uint4 *p = reinterpret_cast<const uint4 *>(slab_ptr(g, slab) + (lane_id() & 3u) * 8);
+    lo = __ldcg(p);
+    hi = __ldcg(p + 1);
+}
+
+// Index (0..7) of the lane's first key word equal to k, 8 if none.
+__device__ __forceinline__ uint32_t set_first_with(const uint4 &lo, const uint4 &hi, uint32_t k)
+{
+    const bool last = (lane_id() & 3u) == 3u;
+    return lo.x == k   ? 0u
+           : lo.y == k ? 1u
+           : lo.z == k ? 2u
+           : lo.w == k ? 3u
+           : hi.x == k ? 4u
+           : hi.y == k ? 5u
+           : hi.z == k ? 6u
+           : (!last && hi.w == k) ? 7u
+                                  : 8u;
+}
+
+// Inserts d into the list of s with one 4-lane group (go == false: the
+// group has nothing to do; every group of the warp calls it in lockstep).
+// Walks the whole chain (a present key ends the walk), claims the lowest
+// free key of the tail with a CAS (a lost CAS re-reads the slab), or links a
+// pool slab holding d with a CAS on the tail's next word (the loser frees
+// its slab and follows the winner's).  Returns 1 if d was stored, 0 if it
+// was present, or a negative device error code, on the group's lanes.
+__device__ __forceinline__ int group_set_insert(const GView &g, bool go, uint32_t s, uint32_t d, uint32_t max_hops,
+                                                unsigned long long &loads, unsigned long long &linked)
+{
+    const uint32_t s4 = lane_id() & 3u, gbase = lane_id() & ~3u;
+    bool active = go;
+    int res = 0;
+    uint32_t slab = go ? set_list(g, s, d) : kNil;
+    uint4 lo = make_uint4(kFull, kFull, kFull, kFull), hi = lo;
+    if (active)
+        set_group_load(g, slab, lo, hi);
+    const uint32_t guard_max = 4 * max_hops + 64;
+    for (uint32_t guard = 0; __any_sync(kFull, active); ++guard) {
+        loads += __popc(__ballot_sync(kFull, active && s4 == 0));
+        const uint32_t hits = set_group_bits(__ballot_sync(kFull, active && set_first_with(lo, hi, d) < 8u));
+        const uint32_t fk = set_first_with(lo, hi, kEmptyKey);
+        const uint32_t frees = set_group_bits(__ballot_sync(kFull, active && fk < 8u));
+        const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
+        // the lowest free key of the group's slab
+        bool ok = false;
+        if (active && !hits && frees && s4 == (uint32_t)(__ffs(frees) - 1))
+            ok = atomicCAS(slab_ptr(g, slab) + 8 * s4 + fk, kEmptyKey, d) == kEmptyKey;
+        const bool claimed = set_group_bits(__ballot_sync(kFull, ok)) != 0;
         // a full tail with nothing after it: a pool slab holding d
-        const uint32_t ns = alloc_slab(g, s * 0x9E3779B9u ^ d ^ (guard << 26));
-        if (ns == kNil)
-            return kErrPool;
-        __stcg(slab_ptr(g, ns) + lane, lane == 0 ? d : (lane == kNextLane ? kNil : kEmptyKey));
-        if (lane == 0)
-            g.owner[ns] = s;
-        __threadfence();
+        const bool grow = active && !hits && !frees && nxt == kNil;
+        uint32_t ns = kNil;
+        if (grow && s4 == 0)
+            ns = alloc_slab_one(g, s * 0x9E3779B9u ^ d ^ (guard << 26));
+        ns = __shfl_sync(kFull, ns, gbase);
         uint32_t old = kNil;
-        if (lane == 0)
-            old = atomicCAS(slab_ptr(g, slab) + kNextLane, kNil, ns);
-        old = __shfl_sync(kFull, old, 0);
-        if (old == kNil) {
-            ++linked;
-            return 1;
+        if (grow && ns != kNil) {
+            const uint4 e = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
+            const uint4 wlo = s4 == 0 ? make_uint4(d, kEmptyKey, kEmptyKey, kEmptyKey) : e;
+            const uint4 whi = s4 == 3u ? make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kNil) : e;
+            uint4 *q = reinterpret_cast<uint4 *>(slab_ptr(g, ns) + s4 * 8);
+            __stcg(q, wlo);
+            __stcg(q + 1, whi);
+            if (s4 == 0)
+                g.owner[ns] = s;
+            __threadfence();
+            if (s4 == 0)
+                old = atomicCAS(slab_ptr(g, slab) + kNextLane, kNil, ns);
         }
-        // lost the link: give the slab back and follow the winner's
-        if (lane == 0)
-            g.owner[ns] = kNil;
-        __threadfence();
-        if (lane == 0)
-            free_slab(g, ns);
-        slab = old;
+        old = __shfl_sync(kFull, old, gbase);
+        const bool won = grow && ns != kNil && old == kNil;
+        linked += __popc(__ballot_sync(kFull, won && s4 == 0));
+        if (active) {
+            if (hits) {
+                active = false; // present already
+            } else if (frees) {
+                if (claimed) {
+                    res = 1;
+                    active = false;
+                } // else another group took the key: read the slab again
+            } else if (nxt != kNil) {
+                slab = nxt;
+            } else if (ns == kNil) {
+                res = kErrPool;
+                active = false;
+            } else if (won) {
+                res = 1;
+                active = false;
+            } else { // lost the link: give the slab back, follow the winner's
+                if (s4 == 0)
+                    g.owner[ns] = kNil;
+                __threadfence();
+                if (s4 == 0)
+                    free_slab(g, ns);
+                slab = old;
+            }
+            if (active && guard >= guard_max) {
+                res = kErrTimeout;
+                active = false;
+            }
+        }
+        if (active)
+            set_group_load(g, slab, lo, hi);
     }
-    return kErrTimeout;
+    return res;
+}
+
+// Deletes d from the list of s with one 4-lane group (layout and lockstep
+// as above): the key becomes TOMBSTONE (never reused); the walk stops at the
+// key, at the chain's first free key or at its end.  Returns 1 if d was
+// removed.
+__device__ __forceinline__ int group_set_delete(const GView &g, bool go, uint32_t s, uint32_t d, uint32_t max_hops,
+                                                unsigned long long &loads)
+{
+    const uint32_t s4 = lane_id() & 3u, gbase = lane_id() & ~3u;
+    bool active = go;
+    int res = 0;
+    uint32_t slab = go ? set_list(g, s, d) : kNil;
+    uint4 lo = make_uint4(kFull, kFull, kFull, kFull), hi = lo;
+    for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+        if (active)
+            set_group_load(g, slab, lo, hi);
+        loads += __popc(__ballot_sync(kFull, active && s4 == 0));
+        const uint32_t hk = set_first_with(lo, hi, d);
+        const uint32_t hits = set_group_bits(__ballot_sync(kFull, active && hk < 8u));
+        const uint32_t frees = set_group_bits(__ballot_sync(kFull, active && set_first_with(lo, hi, kEmptyKey) < 8u));
+        const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
+        bool ok = false;
+        if (active && hits && s4 == (uint32_t)(__ffs(hits) - 1))
+            ok = atomicCAS(slab_ptr(g, slab) + 8 * s4 + hk, d, kTombKey) == d;
+        const bool removed = set_group_bits(__ballot_sync(kFull, ok)) != 0;
+        if (active) {
+            if (hits) {
+                res = removed ? 1 : 0;
+                active = false;
+            } else if (frees || nxt == kNil || hop + 1 >= max_hops) {
+                active = false;
+            } else {
+                slab = nxt;
+            }
+        }
+    }
+    return res;
 }
 
 } // namespace
 
-// One warp per chunk of 32 edges, the chunk's first occurrences one at a time.
+// One warp per chunk of 32 edges: eight 4-lane groups take the chunk's first
+// occurrences eight at a time (edge it * 8 + group in step it), so eight
+// chains are walked at once.
 __global__ void __launch_bounds__(256) k_set_insert(GView g, const uint32_t *__restrict__ src,
                                                     const uint32_t *__restrict__ dst, uint64_t n,
                                                     const uint32_t *__restrict__ tpos,
                                                     const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
                                                     uint32_t max_hops)
 {
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 2;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long loads = 0, linked = 0;
     for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
@@ -165,18 +263,18 @@ __global__ void __launch_bounds__(256) k_set_insert(GView g, const uint32_t *__r
             d = dst[i];
         }
         uint8_t mine = 0;
-        uint32_t todo = __ballot_sync(kFull, first);
-        while (todo) {
-            const uint32_t j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int r = warp_set_insert(g, __shfl_sync(kFull, s, j), __shfl_sync(kFull, d, j), max_hops, loads,
-                                          linked);
-            if (r < 0) {
-                if (lane == 0)
-                    set_status(g.st, r);
-            } else if (lane == j) {
-                mine = (uint8_t)r;
-            }
+#pragma unroll 1
+        for (uint32_t it = 0; it < 4; ++it) {
+            const uint32_t who = it * 8 + gi;
+            const bool go = __shfl_sync(kFull, first, who);
+            const int r = group_set_insert(g, go, __shfl_sync(kFull, s, who), __shfl_sync(kFull, d, who), max_hops,
+                                           loads, linked);
+            if (r < 0 && (lane & 3u) == 0)
+                set_status(g.st, r);
+            // lane L's edge was taken by group L % 8 in step L / 8
+            const int rl = __shfl_sync(kFull, r, (lane & 7u) * 4);
+            if (lane / 8 == it)
+                mine = rl > 0 ? 1 : 0;
         }
         if (flags && i < n)
             flags[i] = mine;
@@ -185,15 +283,14 @@ __global__ void __launch_bounds__(256) k_set_insert(GView g, const uint32_t *__r
     count_add(g.st, kCtrInsertNewSlabs, linked);
 }
 
-// Deletes: the key becomes TOMBSTONE (never reused); the walk stops at the
-// key or at the chain's first free key.
+// Deletes, in the same chunks and groups.
 __global__ void __launch_bounds__(256) k_set_delete(GView g, const uint32_t *__restrict__ src,
                                                     const uint32_t *__restrict__ dst, uint64_t n,
                                                     const uint32_t *__restrict__ tpos,
                                                     const uint32_t *__restrict__ slot, uint8_t *__restrict__ flags,
                                                     uint32_t max_hops)
 {
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), gi = lane >> 2;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long loads = 0;
     for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
@@ -209,30 +306,15 @@ __global__ void __launch_bounds__(256) k_set_delete(GView g, const uint32_t *__r
             d = dst[i];
         }
         uint8_t mine = 0;
-        uint32_t todo = __ballot_sync(kFull, first);
-        while (todo) {
-            const uint32_t j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t sj = __shfl_sync(kFull, s, j), dj = __shfl_sync(kFull, d, j);
-            uint32_t slab = set_list(g, sj, dj);
-            uint32_t removed = 0;
-            for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
-                const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
-                ++loads;
-                const uint32_t hit = __ballot_sync(kFull, is_set_key_lane(lane) && w == dj);
-                if (hit) {
-                    const uint32_t l = __ffs(hit) - 1;
-                    if (lane == l)
-                        removed = atomicCAS(slab_ptr(g, slab) + l, dj, kTombKey) == dj;
-                    removed = __shfl_sync(kFull, removed, l);
-                    break;
-                }
-                if (__ballot_sync(kFull, is_set_key_lane(lane) && w == kEmptyKey))
-                    break;
-                slab = __shfl_sync(kFull, w, kNextLane);
-            }
-            if (lane == j)
-                mine = (uint8_t)removed;
+#pragma unroll 1
+        for (uint32_t it = 0; it < 4; ++it) {
+            const uint32_t who = it * 8 + gi;
+            const bool go = __shfl_sync(kFull, first, who);
+            const int r = group_set_delete(g, go, __shfl_sync(kFull, s, who), __shfl_sync(kFull, d, who), max_hops,
+                                           loads);
+            const int rl = __shfl_sync(kFull, r, (lane & 7u) * 4);
+            if (lane / 8 == it)
+                mine = rl > 0 ? 1 : 0;
         }
         if (flags && i < n)
             flags[i] = mine;
