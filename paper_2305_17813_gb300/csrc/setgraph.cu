@@ -396,87 +396,119 @@ __global__ void __launch_bounds__(256) k_set_query(GView g, const uint32_t *__re
     count_add(g.st, kCtrQuerySlabs, loads);
 }
 
-// One BFS level over a frontier of lists (one warp per list, so a hub's
-// buckets spread over many warps).  A destination still unreached gets
-// level + 1 with a CAS and its lists join the next frontier: one atomicAdd
-// a warp per slab for all of the slab's new vertices.  The frontier sizes
-// live on the device in three rotating counters (this level reads
-// cnt[L % 3], appends to cnt[(L + 1) % 3] and clears cnt[(L + 2) % 3], the
-// input of the level before), so several levels go out without the host.
+// One BFS level over a frontier of lists, one list per 4-lane group (eight
+// lists per warp in flight, so a hub's buckets spread over many groups);
+// each lane tests the eight keys of its 32 bytes of a slab at once.  A
+// destination still unreached gets level + 1 with a CAS and its lists join
+// the next frontier: one atomicAdd a warp per slab step for all the new
+// vertices of its eight slabs.  The frontier sizes live on the device in
+// three rotating counters (this level reads cnt[L % 3], appends to
+// cnt[(L + 1) % 3] and clears cnt[(L + 2) % 3], the input of the level
+// before), so several levels go out without the host.
 __global__ void __launch_bounds__(256) k_set_bfs_level(GView g, const uint32_t *__restrict__ front, uint32_t *next,
-                                                       uint32_t *cnt, uint32_t *dist, uint32_t level,
-                                                       uint32_t max_hops)
+                                                       uint32_t *cnt, uint32_t *dist, uint32_t *parent,
+                                                       uint32_t level, uint32_t max_hops)
 {
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), s4 = lane & 3u, gbase = lane & ~3u;
     const uint32_t n = __ldcg(&cnt[level % 3]);
     uint32_t *next_count = &cnt[(level + 1) % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0)
         cnt[(level + 2) % 3] = 0;
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t groups = ((uint64_t)gridDim.x * blockDim.x) >> 2;
+    const uint64_t g0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 2;
     unsigned long long loads = 0;
-    for (uint64_t k = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
-        uint32_t slab = __ldcg(&front[k]);
-        for (uint32_t hop = 0; hop < max_hops && slab != kNil; ++hop) {
-            const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
-            ++loads;
-            bool grab = false;
-            if (is_set_key_lane(lane) && w < kTombKey && __ldcg(&dist[w]) == kNil)
-                grab = atomicCAS(&dist[w], kNil, level + 1) == kNil;
-            if (__any_sync(kFull, grab)) {
-                uint2 vi = make_uint2(0, 0);
-                if (grab)
-                    vi = __ldg(&g.vinfo[w]);
-                // exclusive scan of the new vertices' list counts
-                uint32_t incl = vi.y;
+    // the warp's eight groups move together: `wb` is its first group's index
+    for (uint64_t wb = g0 & ~7ull; wb < n; wb += groups) {
+        const uint64_t k = wb + (g0 & 7u);
+        uint32_t slab = k < n ? __ldcg(&front[k]) : kNil;
+        bool active = slab != kNil;
+        const uint32_t u = active ? __ldg(&g.owner[slab]) : 0u; // the list's source, at this level
+        for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+            uint4 lo = make_uint4(kFull, kFull, kFull, kFull), hi = lo;
+            if (active)
+                set_group_load(g, slab, lo, hi);
+            loads += __popc(__ballot_sync(kFull, active && s4 == 0));
+            const uint32_t wv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            uint32_t cur[8];
+            bool key[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                key[q] = active && s4 * 8 + q < kSetKeys && wv[q] < kTombKey;
+                cur[q] = key[q] ? __ldcg(&dist[wv[q]]) : 0u;
+            }
+            uint32_t grab = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (key[q] && cur[q] == kNil && atomicCAS(&dist[wv[q]], kNil, level + 1) == kNil)
+                    grab |= 1u << q;
+            // every edge into a vertex of the next level is tight: the
+            // smallest such source is the parent (dist only moves from
+            // unreached to level + 1 during this launch, so a destination
+            // read as unreached is at level + 1 now, whoever took it)
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (key[q] && (cur[q] == kNil || cur[q] == level + 1))
+                    atomicMin(&parent[wv[q]], u);
+            const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
+            if (__any_sync(kFull, grab != 0)) {
+                uint2 vi[8];
+                uint32_t c = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    vi[q] = (grab >> q) & 1u ? __ldg(&g.vinfo[wv[q]]) : make_uint2(0, 0);
+                    c += vi[q].y;
+                }
+                // exclusive scan of the lanes' list counts, one reservation
+                uint32_t incl = c;
+#pragma unroll
                 for (uint32_t o = 1; o < 32; o <<= 1) {
                     const uint32_t t = __shfl_up_sync(kFull, incl, o);
                     if (lane >= o)
                         incl += t;
                 }
                 const uint32_t total = __shfl_sync(kFull, incl, 31);
-                uint32_t base = 0;
+                uint32_t wbase = 0;
                 if (lane == 0)
-                    base = atomicAdd(next_count, total);
-                base = __shfl_sync(kFull, base, 0) + incl - vi.y;
-                if (vi.y <= 8) {
-                    for (uint32_t b = 0; b < vi.y; ++b)
-                        next[base + b] = vi.x + b;
+                    wbase = atomicAdd(next_count, total);
+                uint32_t off[8];
+                uint32_t o = __shfl_sync(kFull, wbase, 0) + incl - c;
+                bool big = false;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    off[q] = o;
+                    if (vi[q].y <= 8) {
+                        for (uint32_t b = 0; b < vi[q].y; ++b)
+                            next[o + b] = vi[q].x + b;
+                    } else {
+                        big = true;
+                    }
+                    o += vi[q].y;
                 }
-                uint32_t big = __ballot_sync(kFull, vi.y > 8);
-                while (big) {
-                    const uint32_t j = __ffs(big) - 1;
-                    big &= big - 1;
-                    const uint32_t bj = __shfl_sync(kFull, base, j), fj = __shfl_sync(kFull, vi.x, j),
-                                   nj = __shfl_sync(kFull, vi.y, j);
-                    for (uint32_t b = lane; b < nj; b += 32)
-                        next[bj + b] = fj + b;
+                // vertices with many lists: written by the whole warp
+                uint32_t bigs = __ballot_sync(kFull, big);
+                while (bigs) {
+                    const uint32_t j = __ffs(bigs) - 1;
+                    bigs &= bigs - 1;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint32_t nj = __shfl_sync(kFull, vi[q].y, j);
+                        const uint32_t fj = __shfl_sync(kFull, vi[q].x, j);
+                        const uint32_t oj = __shfl_sync(kFull, off[q], j);
+                        if (nj > 8)
+                            for (uint32_t b = lane; b < nj; b += 32)
+                                next[oj + b] = fj + b;
+                    }
                 }
             }
-            slab = __shfl_sync(kFull, w, kNextLane);
+            if (active) {
+                if (nxt == kNil || hop + 1 >= max_hops)
+                    active = false;
+                else
+                    slab = nxt;
+            }
         }
     }
     count_add(g.st, kCtrRelaxSlabs, loads);
-}
-
-// BFS parents: the smallest u with a live edge u -> v and dist[u] + 1 ==
-// dist[v] (one warp per slab in use, the owner is u).
-__global__ void __launch_bounds__(256) k_set_bfs_parent(GView g, const uint32_t *__restrict__ dist,
-                                                        uint32_t *parent, uint32_t source)
-{
-    const uint32_t lane = lane_id();
-    const uint64_t total = (uint64_t)g.H + g.P;
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t s = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; s < total; s += warps) {
-        const uint32_t u = __ldg(&g.owner[s]);
-        if (u == kNil)
-            continue;
-        const uint32_t du = __ldg(&dist[u]);
-        if (du == kNil)
-            continue;
-        const uint32_t w = __ldcg(slab_ptr(g, (uint32_t)s) + lane);
-        if (is_set_key_lane(lane) && w < kTombKey && w != source && __ldg(&dist[w]) == du + 1)
-            atomicMin(&parent[w], u);
-    }
 }
 
 // dist / parent start values; the first frontier is the source's lists.
@@ -839,8 +871,8 @@ mk_status mk_set_bfs(mk_set_graph *g, uint32_t source, uint32_t *d_dist, uint32_
             break;
         }
         for (uint32_t i = 0; i < kGroup; ++i, ++level)
-            k_set_bfs_level<<<grid, 256, 0, s>>>(g->v, front[level & 1], front[(level + 1) & 1], cnt, d_dist, level,
-                                                 g->v.P + 2);
+            k_set_bfs_level<<<grid, 256, 0, s>>>(g->v, front[level & 1], front[(level + 1) & 1], cnt, d_dist,
+                                                 d_parent, level, g->v.P + 2);
         if (cudaMemcpyAsync(g->h_pinned, cnt + level % 3, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = MK_ERR_CUDA;
@@ -848,12 +880,6 @@ mk_status mk_set_bfs(mk_set_graph *g, uint32_t source, uint32_t *d_dist, uint32_
         }
         if (g->h_pinned[0] == 0)
             break;
-    }
-    if (st == MK_OK) {
-        k_set_bfs_parent<<<set_grid(((uint64_t)g->v.H + g->v.P + 31) / 32), 256, 0, s>>>(g->v, d_dist, d_parent,
-                                                                                     source);
-        if (cudaGetLastError() != cudaSuccess)
-            st = MK_ERR_CUDA;
     }
     cudaFreeAsync(front[0], s);
     cudaFreeAsync(front[1], s);
