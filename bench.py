@@ -1263,21 +1263,15 @@ def run_served(args):
     return res
 
 
-def run_road(args):
-    """Road-like workload: 4,096 x 4,096 grid + 0.1% long-range edges, 64
-    mixed batches of 2^16 (half deletes of grid links, half inserts), the
-    incremental SSSP from the corner vertex after each batch."""
+def road_pass(R, batches, delta_static, delta_incremental):
+    """One pass of the road workload on a fresh graph: the static SSSP from
+    vertex 0, then each mixed batch and the incremental SSSP after it."""
     import torch
 
     import paper_2305_17813_gb300 as mk
-    import synth
 
-    torch.cuda.set_device(0)
-    t0 = time.time()
-    R = synth.road_graph(4096, 4096)
-    batches = [synth.road_batch(R, k) for k in range(64)]
-    gen_s = time.time() - t0
-    g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + 64 * (1 << 16), buckets=1)
+    g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + len(batches) * (1 << 16), buckets=1)
+    g.set_sssp_delta(delta_static, delta_incremental)
     chunk = 1 << 22
     for i in range(0, len(R.src), chunk):
         g.insert(R.src[i:i + chunk], R.dst[i:i + chunk], R.w[i:i + chunk], flags=False)
@@ -1285,21 +1279,21 @@ def run_road(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     torch.cuda.synchronize()
     ev[0].record()
-    g.sssp(0)
+    d0, p0 = g.sssp(0)
     ev[1].record()
     torch.cuda.synchronize()
     static_ms = ev[0].elapsed_time(ev[1])
     g.commit()
     dev = [{k: mk.to_device_u32(b[k]) for k in ("ins_src", "ins_dst", "ins_w", "del_src", "del_dst")} for b in batches]
     sssp_ms, del_ms, ins_ms = [], [], []
-    for k in range(64):
+    for k in range(len(batches)):
         b = dev[k]
         ev[0].record()
         g.delete(b["del_src"], b["del_dst"], flags=False)
         ev[1].record()
         g.insert(b["ins_src"], b["ins_dst"], b["ins_w"], flags=False)
         ev[2].record()
-        g.sssp(0)
+        d, p = g.sssp(0)
         ev[3].record()
         g.commit()
         torch.cuda.synchronize()
@@ -1308,18 +1302,43 @@ def run_road(args):
         sssp_ms.append(ev[2].elapsed_time(ev[3]))
     if g.last_error() != mk.MK_OK:
         raise RuntimeError("device status in the road run")
-    nd, ni = len(batches[0]["del_src"]), len(batches[0]["ins_src"])
+    result = (mk.to_numpy_u32(d0), mk.to_numpy_u32(p0), mk.to_numpy_u32(d), mk.to_numpy_u32(p))
     g.close()
-    return {"workload": "4,096 x 4,096 road-like grid (67,092,480 grid edges + 67,092 long-range edges, weights "
-                        "U[1,1000]); 64 mixed batches of 2^16 (2^15 deletes of grid links, 2^15 inserts); "
-                        "incremental SSSP from vertex 0 after each batch",
-            "static_sssp_ms": round(static_ms, 2),
+    nd, ni = len(batches[0]["del_src"]), len(batches[0]["ins_src"])
+    return {"static_sssp_ms": round(static_ms, 2),
             "incr_sssp_ms_mean": round(statistics.mean(sssp_ms), 3),
             "incr_sssp_ms_p50": round(statistics.median(sssp_ms), 3),
             "incr_sssp_ms_max": round(max(sssp_ms), 3),
             "delete_medges_s": round(nd / statistics.mean(del_ms) / 1e3, 1),
-            "insert_medges_s": round(ni / statistics.mean(ins_ms) / 1e3, 1),
-            "gen_s": round(gen_s, 1)}
+            "insert_medges_s": round(ni / statistics.mean(ins_ms) / 1e3, 1)}, result
+
+
+def run_road(args):
+    """Road-like workload: 4,096 x 4,096 grid + 0.1% long-range edges, 64
+    mixed batches of 2^16 (half deletes of grid links, half inserts), the
+    incremental SSSP from the corner vertex after each batch; run with the
+    plain frontier rounds, with Near-Far ordered rounds (bucket width 4,000,
+    about eight mean weights) for the static call only, and for every call,
+    results compared."""
+    import torch
+
+    import synth
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    R = synth.road_graph(4096, 4096)
+    batches = [synth.road_batch(R, k) for k in range(64)]
+    gen_s = time.time() - t0
+    plain, r0 = road_pass(R, batches, 0, 0)
+    nf_static, r1 = road_pass(R, batches, 4000, 0)
+    nf, r2 = road_pass(R, batches, 4000, 4000)
+    if not all(np.array_equal(x, y) and np.array_equal(x, z) for x, y, z in zip(r0, r1, r2)):
+        raise RuntimeError("the Near-Far rounds disagree with the plain rounds")
+    return {"workload": "4,096 x 4,096 road-like grid (67,092,480 grid edges + 67,092 long-range edges, weights "
+                        "U[1,1000]); 64 mixed batches of 2^16 (2^15 deletes of grid links, 2^15 inserts); "
+                        "incremental SSSP from vertex 0 after each batch",
+            **plain, "near_far_4000_static": nf_static, "near_far_4000_static_and_incremental": nf,
+            "results_equal": True, "gen_s": round(gen_s, 1)}
 
 
 def run_growth(args):

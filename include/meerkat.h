@@ -346,6 +346,26 @@ mk_status mk_incr_sssp(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t 
  * read as 1); distances are hop counts.  Separate state from mk_incr_sssp. */
 mk_status mk_incr_bfs(mk_graph *g, uint32_t source, uint32_t *d_dist, uint32_t *d_parent, void *stream);
 
+/* Near-Far ordering of the SSSP rounds (an addition to the paper, whose
+ * rounds relax every improved vertex's lists at once): with delta > 0, an
+ * improvement to a distance at or above the current split distance T puts
+ * the vertex on a far pile instead of the next frontier; whenever the
+ * frontier holds fewer than 2,048 lists the pile is split at
+ * max(T, smallest distance pushed) + delta (the width doubling for each
+ * split in a row), the vertices below it joining the frontier.  T starts
+ * delta above the smallest source distance of the call's first frontier.  Results are
+ * those of the plain rounds (the same fixpoint: shortest distances, smallest
+ * tight parents); on graphs of large diameter and weight range fewer
+ * vertices are improved more than once.  delta_static applies to the calls
+ * that compute from scratch (the first for a source, or after an error),
+ * delta_incremental to the others: an incremental call's improvements are
+ * spread over the whole distance range, so ordering them costs more splits
+ * and can be slower than the plain rounds.  Applies to later mk_incr_sssp
+ * calls of this graph (not to BFS, the several-state call or the host-driven
+ * fallback); 0 (the default) keeps the plain rounds.  Each SSSP state then
+ * holds 12 more bytes per vertex, allocated at its next ordered call. */
+mk_status mk_set_sssp_delta(mk_graph *g, uint32_t delta_static, uint32_t delta_incremental);
+
 /* Several BFS/SSSP states of one graph advanced by one call (a service of
  * this library; the paper runs one algorithm per call).  Results are those
  * of one mk_incr_sssp / mk_incr_bfs call per request, but the passes over

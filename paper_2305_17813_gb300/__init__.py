@@ -154,6 +154,11 @@ class Graph:
         check(self._lib.mk_incr_sssp(self._h, int(source), _ptr(dist), _ptr(par), _stream(stream)), "mk_incr_sssp")
         return dist, par
 
+    def set_sssp_delta(self, delta_static: int, delta_incremental: int = 0):
+        """Near-Far bucket widths of the SSSP rounds for static and for
+        incremental calls (0 = the plain rounds)."""
+        check(self._lib.mk_set_sssp_delta(self._h, int(delta_static), int(delta_incremental)), "mk_set_sssp_delta")
+
     def bfs(self, source: int, stream=None):
         torch = _torch()
         dist = torch.empty(self.V, dtype=torch.int32, device=self.device)

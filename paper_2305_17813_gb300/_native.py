@@ -155,6 +155,7 @@ SIGNATURES = {
     "mk_set_wcc": (_INT, [_P, _P, _P]),
     "mk_set_stats": (_INT, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64), _P]),
     "mk_set_last_error": (_INT, [_P]),
+    "mk_set_sssp_delta": (_INT, [_P, _U32, _U32]),
     "mk_pagerank": (_INT, [_P, _P, _INT, ctypes.c_float, ctypes.c_float, _U32, ctypes.POINTER(_U32),
                            ctypes.POINTER(ctypes.c_float), _P]),
     "mk_tc_count": (_INT, [_P, _P, _P, _P, _U64, _P, _P]),

@@ -336,6 +336,9 @@ static void destroy_consumer(mk_graph *g, Consumer *c)
     device_free(g, c->stamp, V * 4);
     device_free(g, c->inv, (V + 31) / 32 * 4);
     device_free(g, c->uf, V * 4);
+    device_free(g, c->far[0], V * 4);
+    device_free(g, c->far[1], V * 4);
+    device_free(g, c->fstamp, V * 4);
     device_free(g, c->counters, 64);
     delete c;
 }
@@ -673,6 +676,15 @@ mk_status mk_debug_set(mk_graph *g, int knob, uint64_t value)
     default:
         return MK_ERR_INVALID_ARG;
     }
+}
+
+mk_status mk_set_sssp_delta(mk_graph *g, uint32_t delta_static, uint32_t delta_incremental)
+{
+    if (!g)
+        return MK_ERR_INVALID_ARG;
+    g->sssp_delta_static = delta_static;
+    g->sssp_delta_incr = delta_incremental;
+    return MK_OK;
 }
 
 mk_status mk_list_marker(mk_graph *g, uint32_t v, uint32_t bucket, uint32_t *slab, uint32_t *lane,

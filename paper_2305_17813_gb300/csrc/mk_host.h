@@ -28,6 +28,8 @@ struct Consumer {
     uint32_t *inv = nullptr;    // BFS/SSSP: bitmap of vertices invalidated by this call's deletes
     uint32_t round = 0;         // last stamp value used
     uint32_t *uf = nullptr;     // WCC: union-find parents (V)
+    uint32_t *far[2] = {nullptr, nullptr}; // SSSP with Near-Far ordering: far piles (V each)
+    uint32_t *fstamp = nullptr; // SSSP with Near-Far ordering: pile stamp per vertex (V)
     uint32_t *counters = nullptr; // device: frontier sizes etc. (16 words)
 };
 
@@ -94,6 +96,9 @@ struct mk_graph {
     // cooperative kernel
     uint64_t dbg_barrier_spins = ~0ull;
     bool dbg_host_rounds = false;
+    // Near-Far bucket widths of the SSSP rounds, static and incremental
+    // calls (mk_set_sssp_delta; 0 = off)
+    uint32_t sssp_delta_static = 0, sssp_delta_incr = 0;
     // profiling
     bool prof = false;
     std::vector<mk::TimedLaunch> timed;

@@ -48,7 +48,11 @@ enum {
     kClearWords = 8,  // words [0, 8) are cleared at the start of every call
     kSoloR = 6,       // round index reached by a solo phase of block 0
     kRid = 8,         // last round stamp used (kept across calls)
-    kBar = 10         // grid barrier: arrivals of the launch so far
+    kPhase = 9,       // Near-Far: last far-pile phase stamp used (kept across calls)
+    kBar = 10,        // grid barrier: arrivals of the launch so far
+    kFarCnt0 = 11,    // Near-Far ordering: sizes of the two far piles (11, 12),
+    kFarMin0 = 13,    // the smallest distance pushed to each (13, 14)
+    kThresh = 15      // and the smallest source distance of the first frontier
 };
 // A frontier of at most kSoloLists lists is processed by block 0 alone, with
 // block-level barriers between rounds, for at most kSoloRounds rounds in a
@@ -58,6 +62,10 @@ enum {
 // a grid barrier plus one chain; a larger one is faster on the whole grid.
 constexpr uint32_t kSoloLists = 192;
 constexpr uint32_t kSoloRounds = 4096;
+// Near-Far ordering: the far pile is split into the frontier whenever the
+// frontier holds fewer lists than this (a smaller frontier costs a round
+// about as much as a larger one).
+constexpr uint32_t kNearMin = 2048;
 
 __device__ __forceinline__ uint32_t node_dist(unsigned long long d) { return (uint32_t)(d >> 32); }
 __device__ __forceinline__ uint32_t node_parent(unsigned long long d) { return (uint32_t)d; }
@@ -83,9 +91,51 @@ struct RoundArgs {
     int unit;
     uint32_t *dist;       // the caller's outputs (nullable), written when the phase ends
     uint32_t *parent;
+    uint32_t delta;       // Near-Far bucket width (0: plain frontier rounds)
+    uint32_t *far[2];     // Near-Far: the two far piles (V vertices each)
+    uint32_t *fstamp;     // Near-Far: phase in which a vertex last joined a pile
 };
 
 namespace {
+
+// Near-Far ordering of the rounds (an addition to the paper's frontier
+// rounds, for graphs of large diameter and weight range): an improvement
+// to a distance at or above the split distance T does not enqueue the
+// vertex's lists; the vertex joins the far pile instead (once per phase,
+// through its pile stamp), and whenever the frontier is small the pile is
+// split at a larger T.  Only the order of the relaxations changes: the rounds
+// still run until no distance improves, so the result is the same fixpoint.
+struct NearFar {
+    uint32_t T = kInf32;      // split distance of this phase
+    uint32_t phase = 0;       // pile stamp of this phase
+    uint32_t *pile = nullptr; // the pile this phase appends to
+    uint32_t *count = nullptr;
+    uint32_t *dmin = nullptr; // smallest distance pushed to it
+};
+
+// Appends y (lanes with pred) to the far pile once per phase.  Must be
+// called by the full warp.
+__device__ __forceinline__ void far_push(const RoundArgs &a, const NearFar &nf, uint32_t y, bool pred, uint32_t d)
+{
+    const bool take = pred && atomicExch(&a.fstamp[y], nf.phase) != nf.phase;
+    const uint32_t m = __ballot_sync(kFull, take);
+    if (!m)
+        return;
+    const uint32_t dm = __reduce_min_sync(kFull, take ? d : kInf32);
+    uint32_t base = 0;
+    if (lane_id() == 0) {
+        base = atomicAdd(nf.count, (uint32_t)__popc(m));
+        atomicMin(nf.dmin, dm);
+    }
+    base = __shfl_sync(kFull, base, 0);
+    if (take) {
+        const uint32_t at = base + __popc(m & lanemask_lt());
+        if (at < a.g.V)
+            nf.pile[at] = y;
+        else
+            *(int *)(a.ctr + kOverflow) = 1;
+    }
+}
 
 // Relaxes the lane's four edges (x, y[k], w[k]) with live[k] and enqueues
 // the lists of each vertex whose distance this lane lowered first in this
@@ -95,10 +145,12 @@ namespace {
 // then the improved targets' vinfo entries are read and their round stamps
 // exchanged, so a slab costs three memory round trips per lane instead of
 // three per edge.  Must be called by the full warp.
+template <bool kNF = false>
 __device__ __forceinline__ void relax_edges4(const RoundArgs &a, uint32_t x, uint32_t dx, const uint32_t (&y)[4],
                                              const uint32_t (&w)[4], const bool (&live)[4], uint32_t round,
                                              BlockFrontier &bq, uint2 *Fn, uint32_t *cnt, int *overflow,
-                                             unsigned long long &edges, unsigned long long &improved)
+                                             unsigned long long &edges, unsigned long long &improved,
+                                             const NearFar *nf = nullptr)
 {
     // candidate of edge k: <nd[k], x>
     auto cand = [&](uint32_t d) { return ((unsigned long long)d << 32) | x; };
@@ -121,11 +173,22 @@ __device__ __forceinline__ void relax_edges4(const RoundArgs &a, uint32_t x, uin
             cur[k] = atomicMin(&a.D[y[k]], cand(nd[k]));
         else
             up[k] = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        up[k] = up[k] && cand(nd[k]) < cur[k];
+    if (kNF) {
+        // improvements at or beyond the split distance wait in the far pile
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool fp = up[k] && nd[k] >= nf->T;
+            up[k] = up[k] && !fp;
+            far_push(a, *nf, y[k], fp, nd[k]);
+        }
+    }
     uint2 vi[4];
     uint32_t st[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        up[k] = up[k] && cand(nd[k]) < cur[k];
         vi[k] = make_uint2(0, 0);
         st[k] = round;
         if (up[k]) {
@@ -146,8 +209,10 @@ __device__ __forceinline__ void relax_edges4(const RoundArgs &a, uint32_t x, uin
 // warp in flight), so a round's lists are spread over all warps; each
 // group's entry, source distance and head slab are loaded one step ahead
 // (the entry two steps ahead) while the current list is relaxed.
+template <bool kNF = false>
 __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2 *Fn, uint32_t *cnt,
-                           uint32_t round, uint64_t warp0, uint64_t nwarps, BlockFrontier &bq)
+                           uint32_t round, uint64_t warp0, uint64_t nwarps, BlockFrontier &bq,
+                           const NearFar *nf = nullptr)
 {
     const GView &g = a.g;
     const uint32_t s4 = lane_id() & 3u, g4 = lane_id() >> 2;
@@ -173,8 +238,8 @@ __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2
         const uint32_t x = e.y, d = dx;
         slabs += walk_lists_g4_from(g, L, true, lo, hi, 0, a.max_hops,
                                     [&](const uint32_t(&y)[4], const uint32_t(&w)[4], const bool(&live)[4]) {
-                                        relax_edges4(a, x, d, y, w, live, round, bq, Fn, cnt, overflow, edges,
-                                                     improved);
+                                        relax_edges4<kNF>(a, x, d, y, w, live, round, bq, Fn, cnt, overflow,
+                                                          edges, improved, nf);
                                     });
         e = ne;
         ne = nne;
@@ -193,14 +258,16 @@ __device__ void relax_body(const RoundArgs &a, const uint2 *F, uint32_t n, uint2
 // global counters, or block 0's shared copies during a solo phase).
 // Frontier r is front[r & 1].  Called by whole blocks: the block's staged
 // entries are flushed at the end.
+template <bool kNF = false>
 __device__ __forceinline__ void round_step(const RoundArgs &a, uint32_t *cnts, uint32_t r, uint32_t n, uint64_t warp0,
-                                           uint64_t nwarps, uint32_t rid, BlockFrontier &bq)
+                                           uint64_t nwarps, uint32_t rid, BlockFrontier &bq,
+                                           const NearFar *nf = nullptr)
 {
     const uint32_t in = r & 1;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         cnts[(r + 2) % 3] = 0;
     uint32_t *cnt = cnts + (r + 1) % 3;
-    relax_body(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps, bq);
+    relax_body<kNF>(a, a.front[in], n, a.front[in ^ 1], cnt, rid + 2 + r, warp0, nwarps, bq, nf);
     bq_flush(bq, a.front[in ^ 1], cnt, a.cap, (int *)(a.ctr + kOverflow));
 }
 
@@ -234,6 +301,41 @@ __device__ bool grid_barrier(uint32_t *bar, uint32_t &passed, uint32_t max_spins
     return ok_s != 0;
 }
 
+// Splits the far pile pile[0, fc) at T2 before round r: a vertex whose
+// distance is now below T2 has its lists appended to frontier r (under the
+// stamp of the entries already there, rid + 1 + r, so a vertex queued
+// there already is not queued twice), every other one moves to the pile of
+// `next` under its phase stamp.  Called by every thread of every block.
+__device__ __forceinline__ void far_split(const RoundArgs &a, const uint32_t *pile, uint32_t fc, const NearFar &next,
+                                          uint32_t T2, uint32_t r, uint32_t rid, uint64_t warp0, uint64_t nwarps,
+                                          BlockFrontier &bq)
+{
+    uint2 *out = a.front[r & 1];
+    uint32_t *cnt = a.ctr + kCnt0 + r % 3;
+    const uint32_t stampv = rid + 1 + r;
+    int *overflow = (int *)(a.ctr + kOverflow);
+    for (uint64_t wb = warp0 * 32; wb < fc; wb += nwarps * 32) {
+        const uint64_t i = wb + lane_id();
+        const bool valid = i < fc;
+        uint32_t y = 0, dy = kInf32;
+        if (valid) {
+            y = __ldcg(&pile[i]);
+            dy = node_dist(__ldcg(&a.D[y]));
+        }
+        bool near = valid && dy < T2;
+        uint2 vi = make_uint2(0, 0);
+        uint32_t st = stampv;
+        if (near) {
+            vi = a.g.vinfo[y];
+            st = atomicExch(&a.stamp[y], stampv);
+        }
+        near = near && st != stampv;
+        enqueue_lists_block(bq, y, near, vi, out, cnt, a.cap, overflow);
+        far_push(a, next, y, valid && dy >= T2, dy);
+    }
+    bq_flush(bq, out, cnt, a.cap, overflow);
+}
+
 } // namespace
 
 // All rounds of one phase in one cooperative launch.  The phase input is
@@ -245,6 +347,7 @@ __device__ bool grid_barrier(uint32_t *bar, uint32_t &passed, uint32_t max_spins
 // phase sits between two grid barriers, so no block reads a global size
 // while block 0 changes them, and the others wait at one barrier instead of
 // one per round.
+template <bool kNF>
 __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
 {
     __shared__ uint32_t solo_cnt[3];
@@ -256,20 +359,88 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
     uint32_t *gcnt = a.ctr + kCnt0;
     uint32_t r = 0, bars = 0, passed = 0;
     bool ok = true;
-    __shared__ uint32_t s_word;
-    while (r < a.max_rounds) {
+    __shared__ uint32_t s_word, s_fc, s_fm;
+    // Near-Far: the first split distance is delta above the smallest source
+    // distance of the first frontier (ctr[kThresh] starts at INF)
+    NearFar nf;
+    uint32_t cur = 0, splits = 0, burst = 0;
+    const uint32_t phase0 = kNF ? __ldg(a.ctr + kPhase) + 1 : 0;
+    if (kNF) {
+        const uint32_t n0 = min(ld_volatile(gcnt), a.cap);
+        uint32_t m = kInf32;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n0;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            m = min(m, node_dist(__ldcg(&a.D[__ldcg(&a.front[0][i].y)])));
+        m = __reduce_min_sync(kFull, m);
+        if ((threadIdx.x & 31) == 0 && m != kInf32)
+            atomicMin(a.ctr + kThresh, m);
+        ++bars;
+        ok = grid_barrier(a.ctr + kBar, passed, a.barrier_spins);
+        const uint32_t t0 = ld_volatile(a.ctr + kThresh);
+        nf.T = t0 >= kInf32 - a.delta ? kInf32 : t0 + a.delta;
+        nf.phase = phase0;
+        nf.pile = a.far[0];
+        nf.count = a.ctr + kFarCnt0;
+        nf.dmin = a.ctr + kFarMin0;
+    }
+    while (ok && r < a.max_rounds) {
         // one read of the frontier size per block (the grid's warps would
         // otherwise all read the same word)
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_word = ld_volatile(gcnt + r % 3);
+            if (kNF) {
+                s_fc = ld_volatile(a.ctr + kFarCnt0 + cur);
+                s_fm = ld_volatile(a.ctr + kFarMin0 + cur);
+            }
+        }
         __syncthreads();
         // a frontier never holds more than `cap` entries; a larger count
         // (entries dropped on overflow, reported below) is read as cap
         uint32_t n = min(s_word, a.cap);
+        if (kNF && n < kNearMin && s_fc != 0) {
+            // the near frontier is small: move the far pile's vertices below
+            // the next split distance into it, once every block has read
+            // the sizes above; the distance grows with each split in a row
+            const uint32_t fc = min(s_fc, a.g.V), fm = s_fm;
+            ++bars;
+            if (!grid_barrier(a.ctr + kBar, passed, a.barrier_spins)) {
+                ok = false;
+                break;
+            }
+            const uint32_t base = max(nf.T, fm);
+            const uint64_t width = (uint64_t)a.delta << min(burst, 16u);
+            NearFar next;
+            next.T = (uint64_t)base + width >= kInf32 ? kInf32 : (uint32_t)(base + width);
+            next.phase = phase0 + ++splits;
+            next.pile = a.far[cur ^ 1];
+            next.count = a.ctr + kFarCnt0 + (cur ^ 1);
+            next.dmin = a.ctr + kFarMin0 + (cur ^ 1);
+            far_split(a, nf.pile, fc, next, next.T, r, rid, warp0, nwarps, bq);
+            ++bars;
+            if (!grid_barrier(a.ctr + kBar, passed, a.barrier_spins)) {
+                ok = false;
+                break;
+            }
+            // the old pile is empty again; no block reads its words before
+            // the next split, two grid barriers on
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.ctr[kFarCnt0 + cur] = 0;
+                a.ctr[kFarMin0 + cur] = kInf32;
+            }
+            cur ^= 1;
+            nf = next;
+            ++burst;
+            if (splits > a.max_rounds) {
+                ok = false;
+                break;
+            }
+            continue;
+        }
+        burst = 0;
         if (n == 0)
             break;
         if (n > kSoloLists) {
-            round_step(a, gcnt, r, n, warp0, nwarps, rid, bq);
+            round_step<kNF>(a, gcnt, r, n, warp0, nwarps, rid, bq, &nf);
             ++bars;
             if (!grid_barrier(a.ctr + kBar, passed, a.barrier_spins)) {
                 ok = false;
@@ -294,7 +465,7 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
             __syncthreads();
             uint32_t steps = 0;
             do {
-                round_step(a, solo_cnt, r, n, bw0, bnw, rid, bq);
+                round_step<kNF>(a, solo_cnt, r, n, bw0, bnw, rid, bq, &nf);
                 __syncthreads();
                 ++r;
                 ++steps;
@@ -336,6 +507,8 @@ __global__ void __launch_bounds__(kRoundsMaxThreads, 1) k_rounds(RoundArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr[kRoundsDone] = r;
         a.ctr[kRid] += r + 2;
+        if (kNF)
+            a.ctr[kPhase] = phase0 + splits;
         atomicAdd(&a.g.st->ctr[kCtrRounds][0], (unsigned long long)r);
         atomicAdd(&a.g.st->ctr[kCtrGridBarriers][0], (unsigned long long)bars);
         if (a.dist || a.parent)
@@ -1074,7 +1247,7 @@ int rounds_max_blocks_per_sm()
 {
     static int per = 0;
     if (!per) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds<false>, 256, 0);
         per = std::min(std::max(per, 1), (int)(kRoundsMaxThreads / 256));
     }
     return per;
@@ -1102,7 +1275,8 @@ mk_status run_phase(mk_graph *g, RoundArgs a, const char *name, cudaStream_t s)
     void *args[] = {&a};
     if (!g->dbg_host_rounds) {
         const mk_status st = timed(g, name, s, 1, [&]() {
-            return cudaLaunchCooperativeKernel((const void *)k_rounds, dim3(grid), dim3(block), args, 0, s);
+            const void *k = a.delta ? (const void *)k_rounds<true> : (const void *)k_rounds<false>;
+            return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), args, 0, s);
         });
         if (st == MK_OK)
             return MK_OK;
@@ -1154,8 +1328,35 @@ mk_status run_sssp(mk_graph *g, int kind, uint32_t source, uint32_t *d_dist, uin
     a.dist = d_dist;
     a.parent = d_parent;
     const bool incremental = c->epoch == g->epoch;
+    // Near-Far ordering for SSSP when a bucket width is set for this kind of
+    // call (the host-driven fallback runs plain rounds)
+    a.delta = kind == kSssp && !g->dbg_host_rounds ? (incremental ? g->sssp_delta_incr : g->sssp_delta_static) : 0;
+    if (a.delta && !c->fstamp) {
+        mk_status st = device_alloc(g, (void **)&c->far[0], (size_t)V * 4);
+        if (st == MK_OK)
+            st = device_alloc(g, (void **)&c->far[1], (size_t)V * 4);
+        if (st == MK_OK)
+            st = device_alloc(g, (void **)&c->fstamp, (size_t)V * 4);
+        if (st == MK_OK && cudaMemsetAsync(c->fstamp, 0, (size_t)V * 4, s) != cudaSuccess)
+            st = MK_ERR_CUDA;
+        if (st != MK_OK) {
+            device_free(g, c->far[0], (size_t)V * 4);
+            device_free(g, c->far[1], (size_t)V * 4);
+            device_free(g, c->fstamp, (size_t)V * 4);
+            c->far[0] = c->far[1] = c->fstamp = nullptr;
+            return st;
+        }
+    }
+    a.far[0] = c->far[0];
+    a.far[1] = c->far[1];
+    a.fstamp = c->fstamp;
     MK_CUDA(cudaMemsetAsync(c->counters, 0, kClearWords * 4, s));
     MK_CUDA(cudaMemsetAsync(c->counters + kBar, 0, 4, s));
+    if (a.delta) {
+        // empty far piles, their minima and the first frontier's minimum at INF
+        MK_CUDA(cudaMemsetAsync(c->counters + kFarCnt0, 0, 8, s));
+        MK_CUDA(cudaMemsetAsync(c->counters + kFarMin0, 0xFF, 12, s));
+    }
     if (!incremental) {
         MK_TRY(timed(g, "sssp_init", s, 1, [&]() {
             k_sssp_init<<<grid_for(V, 256), 256, 0, s>>>(c->D, V, source, c->front[0], c->counters + kCnt0,

@@ -63,6 +63,7 @@ def test_host_side_argument_errors_need_no_device(lib):
     assert L.mk_tc_update(None, None, None, None, 0, 0, None, None) == mk.MK_ERR_INVALID_ARG
     assert L.mk_l2_window(None, mk.MK_L2_VINFO, None, None) == mk.MK_ERR_INVALID_ARG
     assert L.mk_debug_set(None, 1, 0) == mk.MK_ERR_INVALID_ARG
+    assert L.mk_set_sssp_delta(None, 0, 0) == mk.MK_ERR_INVALID_ARG
     # the set layout's entry points
     assert L.mk_set_create(0, 0, 1, None, None, ctypes.byref(out)) == mk.MK_ERR_INVALID_ARG
     assert L.mk_set_create(0xFFFFFFFE, 0, 1, None, None, ctypes.byref(out)) == mk.MK_ERR_INVALID_ARG

@@ -182,3 +182,39 @@ def test_long_path_and_mixed_frontier_sizes(cuda_lib):
     for x in (g, o):
         x.insert([P // 2], [P // 2 + 1], [3])
     check_algos(g, o, [0], wcc=True)
+
+
+@pytest.mark.parametrize("delta", [7, 300])
+def test_near_far_sssp_power_law_stream(cuda_lib, delta):
+    """Near-Far ordered SSSP on R-MAT batches of inserts and deletes of live
+    edges: the tree equals the oracle's after every batch, BFS (never
+    ordered) too, and switching the ordering off mid-stream keeps it."""
+    mk = _mk()
+    G = synth.powerlaw_graph(scale=13, draws=1 << 17)
+    S = synth.PowerlawStream(G, max_batch=1 << 12)
+    src = int(np.argmax(np.bincount(G.src, minlength=G.V)))
+    g = mk.Graph(G.V, edge_capacity_hint=len(G.src) + (1 << 16), buckets=mk.bucket_rule(G.V, G.src, 0.7))
+    g.set_sssp_delta(delta, delta)
+    o = oracle.OracleGraph(G.V)
+    g.insert(G.src, G.dst, G.w, flags=False)
+    o.insert(G.src, G.dst, G.w)
+    g.commit()
+    for k in range(6):
+        if k == 4:
+            g.set_sssp_delta(0, 0)
+        b = S.batch(1 << 12)
+        g.insert(b.ins_src, b.ins_dst, b.ins_w, flags=False)
+        o.insert(b.ins_src, b.ins_dst, b.ins_w)
+        for fn, ofn in ((g.sssp, o.sssp), (g.bfs, o.bfs)):
+            d, p = fn(src)
+            od, op = ofn(src)
+            assert np.array_equal(mk.to_numpy_u32(d), od) and np.array_equal(mk.to_numpy_u32(p), op), k
+        g.commit()
+        g.delete(b.del_src, b.del_dst, flags=False)
+        o.delete(b.del_src, b.del_dst)
+        d, p = g.sssp(src)
+        od, op = o.sssp(src)
+        assert np.array_equal(mk.to_numpy_u32(d), od) and np.array_equal(mk.to_numpy_u32(p), op), k
+        g.commit()
+        assert g.last_error() == mk.MK_OK
+    g.close()

@@ -119,10 +119,11 @@ def test_powerlaw_full_size_all_batch_sizes(cuda_lib):
     g.close()
 
 
-def road_run(rows, cols, batches, full_check_every):
+def road_run(rows, cols, batches, full_check_every, delta=0):
     mk = _mk()
     R = synth.road_graph(rows, cols)
     g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + batches * (1 << 16), buckets=1)
+    g.set_sssp_delta(delta, delta)
     o = oracle.OracleGraph(R.V)
     chunk = 1 << 22
     for i in range(0, len(R.src), chunk):
@@ -162,3 +163,19 @@ def test_road_small_every_batch(cuda_lib):
 
 def test_road_full_size_64_batches(cuda_lib):
     road_run(4096, 4096, 64, full_check_every=0)
+
+
+@pytest.mark.parametrize("delta", [1, 1500, 1 << 31])
+def test_road_small_near_far_every_batch(cuda_lib, delta):
+    """Near-Far ordered SSSP rounds (a bucket width of one weight unit, a
+    few edges' worth, and wider than every distance) give the oracle's tree
+    after every mixed batch."""
+    road_run(256, 256, 12, full_check_every=1, delta=delta)
+
+
+def test_road_near_far_mid_size(cuda_lib):
+    road_run(1024, 1024, 8, full_check_every=4, delta=4000)
+
+
+def test_road_full_size_near_far(cuda_lib):
+    road_run(4096, 4096, 6, full_check_every=0, delta=4000)
