@@ -243,21 +243,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "59f81cbea540d26fc57317f67445bd530bc143395cf4289242ab3afc8f23218e"
+NCU_TRAFFIC_SOURCES_SHA = "e4bfaf9ae99e3fff086d6a9e144dc04b4f79d7fe1a10903f138e0378af0152fa"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49420160,
-    "sssp_relax_into_invalid": 280909056,
-    "sssp_enqueue_invalid": 11006080,
-    "sssp_relax_updated": 26475584,
-    "sssp_invalidate_walk": 8523968,
-    "sssp_invalidate": 13739072,
-    "wcc_hook_all": 350713984,
-    "wcc_hook_updated": 19097344,
-    "insert": 255048448,
-    "delete": 198481024,
-    "query": 130871552,
-    "stage_dedup": 40150976,
-    "update_slab_pointers": 60557760,
+    "sssp_rounds": 49617504,
+    "sssp_relax_into_invalid": 280918784,
+    "sssp_enqueue_invalid": 11005056,
+    "sssp_relax_updated": 26470336,
+    "sssp_invalidate_walk": 8525568,
+    "sssp_invalidate": 13739712,
+    "wcc_hook_all": 350567424,
+    "wcc_hook_updated": 19099392,
+    "insert": 255136256,
+    "delete": 198451328,
+    "query": 130815360,
+    "stage_dedup": 40147392,
+    "update_slab_pointers": 60570560,
 }
 
 
