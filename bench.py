@@ -82,7 +82,14 @@ def parse_args(argv=None):
                         "scale-21 request stream; road: incremental SSSP on the 4096^2 road-like grid; "
                         "analytics: PageRank and triangle counting; buckets: the power-law step with the "
                         "load-factor bucket rule against one bucket per vertex (hashing off); l2: the step "
-                        "with L2 persistence windows over parts of the store (each prints its own JSON line)")
+                        "with L2 persistence windows over parts of the store; set: the map layout against "
+                        "the ConcurrentSet layout (each prints its own JSON line)")
+    p.add_argument("--road-size", type=int, default=4096, help="road workload: grid side")
+    p.add_argument("--road-batches", type=int, default=64, help="road workload: mixed batches")
+    p.add_argument("--road-batch-size", type=int, default=1 << 16, help="road workload: edges a batch")
+    p.add_argument("--road-delta", type=int, default=None,
+                   help="road workload: one pass with this Near-Far width for every call instead of the "
+                        "three passes (plain, ordered static call, ordered every call)")
     return p.parse_args(argv)
 
 
@@ -1270,7 +1277,7 @@ def road_pass(R, batches, delta_static, delta_incremental):
 
     import paper_2305_17813_gb300 as mk
 
-    g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + len(batches) * (1 << 16), buckets=1)
+    g = mk.Graph(R.V, edge_capacity_hint=len(R.src) + sum(len(b["ins_src"]) for b in batches), buckets=1)
     g.set_sssp_delta(delta_static, delta_incremental)
     chunk = 1 << 22
     for i in range(0, len(R.src), chunk):
@@ -1326,17 +1333,22 @@ def run_road(args):
 
     torch.cuda.set_device(0)
     t0 = time.time()
-    R = synth.road_graph(4096, 4096)
-    batches = [synth.road_batch(R, k) for k in range(64)]
+    n, nb = args.road_size, args.road_batches
+    R = synth.road_graph(n, n)
+    batches = [synth.road_batch(R, k, args.road_batch_size) for k in range(nb)]
     gen_s = time.time() - t0
+    desc = ("%d x %d road-like grid (%d grid edges + %d long-range edges, weights U[1,1000]); %d mixed batches "
+            "of %d (half deletes of grid links, half inserts); incremental SSSP from vertex 0 after each batch"
+            % (n, n, R.n_grid, len(R.src) - R.n_grid, nb, args.road_batch_size))
+    if args.road_delta is not None:
+        one, _ = road_pass(R, batches, args.road_delta, args.road_delta)
+        return {"workload": desc, "near_far_width": args.road_delta, **one, "gen_s": round(gen_s, 1)}
     plain, r0 = road_pass(R, batches, 0, 0)
     nf_static, r1 = road_pass(R, batches, 4000, 0)
     nf, r2 = road_pass(R, batches, 4000, 4000)
     if not all(np.array_equal(x, y) and np.array_equal(x, z) for x, y, z in zip(r0, r1, r2)):
         raise RuntimeError("the Near-Far rounds disagree with the plain rounds")
-    return {"workload": "4,096 x 4,096 road-like grid (67,092,480 grid edges + 67,092 long-range edges, weights "
-                        "U[1,1000]); 64 mixed batches of 2^16 (2^15 deletes of grid links, 2^15 inserts); "
-                        "incremental SSSP from vertex 0 after each batch",
+    return {"workload": desc,
             **plain, "near_far_4000_static": nf_static, "near_far_4000_static_and_incremental": nf,
             "results_equal": True, "gen_s": round(gen_s, 1)}
 
