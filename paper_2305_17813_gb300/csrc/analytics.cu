@@ -95,23 +95,43 @@ __global__ void k_pr_contrib(const unsigned long long *pr, const uint32_t *out, 
     warp_add_u64(ctr, dangling);
 }
 
-// Pushes contrib[u] along every live edge u -> v (thread per slab word; a
-// warp reads one slab, the owner once per slab).
+// Pushes contrib[u] along every live edge u -> v.  A warp takes
+// 4 * kPushHalves consecutive slabs a step, four at a time: eight lanes a
+// slab, each lane one 16-byte block (two pairs; the last lane of a slab one
+// pair and the unused and next words); the owners, slab parts and
+// contributions of every group of four are loaded before any atomic, so
+// kPushHalves independent load chains are in flight per lane.
+constexpr int kPushHalves = 2;
+
 __global__ void __launch_bounds__(256) k_pr_push(GView g, const unsigned long long *__restrict__ contrib,
                                                  unsigned long long *acc)
 {
-    const uint64_t total = ((uint64_t)g.H + g.P) * 32;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint32_t lane = lane_id();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
-        const uint32_t own = __ldg(&g.owner[i >> 5]);
-        if (own == kNil)
-            continue;
-        const uint32_t word = __ldcg(&g.slabs[i]);
-        if (is_key_lane(lane) && word < kTombKey) {
-            const unsigned long long c = __ldg(&contrib[own]);
-            if (c)
-                atomicAdd(&acc[word], c);
+    const uint64_t nslab = (uint64_t)g.H + g.P;
+    const uint32_t lane = lane_id(), part = lane & 7u, sub = lane >> 3;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t s0 = warp * (4 * kPushHalves); s0 < nslab; s0 += nwarps * (4 * kPushHalves)) {
+        uint32_t own[kPushHalves];
+        uint4 q[kPushHalves];
+#pragma unroll
+        for (int h = 0; h < kPushHalves; ++h) {
+            const uint64_t s = s0 + h * 4 + sub;
+            own[h] = s < nslab ? __ldg(&g.owner[s]) : kNil;
+            q[h] = s < nslab ? __ldcg(reinterpret_cast<const uint4 *>(slab_ptr(g, (uint32_t)s)) + part)
+                             : make_uint4(kEmptyKey, 0u, kEmptyKey, 0u);
+        }
+        unsigned long long c[kPushHalves];
+#pragma unroll
+        for (int h = 0; h < kPushHalves; ++h)
+            c[h] = own[h] != kNil ? __ldg(&contrib[own[h]]) : 0ull; // an unused pool slab holds stale keys
+#pragma unroll
+        for (int h = 0; h < kPushHalves; ++h) {
+            if (!c[h])
+                continue;
+            if (q[h].x < kTombKey)
+                atomicAdd(&acc[q[h].x], c[h]);
+            if (part != 7u && q[h].z < kTombKey)
+                atomicAdd(&acc[q[h].z], c[h]);
         }
     }
 }
@@ -281,7 +301,9 @@ mk_status mk_pagerank(mk_graph *g, float *d_pr, int warm_start, float damping, f
     const unsigned long long base = (unsigned long long)std::llround((1.0 - d) / (double)V * kFix);
     uint32_t it = 0;
     double delta = 0;
-    const uint32_t push_grid = std::min<uint64_t>(grid_for(words, 256), (uint64_t)resident_grid(k_pr_push, 256) * 4);
+    // 4 * kPushHalves slabs per warp step
+    const uint32_t push_grid = std::min<uint64_t>(grid_for(words / (4 * kPushHalves), 256),
+                                                  (uint64_t)resident_grid(k_pr_push, 256) * 4);
     while (st == MK_OK && it < max_iter) {
         if (cudaMemsetAsync(ctr, 0, 16, s) != cudaSuccess) {
             st = MK_ERR_CUDA;
