@@ -250,21 +250,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "e4bfaf9ae99e3fff086d6a9e144dc04b4f79d7fe1a10903f138e0378af0152fa"
+NCU_TRAFFIC_SOURCES_SHA = "d02a4f6321c9d54c597b9755964afff47edcd4e96482c736aa2e814f184ab515"
 NCU_TRAFFIC = {
-    "sssp_rounds": 49617504,
-    "sssp_relax_into_invalid": 280918784,
-    "sssp_enqueue_invalid": 11005056,
-    "sssp_relax_updated": 26470336,
-    "sssp_invalidate_walk": 8525568,
-    "sssp_invalidate": 13739712,
-    "wcc_hook_all": 350567424,
-    "wcc_hook_updated": 19099392,
-    "insert": 255136256,
-    "delete": 198451328,
-    "query": 130815360,
-    "stage_dedup": 40147392,
-    "update_slab_pointers": 60570560,
+"sssp_rounds": 49629632,
+    "sssp_relax_into_invalid": 280982272,
+    "sssp_enqueue_invalid": 11002624,
+    "sssp_relax_updated": 26473792,
+    "sssp_invalidate_walk": 8524416,
+    "sssp_invalidate": 13739904,
+    "wcc_hook_all": 350453888,
+    "wcc_hook_updated": 19096832,
+    "insert": 255198592,
+    "delete": 198552704,
+    "query": 131030400,
+    "stage_dedup": 40155264,
+    "update_slab_pointers": 60566592,
 }
 
 
