@@ -428,8 +428,11 @@ mk_status mk_pagerank(mk_graph *g, float *d_pr, int warm_start, float damping, f
 mk_status mk_tc_count(mk_graph *g1, mk_graph *g2, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                       unsigned long long *d_total, void *stream);
 
-/* Static count: Count(g, g, every live edge) / 6 into *h_triangles (host).
- * Synchronises `stream`. */
+/* Static count into *h_triangles (host): every triangle once, on its two
+ * lower-ranked vertices' edge, the vertices ranked by (bucket count, id);
+ * equal to Count(g, g, every live edge) / 6 on a graph that meets the
+ * conditions above (which this count does not check).  Synchronises
+ * `stream`. */
 mk_status mk_tc_static(mk_graph *g, uint64_t *h_triangles, void *stream);
 
 /* Change in the triangle count after a batch (paper, Algorithms "Triangle

@@ -249,24 +249,58 @@ __global__ void __launch_bounds__(256) k_tc_count(GView g1, GView g2, const uint
     warp_add_u64(total, count);
 }
 
-// Count(G, G, every live edge of G): one warp per slab in use (address
-// order, owner = u), the slab's live edges (u, v) one at a time.
+namespace {
+
+// Rank of a vertex for the oriented static count: (bucket count, id), a
+// strict total order in which vertices with more buckets (higher degree at
+// sizing) come later.
+__device__ __forceinline__ unsigned long long tc_rank(uint32_t buckets, uint32_t x)
+{
+    return ((unsigned long long)buckets << 32) | x;
+}
+
+} // namespace
+
+// Static count, each triangle once: with the vertices ranked by tc_rank, a
+// triangle a < b < c is counted on its edge (a, b) as the common neighbour
+// c.  One warp per slab in use (address order, owner u); each live edge
+// (u, v) with rank(u) < rank(v) walks N(u) (u ranks lower, so it has no
+// more buckets than v) slab by slab, and a key lane w with rank(w) > rank(v)
+// looks (v, w) up.  Needs both directions of every edge stored.
 __global__ void __launch_bounds__(256) k_tc_static(GView g, uint32_t mh, unsigned long long *total)
 {
     const uint32_t lane = lane_id();
     const uint64_t all = (uint64_t)g.H + g.P;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long count = 0, slabs = 0;
+    unsigned long long count = 0;
     for (uint64_t s = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; s < all; s += stride) {
-        const uint32_t own = __ldg(&g.owner[s]);
-        if (own == kNil)
+        const uint32_t u = __ldg(&g.owner[s]);
+        if (u == kNil)
             continue;
+        const uint2 vu = __ldg(&g.vinfo[u]);
+        const unsigned long long ru = tc_rank(vu.y, u);
         const uint32_t word = __ldcg(slab_ptr(g, (uint32_t)s) + lane);
-        uint32_t todo = __ballot_sync(kFull, is_key_lane(lane) && word < kTombKey);
+        bool up = false;
+        unsigned long long rv = 0;
+        if (is_key_lane(lane) && word < kTombKey) {
+            rv = tc_rank(__ldg(&g.vinfo[word]).y, word);
+            up = rv > ru;
+        }
+        uint32_t todo = __ballot_sync(kFull, up);
         while (todo) {
             const uint32_t j = __ffs(todo) - 1;
             todo &= todo - 1;
-            count += warp_edge_count(g, g, own, __shfl_sync(kFull, word, j), mh, mh, slabs);
+            const uint32_t v = __shfl_sync(kFull, word, j);
+            const unsigned long long rvj = __shfl_sync(kFull, rv, j);
+            for (uint32_t b = 0; b < vu.y; ++b) {
+                uint32_t slab = vu.x + b;
+                for (uint32_t hop = 0; hop < mh && slab != kNil; ++hop) {
+                    const uint32_t w = __ldcg(slab_ptr(g, slab) + lane);
+                    if (is_key_lane(lane) && w < kTombKey && tc_rank(__ldg(&g.vinfo[w]).y, w) > rvj)
+                        count += lane_has_edge(g, v, w, mh) ? 1u : 0u;
+                    slab = __shfl_sync(kFull, w, kNextLane);
+                }
+            }
         }
     }
     warp_add_u64(total, count);
@@ -378,9 +412,7 @@ mk_status mk_tc_static(mk_graph *g, uint64_t *h_triangles, void *stream)
                         cudaStreamSynchronize(s) != cudaSuccess))
         st = MK_ERR_CUDA;
     cudaFreeAsync(d, s);
-    if (st == MK_OK && total % 6 != 0)
-        st = MK_ERR_INTERNAL; // an undirected graph counts every triangle six times
-    *h_triangles = total / 6;
+    *h_triangles = total;
     return st;
 }
 
