@@ -424,7 +424,8 @@ mk_status mk_pagerank(mk_graph *g, float *d_pr, int warm_start, float damping, f
  * mk_tc_count is the paper's Count kernel: *d_total (device, one uint64)
  * += sum over the n edges (d_src[i], d_dst[i]) of |N_g1(src) ∩ N_g2(dst)|
  * (the walk goes over the side with fewer buckets; the sum is the same).
- * g1 and g2 must have the same V. */
+ * g1 and g2 must have the same V.  The edges are handed to the warps one
+ * at a time from an 8-byte stream-ordered counter allocated for the call. */
 mk_status mk_tc_count(mk_graph *g1, mk_graph *g2, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                       unsigned long long *d_total, void *stream);
 

@@ -189,8 +189,9 @@ __device__ __forceinline__ bool lane_has_edge(const GView &g, uint32_t u, uint32
 
 // |N_g1(u) ∩ N_g2(v)| spread over the warp's lanes (each lane returns its
 // share; the full warp calls it with warp-uniform u, v).  The side with
-// fewer buckets is walked slab by slab (one coalesced load per slab) and
-// each key lane searches the other side for its neighbour.
+// fewer buckets is walked (one list: slab by slab, a word a lane; several:
+// eight lists at a time in 4-lane groups) and each key lane searches the
+// other side for its neighbour.
 __device__ __forceinline__ uint32_t warp_edge_count(const GView &g1, const GView &g2, uint32_t u, uint32_t v,
                                                     uint32_t mh1, uint32_t mh2, unsigned long long &slabs)
 {
@@ -204,14 +205,46 @@ __device__ __forceinline__ uint32_t warp_edge_count(const GView &g1, const GView
     const uint32_t probe = walk_u ? v : u;
     const uint32_t mh = walk_u ? mh1 : mh2, mhs = walk_u ? mh2 : mh1;
     uint32_t count = 0;
-    for (uint32_t b = 0; b < vw.y; ++b) {
-        uint32_t slab = vw.x + b;
+    if (vw.y == 1) {
+        // one list: the warp reads it slab by slab, one word a lane
+        uint32_t slab = vw.x;
         for (uint32_t hop = 0; hop < mh && slab != kNil; ++hop) {
             const uint32_t word = __ldcg(slab_ptr(gw, slab) + lane);
             ++slabs;
             if (is_key_lane(lane) && word < kTombKey)
                 count += lane_has_edge(gs, probe, word, mhs) ? 1u : 0u;
             slab = __shfl_sync(kFull, word, kNextLane);
+        }
+        return count;
+    }
+    // several lists: eight at a time, one per 4-lane group (bucket b by
+    // group b % 8), each lane holding 32 bytes of the slab (four pairs; the
+    // group's last lane three and the unused and next words)
+    const uint32_t g4 = lane >> 2, s4 = lane & 3u, gbase = lane & ~3u;
+    for (uint32_t b0 = 0; b0 < vw.y; b0 += 8) {
+        uint32_t slab = b0 + g4 < vw.y ? vw.x + b0 + g4 : kNil;
+        bool active = slab != kNil;
+        for (uint32_t hop = 0; __any_sync(kFull, active); ++hop) {
+            uint4 lo = make_uint4(kEmptyKey, 0u, kEmptyKey, 0u), hi = lo;
+            if (active) {
+                const uint4 *q = reinterpret_cast<const uint4 *>(slab_ptr(gw, slab) + s4 * 8);
+                lo = __ldcg(q);
+                hi = __ldcg(q + 1);
+                if (s4 == 0)
+                    ++slabs;
+            }
+            const uint32_t key[4] = {lo.x, lo.z, hi.x, s4 == 3u ? kEmptyKey : hi.z};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (active && key[k] < kTombKey)
+                    count += lane_has_edge(gs, probe, key[k], mhs) ? 1u : 0u;
+            const uint32_t nxt = __shfl_sync(kFull, hi.w, gbase + 3);
+            if (active) {
+                if (nxt == kNil || hop + 1 >= mh)
+                    active = false;
+                else
+                    slab = nxt;
+            }
         }
     }
     return count;
@@ -220,31 +253,30 @@ __device__ __forceinline__ uint32_t warp_edge_count(const GView &g1, const GView
 } // namespace
 
 // Count(G1, G2, edges): total += |N_G1(u) ∩ N_G2(v)| over the n edges
-// (u, v); one warp per chunk of 32 edges, the chunk's edges one at a time.
+// (u, v); a persistent grid whose warps take the edges one at a time from a
+// shared counter (*next, zero at launch), so a few edges between two large
+// neighbourhoods do not hold up a whole chunk of others.
 __global__ void __launch_bounds__(256) k_tc_count(GView g1, GView g2, const uint32_t *__restrict__ src,
                                                   const uint32_t *__restrict__ dst, uint64_t n, uint32_t mh1,
-                                                  uint32_t mh2, unsigned long long *total)
+                                                  uint32_t mh2, unsigned long long *total,
+                                                  unsigned long long *next)
 {
     const uint32_t lane = lane_id();
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long count = 0, slabs = 0;
-    for (uint64_t q0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
-        const uint64_t q = q0 + lane;
-        uint32_t u = kNil, v = kNil;
-        if (q < n) {
-            u = __ldg(src + q);
-            v = __ldg(dst + q);
-            if (u >= g1.V || v >= g2.V) {
+    for (;;) {
+        unsigned long long e = 0;
+        if (lane == 0)
+            e = atomicAdd(next, 1ull);
+        e = __shfl_sync(kFull, e, 0);
+        if (e >= n)
+            break;
+        const uint32_t u = __ldg(src + e), v = __ldg(dst + e);
+        if (u >= g1.V || v >= g2.V) {
+            if (lane == 0)
                 set_status(g1.st, kErrInvalid);
-                u = v = kNil;
-            }
+            continue;
         }
-        uint32_t todo = __ballot_sync(kFull, u != kNil);
-        while (todo) {
-            const uint32_t j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            count += warp_edge_count(g1, g2, __shfl_sync(kFull, u, j), __shfl_sync(kFull, v, j), mh1, mh2, slabs);
-        }
+        count += warp_edge_count(g1, g2, u, v, mh1, mh2, slabs);
     }
     warp_add_u64(total, count);
 }
@@ -388,11 +420,16 @@ mk_status mk_tc_count(mk_graph *g1, mk_graph *g2, const uint32_t *d_src, const u
     if (!n)
         return MK_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const uint32_t grid = std::min<uint64_t>(grid_for((n + 31) / 32 * 32, 256), (uint64_t)num_sms() * 32);
-    return timed(g1, "tc_count", s, 1, [&]() {
-        k_tc_count<<<grid, 256, 0, s>>>(g1->v, g2->v, d_src, d_dst, n, g1->v.P + 2, g2->v.P + 2, d_total);
+    const uint32_t grid = std::min<uint64_t>(grid_for(n * 32, 256), (uint64_t)resident_grid(k_tc_count, 256));
+    unsigned long long *next = nullptr;
+    MK_CUDA(cudaMallocAsync((void **)&next, 8, s));
+    MK_CUDA(cudaMemsetAsync(next, 0, 8, s));
+    const mk_status st = timed(g1, "tc_count", s, 1, [&]() {
+        k_tc_count<<<grid, 256, 0, s>>>(g1->v, g2->v, d_src, d_dst, n, g1->v.P + 2, g2->v.P + 2, d_total, next);
         return cudaSuccess;
     });
+    cudaFreeAsync(next, s);
+    return st;
 }
 
 mk_status mk_tc_static(mk_graph *g, uint64_t *h_triangles, void *stream)
