@@ -250,21 +250,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "d02a4f6321c9d54c597b9755964afff47edcd4e96482c736aa2e814f184ab515"
+NCU_TRAFFIC_SOURCES_SHA = "b202d517c851708b6cfec13bc417f41ffd9aa7e5b02e49ca2ade4e9dba767863"
 NCU_TRAFFIC = {
-"sssp_rounds": 49629632,
-    "sssp_relax_into_invalid": 280982272,
-    "sssp_enqueue_invalid": 11002624,
-    "sssp_relax_updated": 26473792,
-    "sssp_invalidate_walk": 8524416,
-    "sssp_invalidate": 13739904,
-    "wcc_hook_all": 350453888,
-    "wcc_hook_updated": 19096832,
-    "insert": 255198592,
-    "delete": 198552704,
-    "query": 131030400,
-    "stage_dedup": 40155264,
-    "update_slab_pointers": 60566592,
+"sssp_rounds": 49431552,
+    "sssp_relax_into_invalid": 280828544,
+    "sssp_enqueue_invalid": 11006080,
+    "sssp_relax_updated": 26474688,
+    "sssp_invalidate_walk": 8525632,
+    "sssp_invalidate": 13739328,
+    "wcc_hook_all": 350458880,
+    "wcc_hook_updated": 19095808,
+    "insert": 255075712,
+    "delete": 198487808,
+    "query": 130971648,
+    "stage_dedup": 40163072,
+    "update_slab_pointers": 60555328,
 }
 
 
