@@ -101,3 +101,21 @@ def test_traffic_reported_only_for_unchanged_kernel_sources(monkeypatch):
     assert bench.ncu_traffic("query") is None
     monkeypatch.setattr(bench, "NCU_TRAFFIC_SOURCES_SHA", "0" * 64)
     assert bench.ncu_traffic("sssp_rounds") is None
+
+
+def test_bench_arguments_and_workload_names():
+    """Every study the benchmark offers is selectable, the road study's
+    sizes and Near-Far width are arguments, and the default is the
+    power-law step with at least three warm-up steps."""
+    import bench
+
+    a = bench.parse_args([])
+    assert a.workload == "powerlaw" and a.gpus == 1 and a.warmup >= 3
+    for w in ("powerlaw", "growth", "served", "road", "analytics", "buckets", "l2", "set"):
+        assert bench.parse_args(["--workload", w]).workload == w
+    r = bench.parse_args(["--workload", "road", "--road-size", "1024", "--road-batches", "2",
+                          "--road-batch-size", "16384", "--road-delta", "4000"])
+    assert (r.road_size, r.road_batches, r.road_batch_size, r.road_delta) == (1024, 2, 16384, 4000)
+    assert bench.parse_args(["--workload", "road"]).road_delta is None
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--workload", "nonsense"])
