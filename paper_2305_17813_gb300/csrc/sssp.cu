@@ -591,15 +591,41 @@ __global__ void k_inv_walk(RoundArgs a)
     bool bad = false;
     const unsigned long long dv = v < a.g.V && v != a.source ? a.D[v] : kInfNode;
     if (dv != kInfNode) {
+        // only parents are read: a tree node's parent word is kNil exactly
+        // when the node is <INF, INVALID> (every finite node names a
+        // vertex), so one 4-byte load and one compare decide a hop; four
+        // hops an iteration, the bound checked once per four
+        const uint32_t *par = reinterpret_cast<const uint32_t *>(a.D); // low word of node x: par[2x]
         uint32_t x = node_parent(dv), hops = 0;
         while (x != a.source) {
-            const unsigned long long dx = a.D[x];
-            if (dx == kInfNode) {
+            uint32_t p = par[2 * (uint64_t)x];
+            if (p == kNil) {
                 bad = true;
                 break;
             }
-            x = node_parent(dx);
-            if (++hops > a.max_rounds) { // parent pointers not a tree: corrupted state
+            if (p == a.source)
+                break;
+            p = par[2 * (uint64_t)p];
+            if (p == kNil) {
+                bad = true;
+                break;
+            }
+            if (p == a.source)
+                break;
+            p = par[2 * (uint64_t)p];
+            if (p == kNil) {
+                bad = true;
+                break;
+            }
+            if (p == a.source)
+                break;
+            p = par[2 * (uint64_t)p];
+            if (p == kNil) {
+                bad = true;
+                break;
+            }
+            x = p;
+            if ((hops += 4) > a.max_rounds) { // parent pointers not a tree: corrupted state
                 set_status(a.g.st, kErrTimeout);
                 break;
             }
