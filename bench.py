@@ -250,21 +250,21 @@ def algorithmic_bytes(family, ctr, n_per_launch, launches):
 # (full workload, one pass), and
 # the SHA-256 of the kernel sources (csrc/) it was taken with.  A figure is
 # reported only while those sources are unchanged; otherwise traffic is null.
-NCU_TRAFFIC_SOURCES_SHA = "b202d517c851708b6cfec13bc417f41ffd9aa7e5b02e49ca2ade4e9dba767863"
+NCU_TRAFFIC_SOURCES_SHA = "23cc176d5d3307aa6d343140c981b5fca75866b242cd4298c6962f3e813fb31d"
 NCU_TRAFFIC = {
-"sssp_rounds": 49431552,
-    "sssp_relax_into_invalid": 280828544,
-    "sssp_enqueue_invalid": 11006080,
-    "sssp_relax_updated": 26474688,
-    "sssp_invalidate_walk": 8525632,
-    "sssp_invalidate": 13739328,
-    "wcc_hook_all": 350458880,
-    "wcc_hook_updated": 19095808,
-    "insert": 255075712,
-    "delete": 198487808,
-    "query": 130971648,
-    "stage_dedup": 40163072,
-    "update_slab_pointers": 60555328,
+"sssp_rounds": 49676000,
+    "sssp_relax_into_invalid": 280899072,
+    "sssp_enqueue_invalid": 11004224,
+    "sssp_relax_updated": 26472768,
+    "sssp_invalidate_walk": 8524864,
+    "sssp_invalidate": 13739456,
+    "wcc_hook_all": 350455296,
+    "wcc_hook_updated": 19096192,
+    "insert": 255002240,
+    "delete": 198414976,
+    "query": 130889088,
+    "stage_dedup": 40148544,
+    "update_slab_pointers": 60540224,
 }
 
 

@@ -401,7 +401,9 @@ __global__ void __launch_bounds__(256) k_set_query(GView g, const uint32_t *__re
 // each lane tests the eight keys of its 32 bytes of a slab at once.  A
 // destination still unreached gets level + 1 with a CAS and its lists join
 // the next frontier: one atomicAdd a warp per slab step for all the new
-// vertices of its eight slabs.  The frontier sizes live on the device in
+// vertices of its eight slabs.  The parents come out of the same pass: an
+// edge read into a vertex of the next level is tight, so an atomicMin of
+// the list's source (its head slab's owner) leaves the smallest one.  The frontier sizes live on the device in
 // three rotating counters (this level reads cnt[L % 3], appends to
 // cnt[(L + 1) % 3] and clears cnt[(L + 2) % 3], the input of the level
 // before), so several levels go out without the host.
